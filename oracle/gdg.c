@@ -1,0 +1,646 @@
+/*
+ * gdg.c -- CPU ORACLE (test infrastructure only): BP guided decimation
+ * guessing (GDG) and the (W,F) sliding-window driver, written step by step in
+ * the paper's order with explicit per-edge messages.
+ *
+ *   Eq. (1)        min-sum CN update (normalised by alpha, Sec. II-A)
+ *   Eq. (2)-(3)    posterior and VN->CN messages, clipped to [-50, 50]
+ *                  ("Do not waste guesses", Sec. IV)
+ *   Eq. (4)        hard decision, early stop once H e = s
+ *   Eq. (5)        path metric
+ *   Sec. II-A      decimation: inactive VNs keep stale messages that their
+ *                  CNs ignore; decimating to 1 flips the neighbours' syndromes
+ *   Alg. 1         SELECT-VN on the four-iteration LLR history
+ *   Alg. 3         aggressive decimation outside the low-error mode
+ *   Sec. IV        peeling of degree-one CNs after each decimation step;
+ *                  a contradiction kills the path (appendix "GDG implementation")
+ *   Alg. 2, Fig. 2 decision paths; here the 2^k guessing tree: at depth D <= k
+ *                  the branch takes bit (k-D) of its id (most significant
+ *                  first) as b and decimates to b + (-1)^b f
+ *   Sec. III       pre-BP on the full window, ranking by the sum of the last
+ *                  four posteriors (ascending, ties by column index), GDG on
+ *                  the first 2w' columns; commit and syndrome update Eq. (10);
+ *                  success = Eq. (11) and Eq. (12)
+ *
+ * Readings where the paper is silent are marked READING and listed in the
+ * design notes.  FP32 throughout, compiled with -ffp-contract=off.
+ */
+#include "qdo.h"
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+int qdo__w(const qdo_dem* d);
+int qdo__ncols(const qdo_dem* d);
+int qdo__ndet(const qdo_dem* d);
+int qdo__R(const qdo_dem* d);
+const int* qdo__col_ptr(const qdo_dem* d);
+const int* qdo__col_dets(const qdo_dem* d);
+const uint32_t* qdo__col_obs(const qdo_dem* d);
+const float* qdo__col_llr(const qdo_dem* d);
+
+enum { BR_CONVERGED = 0, BR_MAXDEPTH = 1, BR_CONTRADICTION = 2, BR_NOCAND = 3 };
+
+/* Tanner graph: CSC with ascending rows; CSR lists CSC edge ids. */
+typedef struct {
+  int nr, nc, ne;
+  int *col_ptr, *col_rows;
+  int *row_ptr, *row_edges;
+  int *edge_col;
+  float* llr;
+  int* vdeg; /* static column weight */
+} graph_t;
+
+static void graph_init(graph_t* g, int nr, int nc, const int* col_ptr, const int* col_rows,
+                       const float* llr) {
+  g->nr = nr;
+  g->nc = nc;
+  g->ne = col_ptr[nc];
+  g->col_ptr = malloc(sizeof(int) * (nc + 1));
+  memcpy(g->col_ptr, col_ptr, sizeof(int) * (nc + 1));
+  g->col_rows = malloc(sizeof(int) * (g->ne > 0 ? g->ne : 1));
+  memcpy(g->col_rows, col_rows, sizeof(int) * g->ne);
+  g->llr = malloc(sizeof(float) * (nc > 0 ? nc : 1));
+  memcpy(g->llr, llr, sizeof(float) * nc);
+  g->row_ptr = calloc(nr + 1, sizeof(int));
+  g->row_edges = malloc(sizeof(int) * (g->ne > 0 ? g->ne : 1));
+  g->edge_col = malloc(sizeof(int) * (g->ne > 0 ? g->ne : 1));
+  g->vdeg = malloc(sizeof(int) * (nc > 0 ? nc : 1));
+  for (int e = 0; e < g->ne; ++e) g->row_ptr[col_rows[e] + 1]++;
+  for (int j = 0; j < nr; ++j) g->row_ptr[j + 1] += g->row_ptr[j];
+  int* fill = malloc(sizeof(int) * (nr > 0 ? nr : 1));
+  memcpy(fill, g->row_ptr, sizeof(int) * nr);
+  for (int i = 0; i < nc; ++i) {
+    g->vdeg[i] = col_ptr[i + 1] - col_ptr[i];
+    for (int e = col_ptr[i]; e < col_ptr[i + 1]; ++e) {
+      g->edge_col[e] = i;
+      g->row_edges[fill[col_rows[e]]++] = e;
+    }
+  }
+  free(fill);
+}
+
+static void graph_free(graph_t* g) {
+  free(g->col_ptr);
+  free(g->col_rows);
+  free(g->row_ptr);
+  free(g->row_edges);
+  free(g->edge_col);
+  free(g->llr);
+  free(g->vdeg);
+}
+
+/* BP / decimation state of one decision path. */
+typedef struct {
+  float *v2c, *c2v, *post;
+  float* hist[4];   /* hist[0] oldest .. hist[3] newest posterior */
+  int8_t* status;   /* -1 active, 0/1 decimated (vn_status of Sec. IV-A) */
+  uint8_t* sp;      /* current syndrome s' (flipped by decimations to 1) */
+  int* deg;         /* number of active VNs of each CN */
+} state_t;
+
+static void state_alloc(state_t* s, const graph_t* g) {
+  int ne = g->ne > 0 ? g->ne : 1, nc = g->nc > 0 ? g->nc : 1, nr = g->nr > 0 ? g->nr : 1;
+  s->v2c = malloc(sizeof(float) * ne);
+  s->c2v = malloc(sizeof(float) * ne);
+  s->post = malloc(sizeof(float) * nc);
+  for (int k = 0; k < 4; ++k) s->hist[k] = malloc(sizeof(float) * nc);
+  s->status = malloc(nc);
+  s->sp = malloc(nr);
+  s->deg = malloc(sizeof(int) * nr);
+}
+
+static void state_free(state_t* s) {
+  free(s->v2c);
+  free(s->c2v);
+  free(s->post);
+  for (int k = 0; k < 4; ++k) free(s->hist[k]);
+  free(s->status);
+  free(s->sp);
+  free(s->deg);
+}
+
+/* t = 0 initialisation (Sec. II-A): mu_{i->j} = Lambda_i; the history starts
+ * filled with the prior (READING: a history shorter than four iterations is
+ * padded with Lambda_i). */
+static void state_reset(state_t* s, const graph_t* g, const uint8_t* synd) {
+  for (int e = 0; e < g->ne; ++e) {
+    s->v2c[e] = g->llr[g->edge_col[e]];
+    s->c2v[e] = 0.0f;
+  }
+  for (int i = 0; i < g->nc; ++i) {
+    s->post[i] = g->llr[i];
+    for (int k = 0; k < 4; ++k) s->hist[k][i] = g->llr[i];
+    s->status[i] = -1;
+  }
+  for (int j = 0; j < g->nr; ++j) {
+    s->sp[j] = synd[j];
+    s->deg[j] = g->row_ptr[j + 1] - g->row_ptr[j];
+  }
+}
+
+static inline float clipf(float x, float c) {
+  if (x > c) return c;
+  if (x < -c) return -c;
+  return x;
+}
+
+/*
+ * One flooding iteration: CN update Eq. (1) over active VNs only, then the VN
+ * update Eq. (2)-(3) for active VNs.  The minimum over N(j)\i is the smallest
+ * |mu| among the OTHER active edges of CN j: that is the second smallest
+ * overall when e holds the (first) smallest, else the smallest.  The sign
+ * product over N(j)\i is the full product times the sign of e.  sign(x) is -1
+ * for x < 0 and +1 otherwise.  READING: a CN with a single active VN sends
+ * alpha * clip (minimum over the empty set taken as the clip bound).
+ */
+static void bp_iteration(const graph_t* g, state_t* s, float alpha, float clip) {
+  for (int j = 0; j < g->nr; ++j) {
+    float min1 = INFINITY, min2 = INFINITY;
+    int amin = -1, neg = 0, na = 0;
+    for (int q = g->row_ptr[j]; q < g->row_ptr[j + 1]; ++q) {
+      int e = g->row_edges[q];
+      if (s->status[g->edge_col[e]] != -1) continue; /* stale message: ignored */
+      float a = fabsf(s->v2c[e]);
+      if (a < min1) {
+        min2 = min1;
+        min1 = a;
+        amin = e;
+      } else if (a < min2) {
+        min2 = a;
+      }
+      neg ^= (s->v2c[e] < 0.0f);
+      ++na;
+    }
+    if (na == 0) continue;
+    for (int q = g->row_ptr[j]; q < g->row_ptr[j + 1]; ++q) {
+      int e = g->row_edges[q];
+      if (s->status[g->edge_col[e]] != -1) continue;
+      float m = (e == amin) ? min2 : min1;
+      if (na == 1) m = clip;
+      int sgn = neg ^ (s->v2c[e] < 0.0f) ^ s->sp[j];
+      float mag = alpha * m;
+      s->c2v[e] = sgn ? -mag : mag;
+    }
+  }
+  for (int i = 0; i < g->nc; ++i) {
+    if (s->status[i] != -1) continue;
+    float p = g->llr[i];
+    for (int e = g->col_ptr[i]; e < g->col_ptr[i + 1]; ++e) p = p + s->c2v[e];
+    s->post[i] = p;
+    for (int e = g->col_ptr[i]; e < g->col_ptr[i + 1]; ++e) s->v2c[e] = clipf(p - s->c2v[e], clip);
+  }
+  /* history of the last four posteriors (Sec. IV-A) */
+  for (int i = 0; i < g->nc; ++i) {
+    s->hist[0][i] = s->hist[1][i];
+    s->hist[1][i] = s->hist[2][i];
+    s->hist[2][i] = s->hist[3][i];
+    s->hist[3][i] = s->post[i];
+  }
+}
+
+/* Eq. (4): e_i = 1 iff posterior <= 0; decimated VNs hold their value. */
+static inline int hard(const state_t* s, int i) {
+  if (s->status[i] != -1) return s->status[i];
+  return s->post[i] <= 0.0f;
+}
+
+/* H e = s on the whole graph.  Decimated-to-one VNs are already folded into
+ * s', so the check runs over active VNs against s'. */
+static int converged(const graph_t* g, const state_t* s) {
+  for (int j = 0; j < g->nr; ++j) {
+    int par = s->sp[j];
+    for (int q = g->row_ptr[j]; q < g->row_ptr[j + 1]; ++q) {
+      int i = g->edge_col[g->row_edges[q]];
+      if (s->status[i] == -1) par ^= (s->post[i] <= 0.0f);
+    }
+    if (par) return 0;
+  }
+  return 1;
+}
+
+/* Fix VN i to value v (Sec. II-A): it leaves the network; its CNs lose one
+ * active neighbour and flip their syndrome when v = 1. */
+static void decimate(const graph_t* g, state_t* s, int i, int v) {
+  s->status[i] = (int8_t)v;
+  for (int e = g->col_ptr[i]; e < g->col_ptr[i + 1]; ++e) {
+    int j = g->col_rows[e];
+    s->deg[j]--;
+    if (v) s->sp[j] ^= 1;
+  }
+}
+
+/* Peeling (Sec. IV "Do not waste guesses"): while some CN has exactly one
+ * active VN, that VN must equal the CN's current syndrome.  A CN left with no
+ * active VN and syndrome 1 is a contradiction (appendix "GDG implementation").
+ * Returns the number of peeled VNs, or -1 on contradiction. */
+static int peel(const graph_t* g, state_t* s) {
+  int n = 0, changed = 1;
+  while (changed) {
+    changed = 0;
+    for (int j = 0; j < g->nr; ++j) {
+      if (s->deg[j] == 0) {
+        if (s->sp[j]) return -1;
+      } else if (s->deg[j] == 1) {
+        int i = -1;
+        for (int q = g->row_ptr[j]; q < g->row_ptr[j + 1]; ++q) {
+          int c = g->edge_col[g->row_edges[q]];
+          if (s->status[c] == -1) { i = c; break; }
+        }
+        decimate(g, s, i, s->sp[j]);
+        ++n;
+        changed = 1;
+      }
+    }
+  }
+  return n;
+}
+
+/* Alg. 3, AGG-DEC.  "hist < P" means all four entries.  Returns 1, 0 or -1. */
+static int agg_dec(const qdo_params* P, const float* h, float L, int D, int main_branch, int n_unsat) {
+  float PA = main_branch ? P->pa_main : P->pa_other;
+  float PB = main_branch ? P->pb_main : P->pb_other;
+  if (D == 1) PB = P->pb_d1;
+  if (h[0] < PA && h[1] < PA && h[2] < PA && h[3] < PA && L < PB) return 1;
+  int allc = h[0] > P->pc && h[1] > P->pc && h[2] > P->pc && h[3] > P->pc;
+  int alld = h[0] > P->pd && h[1] > P->pd && h[2] > P->pd && h[3] > P->pd;
+  if ((allc && D <= P->pc_max_depth) || (alld && n_unsat >= P->n_unsat_min)) return 0;
+  return -1;
+}
+
+/* Alg. 1, SELECT-VN, with Alg. 3 applied to each candidate outside the low
+ * error mode.  Candidates: active VNs of degree >= 3, in index order; strict
+ * '<' keeps the lowest index on ties.  f = 1 iff L_min <= 0 (the sign of
+ * L_min read through Eq. (4)).  Unsatisfied-neighbour counts are taken from
+ * the state before the loop (an aggressive decision always equals the VN's
+ * current hard decision, so it never changes any CN's satisfaction). */
+static int select_vn(const graph_t* g, state_t* s, const qdo_params* P, int D, int main_branch,
+                     int* f_out, int* n_agg) {
+  int* nus = calloc(g->nc > 0 ? g->nc : 1, sizeof(int));
+  if (!P->low_error_mode) {
+    for (int j = 0; j < g->nr; ++j) {
+      int par = s->sp[j];
+      for (int q = g->row_ptr[j]; q < g->row_ptr[j + 1]; ++q) {
+        int i = g->edge_col[g->row_edges[q]];
+        if (s->status[i] == -1) par ^= hard(s, i);
+      }
+      if (!par) continue;
+      for (int q = g->row_ptr[j]; q < g->row_ptr[j + 1]; ++q) nus[g->edge_col[g->row_edges[q]]]++;
+    }
+  }
+  float Lmin = INFINITY, Lt = INFINITY;
+  int gmin = -1, gt = -1;
+  *n_agg = 0;
+  for (int i = 0; i < g->nc; ++i) {
+    if (s->status[i] != -1) continue;
+    if (g->vdeg[i] <= 2) continue;
+    float h[4] = {s->hist[0][i], s->hist[1][i], s->hist[2][i], s->hist[3][i]};
+    float L = ((h[0] + h[1]) + h[2]) + h[3];
+    if (!P->low_error_mode) {
+      int b = agg_dec(P, h, L, D, main_branch, nus[i]);
+      if (b != -1) {
+        decimate(g, s, i, b);
+        (*n_agg)++;
+        continue;
+      }
+    }
+    if (L < Lmin) {
+      Lmin = L;
+      gmin = i;
+    }
+    if (h[0] <= 0.0f && h[1] <= 0.0f && h[2] <= 0.0f && h[3] <= 0.0f && L < Lt) {
+      Lt = L;
+      gt = i;
+    }
+  }
+  free(nus);
+  if (gt != -1) {
+    *f_out = 1;
+    return gt;
+  }
+  *f_out = (gmin != -1 && Lmin <= 0.0f) ? 1 : 0;
+  return gmin;
+}
+
+/* Eq. (5) accumulated in double from the FP32 priors. */
+static double path_metric(const graph_t* g, const state_t* s) {
+  double pm = 0.0;
+  for (int i = 0; i < g->nc; ++i)
+    if (hard(s, i)) pm += (double)g->llr[i];
+  return pm;
+}
+
+/* One decision path of Alg. 2 on graph g (the shortened window). */
+static void run_branch(const graph_t* g, const uint8_t* synd, const qdo_params* P, int id,
+                       state_t* s, qdo_branch_summary* out, qdo_step_record* steps) {
+  int dmax = id == 0 ? P->d_max_main : P->d_max_other;
+  int main_branch = (id == 0);
+  state_reset(s, g, synd);
+  out->status = BR_MAXDEPTH;
+  out->depth = 0;
+  out->iters = 0;
+  out->pm = INFINITY;
+  if (P->peel_at_init && peel(g, s) < 0) {
+    out->status = BR_CONTRADICTION;
+    return;
+  }
+  for (int D = 1; D <= dmax; ++D) {
+    out->depth = D;
+    for (int it = 0; it < P->iters_per_step; ++it) {
+      bp_iteration(g, s, P->alpha, P->clip);
+      out->iters++;
+      if (converged(g, s)) {
+        out->status = BR_CONVERGED;
+        out->pm = path_metric(g, s);
+        return;
+      }
+    }
+    if (D == dmax) break; /* READING: no decimation after the last BP step */
+    int f, nagg;
+    int gsel = select_vn(g, s, P, D, main_branch, &f, &nagg);
+    qdo_step_record* rec = steps ? &steps[D - 1] : NULL;
+    if (gsel < 0) {
+      if (rec) { rec->g = -1; rec->value = -1; rec->n_agg = nagg; rec->n_peel = 0; }
+      out->status = BR_NOCAND;
+      return;
+    }
+    int v = f;
+    if (D <= P->k_guess) {
+      int b = (id >> (P->k_guess - D)) & 1;
+      v = b ? 1 - f : f; /* b + (-1)^b f */
+    }
+    decimate(g, s, gsel, v);
+    int np = peel(g, s);
+    if (rec) { rec->g = gsel; rec->value = v; rec->n_agg = nagg; rec->n_peel = np < 0 ? -1 : np; }
+    if (np < 0) {
+      out->status = BR_CONTRADICTION;
+      return;
+    }
+  }
+}
+
+/* ---- plain BP on an explicit graph (used by tests) ---- */
+int qdo_bp_run(int n_rows, int n_cols, const int* col_ptr, const int* col_rows, const float* llr,
+               const uint8_t* synd, float alpha, float clip, int max_iter, int early_stop,
+               uint8_t* e_out, float* post_out) {
+  graph_t g;
+  graph_init(&g, n_rows, n_cols, col_ptr, col_rows, llr);
+  state_t s;
+  state_alloc(&s, &g);
+  state_reset(&s, &g, synd);
+  int it = 0, conv = 0;
+  while (it < max_iter) {
+    bp_iteration(&g, &s, alpha, clip);
+    ++it;
+    if (converged(&g, &s)) {
+      conv = 1;
+      if (early_stop) break;
+    }
+  }
+  for (int i = 0; i < n_cols; ++i) {
+    e_out[i] = (uint8_t)hard(&s, i);
+    if (post_out) post_out[i] = s.post[i];
+  }
+  state_free(&s);
+  graph_free(&g);
+  return conv ? it : -it;
+}
+
+/* GDG over all 2^k paths of graph g; returns the winning id or -1. */
+static int gdg_all(const graph_t* g, const uint8_t* synd, const qdo_params* P, uint8_t* e_out,
+                   qdo_branch_summary* br_out, qdo_step_record* steps_out, int8_t* status_out) {
+  int nb = 1 << P->k_guess;
+  int dmx = P->d_max_main > P->d_max_other ? P->d_max_main : P->d_max_other;
+  state_t s;
+  state_alloc(&s, g);
+  int best = -1;
+  double best_pm = INFINITY;
+  uint8_t* e0 = malloc(g->nc > 0 ? g->nc : 1);
+  uint8_t* eb = malloc(g->nc > 0 ? g->nc : 1);
+  for (int id = 0; id < nb; ++id) {
+    qdo_branch_summary sm;
+    qdo_step_record* rec = steps_out ? steps_out + (size_t)id * dmx : NULL;
+    if (rec)
+      for (int q = 0; q < dmx; ++q) { rec[q].g = -2; rec[q].value = -1; rec[q].n_agg = 0; rec[q].n_peel = 0; }
+    run_branch(g, synd, P, id, &s, &sm, rec);
+    if (br_out) br_out[id] = sm;
+    if (status_out) memcpy(status_out + (size_t)id * g->nc, s.status, g->nc);
+    if (id == 0)
+      for (int i = 0; i < g->nc; ++i) e0[i] = (uint8_t)hard(&s, i);
+    /* Alg. 2: the estimate with the smallest path metric; ties keep the
+     * lowest id */
+    if (sm.status == BR_CONVERGED && sm.pm < best_pm) {
+      best_pm = sm.pm;
+      best = id;
+      for (int i = 0; i < g->nc; ++i) eb[i] = (uint8_t)hard(&s, i);
+    }
+  }
+  /* READING: if no path converges, the window outputs path 0's estimate */
+  memcpy(e_out, best >= 0 ? eb : e0, g->nc);
+  free(e0);
+  free(eb);
+  state_free(&s);
+  return best;
+}
+
+int qdo_gdg_graph(const qdo_params* P, int n_rows, int n_cols, const int* col_ptr,
+                  const int* col_rows, const float* llr, const uint8_t* synd, uint8_t* corr,
+                  qdo_branch_summary* br) {
+  graph_t g;
+  graph_init(&g, n_rows, n_cols, col_ptr, col_rows, llr);
+  int best = gdg_all(&g, synd, P, corr, br, NULL, NULL);
+  graph_free(&g);
+  return best;
+}
+
+/* Window of the DEM as a graph over its rows and columns. */
+typedef struct {
+  int k, r0, nb, nr, nc, ne, last;
+  int *gcols, *col_ptr, *col_rows;
+  uint8_t* commit;
+  float* llr;
+} window_t;
+
+static void window_build(const qdo_dem* d, int W, int F, int k, window_t* wd) {
+  int info[7];
+  qdo_window_info(d, W, F, k, info);
+  wd->k = k;
+  wd->r0 = info[0];
+  wd->nb = info[1];
+  wd->nr = info[2];
+  wd->nc = info[3];
+  wd->ne = info[4];
+  wd->last = info[6];
+  wd->gcols = malloc(sizeof(int) * (wd->nc + 1));
+  wd->col_ptr = malloc(sizeof(int) * (wd->nc + 1));
+  wd->col_rows = malloc(sizeof(int) * (wd->ne + 1));
+  wd->commit = malloc(wd->nc + 1);
+  wd->llr = malloc(sizeof(float) * (wd->nc + 1));
+  qdo_window_graph(d, W, F, k, wd->gcols, wd->col_ptr, wd->col_rows, wd->commit);
+  const float* L = qdo__col_llr(d);
+  for (int c = 0; c < wd->nc; ++c) wd->llr[c] = L[wd->gcols[c]];
+}
+
+static void window_free(window_t* wd) {
+  free(wd->gcols);
+  free(wd->col_ptr);
+  free(wd->col_rows);
+  free(wd->commit);
+  free(wd->llr);
+}
+
+typedef struct { float key; int idx; } rank_t;
+static int cmp_rank(const void* a, const void* b) {
+  const rank_t* x = a;
+  const rank_t* y = b;
+  if (x->key < y->key) return -1;
+  if (x->key > y->key) return 1;
+  return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+/*
+ * Decode one window (Sec. III + Sec. IV):
+ *   1. n_pre BP iterations on the full window with early stop; a converged
+ *      pre-BP ends the window (READING);
+ *   2. rank columns by ((h0+h1)+h2)+h3 ascending, ties by column index, keep
+ *      the first 2w' (all columns if there are fewer);
+ *   3. GDG on the kept columns (messages restart from the priors), winner by
+ *      Eq. (5); dropped columns are decided 0.
+ */
+static int decode_window_impl(const window_t* wd, const qdo_params* P, const uint8_t* synd,
+                              uint8_t* corr, int* info, int* short_cols, qdo_branch_summary* br,
+                              qdo_step_record* steps, int8_t* fstat) {
+  graph_t g;
+  graph_init(&g, wd->nr, wd->nc, wd->col_ptr, wd->col_rows, wd->llr);
+  state_t s;
+  state_alloc(&s, &g);
+  state_reset(&s, &g, synd);
+  int conv = 0, it = 0;
+  for (it = 0; it < P->n_pre;) {
+    bp_iteration(&g, &s, P->alpha, P->clip);
+    ++it;
+    if (converged(&g, &s)) { conv = 1; break; }
+  }
+  if (P->n_pre == 0 && converged(&g, &s)) conv = 1;
+  if (info) { info[0] = conv; info[1] = -1; info[2] = 0; info[3] = it; }
+  if (conv) {
+    for (int i = 0; i < wd->nc; ++i) corr[i] = (uint8_t)hard(&s, i);
+    state_free(&s);
+    graph_free(&g);
+    return 0;
+  }
+  int ns = wd->nc;
+  int* sel = malloc(sizeof(int) * (wd->nc + 1));
+  if (P->shorten && wd->nc > 2 * wd->nr) ns = 2 * wd->nr;
+  rank_t* rk = malloc(sizeof(rank_t) * (wd->nc + 1));
+  for (int i = 0; i < wd->nc; ++i) {
+    rk[i].key = ((s.hist[0][i] + s.hist[1][i]) + s.hist[2][i]) + s.hist[3][i];
+    rk[i].idx = i;
+  }
+  qsort(rk, wd->nc, sizeof(rank_t), cmp_rank);
+  for (int k = 0; k < ns; ++k) sel[k] = rk[k].idx;
+  free(rk);
+  state_free(&s);
+  /* shortened graph: kept columns in rank order, all window rows */
+  int* cp = malloc(sizeof(int) * (ns + 1));
+  int* cr = malloc(sizeof(int) * (wd->ne + 1));
+  float* ll = malloc(sizeof(float) * (ns + 1));
+  cp[0] = 0;
+  for (int k = 0; k < ns; ++k) {
+    int c = sel[k];
+    int n = 0;
+    for (int e = wd->col_ptr[c]; e < wd->col_ptr[c + 1]; ++e) cr[cp[k] + n++] = wd->col_rows[e];
+    cp[k + 1] = cp[k] + n;
+    ll[k] = wd->llr[c];
+  }
+  graph_t gs;
+  graph_init(&gs, wd->nr, ns, cp, cr, ll);
+  uint8_t* es = malloc(ns + 1);
+  int best = gdg_all(&gs, synd, P, es, br, steps, fstat);
+  memset(corr, 0, wd->nc);
+  for (int k = 0; k < ns; ++k) corr[sel[k]] = es[k];
+  if (info) { info[1] = best; info[2] = ns; }
+  if (short_cols) memcpy(short_cols, sel, sizeof(int) * ns);
+  free(es);
+  graph_free(&gs);
+  free(cp);
+  free(cr);
+  free(ll);
+  free(sel);
+  graph_free(&g);
+  return 0;
+}
+
+int qdo_decode_window(const qdo_dem* d, const qdo_params* P, int k, const uint8_t* synd,
+                      uint8_t* corr, int* info, int* short_cols, qdo_branch_summary* br,
+                      qdo_step_record* steps, int8_t* final_status) {
+  window_t wd;
+  window_build(d, P->W, P->F, k, &wd);
+  int rc = decode_window_impl(&wd, P, synd, corr, info, short_cols, br, steps, final_status);
+  window_free(&wd);
+  return rc;
+}
+
+/*
+ * The (W,F) sliding-window memory experiment (Sec. III).  For each window:
+ * decode, then commit the window's committed columns: XOR their full
+ * detector sets into the running syndrome (this is s_{r+1}' = s_{r+1} +
+ * H_2 e_1, Eq. (10)) and their observable masks into the prediction.  After a
+ * commit the committed blocks must read all zero (Eq. (11)); the final
+ * prediction must equal the sampled observables (Eq. (12)).
+ */
+int qdo_run_shots(const qdo_dem* d, const qdo_params* P, const uint32_t* det_bits,
+                  const uint32_t* obs_bits, int64_t n_shots, uint8_t* fail, uint32_t* obs_pred,
+                  uint32_t* win_corr_words, int corr_words_per_window) {
+  int W = P->W, F = P->F, w = qdo__w(d), ndet = qdo__ndet(d);
+  int nwin = qdo_n_windows(d, W, F);
+  int dw = (ndet + 31) / 32;
+  const int* cptr = qdo__col_ptr(d);
+  const int* cdet = qdo__col_dets(d);
+  const uint32_t* cobs = qdo__col_obs(d);
+  window_t* wins = malloc(sizeof(window_t) * nwin);
+  int maxr = 0, maxc = 0;
+  for (int k = 0; k < nwin; ++k) {
+    window_build(d, W, F, k, &wins[k]);
+    if (wins[k].nr > maxr) maxr = wins[k].nr;
+    if (wins[k].nc > maxc) maxc = wins[k].nc;
+  }
+  uint32_t* det = malloc(sizeof(uint32_t) * dw);
+  uint8_t* synd = malloc(maxr + 1);
+  uint8_t* corr = malloc(maxc + 1);
+  for (int64_t sh = 0; sh < n_shots; ++sh) {
+    memcpy(det, det_bits + sh * dw, sizeof(uint32_t) * dw);
+    uint32_t pred = 0;
+    int fl = 0;
+    for (int k = 0; k < nwin; ++k) {
+      window_t* wd = &wins[k];
+      int row0 = wd->r0 * w;
+      for (int j = 0; j < wd->nr; ++j) synd[j] = (det[(row0 + j) >> 5] >> ((row0 + j) & 31)) & 1;
+      decode_window_impl(wd, P, synd, corr, NULL, NULL, NULL, NULL, NULL);
+      if (win_corr_words) {
+        uint32_t* o = win_corr_words + ((size_t)sh * nwin + k) * corr_words_per_window;
+        memset(o, 0, sizeof(uint32_t) * corr_words_per_window);
+        for (int c = 0; c < wd->nc; ++c)
+          if (corr[c]) o[c >> 5] |= 1u << (c & 31);
+      }
+      for (int c = 0; c < wd->nc; ++c) {
+        if (!wd->commit[c] || !corr[c]) continue;
+        int gc = wd->gcols[c];
+        for (int e = cptr[gc]; e < cptr[gc + 1]; ++e) det[cdet[e] >> 5] ^= 1u << (cdet[e] & 31);
+        pred ^= cobs[gc];
+      }
+      int cb1 = wd->last ? wd->r0 + wd->nb : wd->r0 + F;
+      for (int q = wd->r0 * w; q < cb1 * w; ++q)
+        if ((det[q >> 5] >> (q & 31)) & 1) fl |= 1;
+    }
+    if (pred != obs_bits[sh]) fl |= 2;
+    fail[sh] = (uint8_t)fl;
+    if (obs_pred) obs_pred[sh] = pred;
+  }
+  free(det);
+  free(synd);
+  free(corr);
+  for (int k = 0; k < nwin; ++k) window_free(&wins[k]);
+  free(wins);
+  return 0;
+}

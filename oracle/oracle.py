@@ -1,0 +1,299 @@
+"""ctypes wrapper around the CPU oracle (test infrastructure only).
+
+Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference
+leg may import this module.  The product package never does.
+"""
+import ctypes as C
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class QdoCode(C.Structure):
+    _fields_ = [("l", C.c_int), ("m", C.c_int), ("ax", C.c_int * 3), ("ay", C.c_int * 3),
+                ("bx", C.c_int * 3), ("by", C.c_int * 3)]
+
+
+class QdoParams(C.Structure):
+    _fields_ = [("W", C.c_int), ("F", C.c_int), ("alpha", C.c_float), ("n_pre", C.c_int),
+                ("iters_per_step", C.c_int), ("d_max_main", C.c_int), ("d_max_other", C.c_int),
+                ("k_guess", C.c_int), ("low_error_mode", C.c_int), ("peel_at_init", C.c_int),
+                ("shorten", C.c_int), ("clip", C.c_float), ("pa_main", C.c_float),
+                ("pa_other", C.c_float), ("pb_main", C.c_float), ("pb_other", C.c_float),
+                ("pb_d1", C.c_float), ("pc", C.c_float), ("pd", C.c_float),
+                ("pc_max_depth", C.c_int), ("n_unsat_min", C.c_int)]
+
+
+class QdoBranch(C.Structure):
+    _fields_ = [("status", C.c_int), ("depth", C.c_int), ("iters", C.c_int), ("pm", C.c_double)]
+
+
+class QdoStep(C.Structure):
+    _fields_ = [("g", C.c_int), ("value", C.c_int), ("n_agg", C.c_int), ("n_peel", C.c_int)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        P = C.POINTER
+        L.qdo_dem_build.restype = C.c_void_p
+        L.qdo_dem_build.argtypes = [P(QdoCode), C.c_double, C.c_int]
+        L.qdo_dem_free.argtypes = [C.c_void_p]
+        L.qdo_dem_info.argtypes = [C.c_void_p, C.c_void_p]
+        L.qdo_dem_columns.argtypes = [C.c_void_p] + [C.c_void_p] * 5
+        L.qdo_n_fault_locations.argtypes = [C.c_void_p]
+        L.qdo_fault_effect.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                       C.c_void_p, C.c_void_p]
+        L.qdo_circuit_ops.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
+        L.qdo_logical_matrix.argtypes = [C.c_void_p, C.c_void_p]
+        L.qdo_noiseless_detectors.argtypes = [C.c_void_p, C.c_void_p]
+        L.qdo_n_windows.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.qdo_window_info.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]
+        L.qdo_window_graph.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int] + [C.c_void_p] * 4
+        L.qdo_philox4x32_10.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+        L.qdo_sample.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int64, C.c_void_p,
+                                 C.c_void_p]
+        L.qdo_code_matrices.argtypes = [P(QdoCode), C.c_void_p, C.c_void_p]
+        L.qdo_gf2_rank.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.qdo_logical_z.argtypes = [P(QdoCode), C.c_void_p, C.c_int]
+        L.qdo_bp_run.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_float, C.c_float, C.c_int, C.c_int,
+                                 C.c_void_p, C.c_void_p]
+        L.qdo_decode_window.argtypes = [C.c_void_p, P(QdoParams), C.c_int, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p]
+        L.qdo_gdg_graph.argtypes = [P(QdoParams), C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.qdo_run_shots.argtypes = [C.c_void_p, P(QdoParams), C.c_void_p, C.c_void_p,
+                                    C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def make_code(code):
+    """code: dict(l, m, A=[(ax, ay)]*3, B=[(bx, by)]*3)."""
+    c = QdoCode()
+    c.l, c.m = code["l"], code["m"]
+    for k in range(3):
+        c.ax[k], c.ay[k] = code["A"][k]
+        c.bx[k], c.by[k] = code["B"][k]
+    return c
+
+
+def make_params(p):
+    q = QdoParams()
+    for name, _ in QdoParams._fields_:
+        setattr(q, name, p[name])
+    return q
+
+
+def code_matrices(code):
+    c = make_code(code)
+    w = code["l"] * code["m"]
+    HX = np.zeros((w, 2 * w), np.uint8)
+    HZ = np.zeros((w, 2 * w), np.uint8)
+    lib().qdo_code_matrices(C.byref(c), _ptr(HX), _ptr(HZ))
+    return HX, HZ
+
+
+def gf2_rank(M):
+    M = np.ascontiguousarray(M, dtype=np.uint8)
+    return lib().qdo_gf2_rank(_ptr(M), M.shape[0], M.shape[1])
+
+
+def logical_z(code):
+    c = make_code(code)
+    w = code["l"] * code["m"]
+    LZ = np.zeros((64, 2 * w), np.uint8)
+    K = lib().qdo_logical_z(C.byref(c), _ptr(LZ), 64)
+    return LZ[:K].copy()
+
+
+def philox4x32_10(ctr, key):
+    c = np.asarray(ctr, np.uint32)
+    k = np.asarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().qdo_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def bp_run(n_rows, col_ptr, col_rows, llr, synd, alpha=1.0, clip=50.0, max_iter=100,
+           early_stop=True):
+    col_ptr = np.ascontiguousarray(col_ptr, np.int32)
+    col_rows = np.ascontiguousarray(col_rows, np.int32)
+    llr = np.ascontiguousarray(llr, np.float32)
+    synd = np.ascontiguousarray(synd, np.uint8)
+    n = len(col_ptr) - 1
+    e = np.zeros(n, np.uint8)
+    post = np.zeros(n, np.float32)
+    it = lib().qdo_bp_run(n_rows, n, _ptr(col_ptr), _ptr(col_rows), _ptr(llr), _ptr(synd),
+                          alpha, clip, max_iter, int(early_stop), _ptr(e), _ptr(post))
+    return it, e, post
+
+
+def gdg_graph(params, n_rows, col_ptr, col_rows, llr, synd):
+    col_ptr = np.ascontiguousarray(col_ptr, np.int32)
+    col_rows = np.ascontiguousarray(col_rows, np.int32)
+    llr = np.ascontiguousarray(llr, np.float32)
+    synd = np.ascontiguousarray(synd, np.uint8)
+    n = len(col_ptr) - 1
+    e = np.zeros(n, np.uint8)
+    nb = 1 << params["k_guess"]
+    br = (QdoBranch * nb)()
+    P = make_params(params)
+    best = lib().qdo_gdg_graph(C.byref(P), n_rows, n, _ptr(col_ptr), _ptr(col_rows), _ptr(llr),
+                               _ptr(synd), _ptr(e), br)
+    return best, e, [(b.status, b.depth, b.iters, b.pm) for b in br]
+
+
+class OracleDEM:
+    """Detector error model built by the oracle (direct per-fault simulation)."""
+
+    def __init__(self, code, p, rounds):
+        self.code = code
+        self.p = p
+        self.rounds = rounds
+        self._c = make_code(code)
+        self.h = lib().qdo_dem_build(C.byref(self._c), p, rounds)
+        info = np.zeros(6, np.int32)
+        lib().qdo_dem_info(self.h, _ptr(info))
+        self.n_det, self.n_cols, self.K, self.n_blocks, self.w, nnz = (int(x) for x in info)
+        self.col_ptr = np.zeros(self.n_cols + 1, np.int32)
+        self.col_dets = np.zeros(max(nnz, 1), np.int32)
+        self.col_obs = np.zeros(self.n_cols, np.uint32)
+        self.col_p = np.zeros(self.n_cols, np.float64)
+        self.col_llr = np.zeros(self.n_cols, np.float32)
+        lib().qdo_dem_columns(self.h, _ptr(self.col_ptr), _ptr(self.col_dets), _ptr(self.col_obs),
+                              _ptr(self.col_p), _ptr(self.col_llr))
+        self.det_words = (self.n_det + 31) // 32
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().qdo_dem_free(self.h)
+            self.h = None
+
+    def column(self, c):
+        return tuple(self.col_dets[self.col_ptr[c]:self.col_ptr[c + 1]].tolist()), int(self.col_obs[c])
+
+    def n_fault_locations(self):
+        return lib().qdo_n_fault_locations(self.h)
+
+    def fault_effect(self, loc, pattern):
+        dets = np.zeros(self.n_det, np.int32)
+        obs = np.zeros(1, np.uint32)
+        info = np.zeros(4, np.int32)
+        nd = lib().qdo_fault_effect(self.h, loc, pattern, _ptr(dets), self.n_det, _ptr(obs),
+                                    _ptr(info))
+        return tuple(dets[:nd].tolist()), int(obs[0]), info.tolist()
+
+    def circuit_ops(self):
+        n = lib().qdo_circuit_ops(self.h, None, 0)
+        out = np.zeros((n, 4), np.int32)
+        lib().qdo_circuit_ops(self.h, _ptr(out), n)
+        return out
+
+    def logical_matrix(self):
+        LZ = np.zeros((self.K, 2 * self.w), np.uint8)
+        lib().qdo_logical_matrix(self.h, _ptr(LZ))
+        return LZ
+
+    def noiseless_detectors(self):
+        out = np.zeros(self.n_det, np.uint8)
+        lib().qdo_noiseless_detectors(self.h, _ptr(out))
+        return out
+
+    # ---- windows ----
+    def n_windows(self, W, F):
+        return lib().qdo_n_windows(self.h, W, F)
+
+    def window(self, W, F, k):
+        info = np.zeros(7, np.int32)
+        lib().qdo_window_info(self.h, W, F, k, _ptr(info))
+        r0, nb, nr, nc, ne, ncom, last = (int(x) for x in info)
+        gcols = np.zeros(nc, np.int32)
+        cp = np.zeros(nc + 1, np.int32)
+        cr = np.zeros(max(ne, 1), np.int32)
+        com = np.zeros(nc, np.uint8)
+        lib().qdo_window_graph(self.h, W, F, k, _ptr(gcols), _ptr(cp), _ptr(cr), _ptr(com))
+        return dict(r0=r0, n_blocks=nb, n_rows=nr, n_cols=nc, n_edges=ne, n_commit=ncom,
+                    last=bool(last), gcols=gcols, col_ptr=cp, col_rows=cr[:ne], commit=com,
+                    llr=self.col_llr[gcols])
+
+    # ---- sampling ----
+    def sample(self, seed, shot_offset, n_shots):
+        det = np.zeros((n_shots, self.det_words), np.uint32)
+        obs = np.zeros(n_shots, np.uint32)
+        lib().qdo_sample(self.h, seed, shot_offset, n_shots, _ptr(det), _ptr(obs))
+        return det, obs
+
+    # ---- decoding ----
+    def decode_window(self, params, k, synd, trace=False):
+        W, F = params["W"], params["F"]
+        win = self.window(W, F, k)
+        synd = np.ascontiguousarray(synd, np.uint8)
+        corr = np.zeros(win["n_cols"], np.uint8)
+        info = np.zeros(4, np.int32)
+        P = make_params(params)
+        nb = 1 << params["k_guess"]
+        dmx = max(params["d_max_main"], params["d_max_other"])
+        if trace:
+            sc = np.zeros(win["n_cols"], np.int32)
+            br = (QdoBranch * nb)()
+            steps = (QdoStep * (nb * dmx))()
+            fst = np.zeros(nb * win["n_cols"], np.int8)
+            lib().qdo_decode_window(self.h, C.byref(P), k, _ptr(synd), _ptr(corr), _ptr(info),
+                                    _ptr(sc), br, steps, _ptr(fst))
+            ns = int(info[2])
+            tr = dict(short_cols=sc[:ns].copy(),
+                      branches=[(b.status, b.depth, b.iters, b.pm) for b in br],
+                      steps=[[(s.g, s.value, s.n_agg, s.n_peel) for s in steps[i * dmx:(i + 1) * dmx]]
+                             for i in range(nb)],
+                      final_status=fst.reshape(nb, win["n_cols"])[:, :ns].copy())
+        else:
+            lib().qdo_decode_window(self.h, C.byref(P), k, _ptr(synd), _ptr(corr), _ptr(info),
+                                    None, None, None, None)
+            tr = None
+        return corr, dict(prebp_converged=bool(info[0]), winner=int(info[1]),
+                          n_short=int(info[2]), prebp_iters=int(info[3])), tr
+
+    def run_shots(self, params, det, obs, threads=1, want_corr=False):
+        """Sliding-window decode of every shot.  Returns (fail, obs_pred, corr_words)."""
+        det = np.ascontiguousarray(det, np.uint32)
+        obs = np.ascontiguousarray(obs, np.uint32)
+        n = det.shape[0]
+        fail = np.zeros(n, np.uint8)
+        pred = np.zeros(n, np.uint32)
+        nwin = self.n_windows(params["W"], params["F"])
+        maxc = max(self.window(params["W"], params["F"], k)["n_cols"] for k in range(nwin))
+        cw = (maxc + 31) // 32
+        corr = np.zeros((n, nwin, cw), np.uint32) if want_corr else None
+        P = make_params(params)
+
+        def work(a, b):
+            lib().qdo_run_shots(self.h, C.byref(P), _ptr(det[a:b]), _ptr(obs[a:b]), b - a,
+                                _ptr(fail[a:b]), _ptr(pred[a:b]),
+                                _ptr(corr[a:b]) if want_corr else None, cw)
+
+        threads = max(1, min(threads, n))
+        if threads == 1:
+            work(0, n)
+        else:
+            bounds = np.linspace(0, n, threads + 1).astype(int)
+            with ThreadPoolExecutor(threads) as ex:
+                list(ex.map(lambda ab: work(*ab), zip(bounds[:-1], bounds[1:])))
+        return fail, pred, corr
+
+
+def default_threads():
+    return max(1, len(os.sched_getaffinity(0)))

@@ -1,0 +1,55 @@
+"""Workload definitions: BB codes, noise, decoder presets and seeds.
+
+Plain data only (no decoder arithmetic), so that both the CUDA path and the
+CPU oracle used by the tests draw their inputs from the same definitions.
+
+Codes (appendix "Single shot syndrome noise" gives the [[288,12,18]]
+polynomials; the others are the bivariate-bicycle family decoded in Fig. 3):
+A and B are lists of three monomials x^a y^b as (a, b), in the order the
+polynomial is written; that order fixes which term each CNOT layer uses.
+"""
+
+CODES = {
+    "72": dict(name="[[72,12,6]]", n=72, k=12, d=6, l=6, m=6,
+               A=[(3, 0), (0, 1), (0, 2)], B=[(0, 3), (1, 0), (2, 0)]),
+    "90": dict(name="[[90,8,10]]", n=90, k=8, d=10, l=15, m=3,
+               A=[(9, 0), (0, 1), (0, 2)], B=[(0, 0), (2, 0), (7, 0)]),
+    "108": dict(name="[[108,8,10]]", n=108, k=8, d=10, l=9, m=6,
+                A=[(3, 0), (0, 1), (0, 2)], B=[(0, 3), (1, 0), (2, 0)]),
+    "144": dict(name="[[144,12,12]]", n=144, k=12, d=12, l=12, m=6,
+                A=[(3, 0), (0, 1), (0, 2)], B=[(0, 3), (1, 0), (2, 0)]),
+    "288": dict(name="[[288,12,18]]", n=288, k=12, d=18, l=12, m=12,
+                A=[(3, 0), (0, 2), (0, 7)], B=[(0, 3), (1, 0), (2, 0)]),
+}
+
+# Decoder parameters shared by both presets: Alg. 3 thresholds (P_A..P_D),
+# the message clip of 50, peeling and shortening to 2w' columns.
+_COMMON = dict(W=3, F=1, low_error_mode=0, peel_at_init=1, shorten=1, clip=50.0,
+               pa_main=-3.0, pa_other=0.0, pb_main=-12.0, pb_other=-10.0, pb_d1=-16.0,
+               pc=30.0, pd=3.0, pc_max_depth=4, n_unsat_min=3)
+
+# "configured": normalised min-sum alpha = 0.625, 100 BP iterations on the
+# full window, decimation steps of 10 iterations, 2^k guessing tree.
+CONFIGURED = dict(_COMMON, alpha=0.625, n_pre=100, iters_per_step=10, d_max_main=25)
+
+# "paper": the values of Sec. IV-C (alpha = 1.0, 8 pre-BP iterations for
+# N <= 144, 6 iterations per step, D_max 25 on the main path).
+PAPER = dict(_COMMON, alpha=1.0, n_pre=8, iters_per_step=6, d_max_main=25)
+
+
+def preset(name, k_guess, p=None, **over):
+    """Decoder parameters; the non-main paths run 10 steps past depth k."""
+    base = {"configured": CONFIGURED, "paper": PAPER}[name]
+    out = dict(base, k_guess=k_guess, d_max_other=k_guess + 10)
+    if p is not None and p <= 0.002:
+        out["low_error_mode"] = 1  # Fig. 3 caption: no Alg. 3 for p <= 0.002
+    out.update(over)
+    return out
+
+
+# Seeded synthetic workloads (Monte-Carlo memory experiments).
+WORKLOADS = {
+    "bb72_r6_p3e-3": dict(code="72", rounds=6, p=0.003, k_guess=3, shots=2000, seed=72_003),
+    "bb144_r12_p3e-3": dict(code="144", rounds=12, p=0.003, k_guess=4, shots=100_000,
+                            seed=144_003),
+}
