@@ -1,0 +1,232 @@
+/*
+ * qdec.h -- C ABI of libqdec: a GB300 (sm_103a) sliding-window decoder for
+ * bivariate-bicycle (BB) codes under circuit-level noise, with BP guided
+ * decimation guessing (GDG) as the inner decoder (Gong, Cammerer, Renes,
+ * "Toward Low-latency Iterative Decoding of QLDPC Codes Under Circuit-Level
+ * Noise").
+ *
+ * Conventions
+ *  - Every call returns a qd_status; QD_OK is 0.  On error,
+ *    qd_last_error_message() returns a thread-local description.
+ *  - Handles (qd_dem, qd_decoder) are owned by the library and released with
+ *    the matching *_destroy call.
+ *  - Device buffers are owned by the caller.  Pointers marked "device" must
+ *    point to GPU memory of the current device; all device work is enqueued
+ *    on the given stream and is asynchronous unless stated otherwise.
+ *  - Bit vectors are packed little-endian into uint32 words: bit b of a
+ *    vector is bit (b mod 32) of word b / 32.  Per-shot arrays are row-major
+ *    [n_shots][words].
+ *  - Detector d (0 <= d < n_det) belongs to syndrome block d / w, check
+ *    d mod w, with w = N/2 checks per round (Fig. 1).
+ *  - No entry point allocates device memory after qd_decoder_create.  The
+ *    DEM is copied to the device on its first device use (qd_sample_shots
+ *    or qd_decoder_create); qd_build_dem itself needs no GPU.
+ */
+#ifndef QDEC_H
+#define QDEC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* qd_stream_t; /* a cudaStream_t; NULL = legacy default */
+
+typedef enum {
+  QD_OK = 0,
+  QD_EINVAL = 1,       /* bad argument (null pointer, size out of range)            */
+  QD_ENOMEM = 2,       /* host or device allocation failed                           */
+  QD_ECUDA = 3,        /* a CUDA runtime call failed                                 */
+  QD_ETIMEOUT = 4,     /* a bounded device wait gave up                              */
+  QD_EUNSUPPORTED = 5  /* parameter combination this build does not implement        */
+} qd_status;
+
+/* A BB code (appendix "Single shot syndrome noise"): H_X = [A | B],
+ * H_Z = [B^T | A^T], A = sum_k x^{a_x[k]} y^{a_y[k]}, B likewise, with
+ * x = S_l (x) I_m, y = I_l (x) S_m.  The order of the three terms fixes which
+ * term each CNOT layer of the syndrome circuit uses. */
+typedef struct {
+  int l, m;
+  int a_x[3], a_y[3];
+  int b_x[3], b_y[3];
+} qd_bb_code;
+
+/* Circuit-level depolarizing noise of rate p (Sec. II) on a Z-basis memory
+ * experiment of `rounds` noisy syndrome rounds followed by a noiseless data
+ * readout (appendix "Stim circuit implementation"). */
+typedef struct {
+  double p;
+  int rounds;
+} qd_noise;
+
+/* GDG decoder parameters (Sec. III, Sec. IV, Alg. 1-3, Fig. 2). */
+typedef struct {
+  int W, F;              /* (W,F) sliding window, in syndrome rounds (Sec. III)   */
+  float alpha;           /* normalised min-sum factor (Sec. II-A)                 */
+  int n_pre;             /* BP iterations on the full window before ranking       */
+  int iters_per_step;    /* BP iterations per decimation step; >= 4 on the GPU    */
+  int d_max_main;        /* D_max of path 0 (the main branch)                     */
+  int d_max_other;       /* D_max of every other path                             */
+  int k_guess;           /* guessing depths: 2^k decision paths, 0 <= k <= 5      */
+  int low_error_mode;    /* 1 disables aggressive decimation (Alg. 3)             */
+  int peel_at_init;      /* peel degree-one checks once before the first step    */
+  int shorten;           /* GDG on the first 2w' ranked columns only (Sec. III)   */
+  float clip;            /* bound on |VN->CN| messages (50 in the paper)          */
+  float pa_main, pa_other, pb_main, pb_other, pb_d1, pc, pd; /* Alg. 3 thresholds */
+  int pc_max_depth;      /* P_C applies while D <= this                           */
+  int n_unsat_min;       /* unsatisfied-neighbour count of Alg. 3                 */
+} qd_gdg_params;
+
+typedef struct qd_dem qd_dem;
+typedef struct qd_decoder qd_decoder;
+
+typedef struct {
+  int n_det;       /* detectors = (rounds + 1) * w                            */
+  int n_cols;      /* fault mechanisms (DEM columns) after merging            */
+  int n_obs;       /* logical observables K                                   */
+  int n_blocks;    /* rounds + 1                                              */
+  int w;           /* checks per round, N/2                                   */
+  int det_words;   /* ceil(n_det / 32)                                        */
+  int n_edges;     /* nonzeros of the DEM parity-check matrix                 */
+} qd_dem_info_t;
+
+typedef struct {
+  int r0;          /* first syndrome block of the window                       */
+  int n_blocks;    /* blocks covered                                           */
+  int n_rows;      /* detectors in the window (n_blocks * w)                   */
+  int n_cols;      /* window columns (un-committed faults touching its rows)   */
+  int n_edges;     /* nonzeros of the window matrix                            */
+  int n_commit;    /* committed columns: window columns [0, n_commit)          */
+  int is_last;     /* the last window commits all of its columns               */
+  int n_short;     /* columns GDG runs on (2w' or all)                         */
+} qd_window_info_t;
+
+const char* qd_last_error_message(void);
+
+/*
+ * Build the detector error model of the Z-basis memory experiment
+ * (Sec. II-B): every single fault location of the circuit, X part only, is
+ * mapped to the detectors and observables it flips; mechanisms with the same
+ * detectors and observables merge with p <- p(1-q) + q(1-p), ascending q.
+ * Columns are in canonical order (sorted detector lists, then observable
+ * mask).  Host-side work; needs no GPU.
+ * Errors: QD_EINVAL for l, m < 1, rounds < 1, p outside (0, 0.5).
+ */
+qd_status qd_build_dem(const qd_bb_code* code, const qd_noise* noise, qd_dem** out);
+qd_status qd_dem_info(const qd_dem* dem, qd_dem_info_t* out);
+/* Host copies of the DEM (CSC over detectors): col_ptr[n_cols+1],
+ * col_dets[n_edges], obs[n_cols], prob[n_cols], llr[n_cols] (Lambda_i =
+ * log((1-p_i)/p_i), Sec. II-A).  Any pointer may be NULL. */
+qd_status qd_dem_columns(const qd_dem* dem, int* col_ptr, int* col_dets, uint32_t* obs,
+                         double* prob, float* llr);
+qd_status qd_dem_destroy(qd_dem* dem);
+
+/*
+ * Sample n_shots Monte-Carlo shots of the DEM on the GPU.  Shot s (global
+ * index shot_offset + s) fires column c iff u < round(p_c 2^32), where u is
+ * word (c mod 4) of Philox4x32-10(counter = (c/4, s_lo, s_hi, 0),
+ * key = (seed_lo, seed_hi)); detectors and observables are the XOR of the
+ * fired columns (s = H e, l = L e, Sec. III).
+ * det_bits: device, [n_shots][det_words]; obs_bits: device, [n_shots] (bit k =
+ * observable k).  Errors: QD_EINVAL on null pointers or n_shots < 0.
+ */
+qd_status qd_sample_shots(const qd_dem* dem, uint64_t seed, uint64_t shot_offset, int64_t n_shots,
+                          uint32_t* det_bits, uint32_t* obs_bits, qd_stream_t stream);
+
+/*
+ * Prepare the (W,F) window matrices (Eq. (8)) and the GPU launch plan for
+ * batches of up to max_shots shots.  Allocates all device scratch.  Errors:
+ * QD_EINVAL for bad parameters, QD_EUNSUPPORTED when iters_per_step < 4,
+ * k_guess > 5, or a window too large for shared memory.
+ */
+qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* params, int64_t max_shots,
+                            qd_decoder** out);
+qd_status qd_decoder_destroy(qd_decoder* dec);
+qd_status qd_decoder_n_windows(const qd_decoder* dec, int* n_windows);
+/* Words per shot of the window-correction buffer (max over windows). */
+qd_status qd_decoder_corr_words(const qd_decoder* dec, int* corr_words);
+/* Window k's shape and, if gcols != NULL, its DEM column ids [n_cols]. */
+qd_status qd_window_info(const qd_decoder* dec, int k, qd_window_info_t* out, int* gcols);
+/* Bytes of the optional per-shot trace written by qd_decode_windows. */
+qd_status qd_decoder_trace_bytes(const qd_decoder* dec, size_t* bytes_per_shot);
+
+/*
+ * Decode window k of every shot (Sec. III + Sec. IV): n_pre flooding
+ * min-sum iterations on the window with early stop; if they do not satisfy
+ * the window syndrome, rank columns by the sum of the last four posteriors
+ * and run GDG (Alg. 2, 2^k paths, Alg. 1 selection, Alg. 3 aggressive
+ * decimation, peeling) on the first 2w' columns; the output is the estimate
+ * of least path metric (Eq. (5)).  The window syndrome is read from det_bits
+ * rows [r0*w, (r0+n_blocks)*w) (call qd_commit_and_slide for windows 0..k-1
+ * first).
+ *   det_bits       device [n_shots][det_words], read only
+ *   win_correction device [n_shots][corr_words], out: bit c = estimate of
+ *                  window column c
+ *   status         device [n_shots] or NULL, out: winning path id, -1 when
+ *                  the pre-BP converged, -2 when no path converged
+ *   trace          device, n_shots * trace_bytes, or NULL
+ * Errors: QD_EINVAL (k out of range, n_shots > max_shots, null pointers).
+ */
+qd_status qd_decode_windows(qd_decoder* dec, int k, const uint32_t* det_bits, int64_t n_shots,
+                            uint32_t* win_correction, int32_t* status, void* trace,
+                            qd_stream_t stream);
+
+/*
+ * Commit window k (Sec. III, Eq. (10)): XOR the full detector sets of the
+ * committed columns whose estimate is 1 into det_bits (this is
+ * s_{r+1}' = s_{r+1} + H_2 e_1), XOR their observable masks into obs_pred,
+ * and set bit 0 of residue_fail when a committed block is left non-zero
+ * (Eq. (11) fails).
+ *   det_bits device [n_shots][det_words], updated in place
+ *   obs_pred device [n_shots], updated in place (start from 0)
+ *   residue_fail device [n_shots], updated in place (start from 0)
+ */
+qd_status qd_commit_and_slide(qd_decoder* dec, int k, const uint32_t* win_correction,
+                              int64_t n_shots, uint32_t* det_bits, uint32_t* obs_pred,
+                              uint32_t* residue_fail, qd_stream_t stream);
+
+/*
+ * Success test (Sec. III, appendix "Stim circuit implementation"): a shot
+ * fails when Eq. (11) failed in some window (bit 0) or L e differs from the
+ * sampled observables, Eq. (12) (bit 1).  fail: device [n_shots] out;
+ * n_fail: device int64 counter, incremented by the number of failed shots.
+ */
+qd_status qd_evaluate(const uint32_t* obs_pred, const uint32_t* obs_true,
+                      const uint32_t* residue_fail, int64_t n_shots, uint32_t* fail,
+                      long long* n_fail, qd_stream_t stream);
+
+/*
+ * Whole sliding-window pass on device buffers: for k = 0..n_windows-1
+ * decode window k and commit it, then evaluate.  det_bits is consumed (holds
+ * the residues afterwards); obs_pred, fail: device [n_shots] out; n_fail:
+ * device int64 accumulator (may be NULL).  Uses the decoder's own scratch
+ * for window corrections.
+ */
+qd_status qd_decode_all(qd_decoder* dec, uint32_t* det_bits, const uint32_t* obs_true,
+                        int64_t n_shots, uint32_t* obs_pred, uint32_t* fail, long long* n_fail,
+                        qd_stream_t stream);
+
+/*
+ * qd_decode_all on HOST buffers: copies det_bits / obs_true to the device,
+ * decodes, and copies obs_pred and fail back (pageable or pinned host
+ * memory).  Synchronous: returns when the outputs are on the host.
+ *   det_bits [n_shots][det_words], obs_true [n_shots] in
+ *   obs_pred [n_shots], fail [n_shots] out (either may be NULL)
+ * Errors: QD_EINVAL when n_shots exceeds the decoder's max_shots.
+ */
+qd_status qd_decode_shots_host(qd_decoder* dec, const uint32_t* det_bits, const uint32_t* obs_true,
+                               int64_t n_shots, uint32_t* obs_pred, uint32_t* fail,
+                               long long* n_fail, qd_stream_t stream);
+
+/* Counters of the last qd_decode_windows call of window k, summed over shots:
+ * out[0] pre-BP edge-iterations, out[1] GDG edge-iterations, out[2] windows
+ * whose pre-BP converged, out[3] windows that ran GDG.  Synchronous. */
+qd_status qd_decoder_counters(qd_decoder* dec, long long out[4]);
+qd_status qd_decoder_reset_counters(qd_decoder* dec, qd_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QDEC_H */

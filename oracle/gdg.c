@@ -233,27 +233,28 @@ static void decimate(const graph_t* g, state_t* s, int i, int v) {
 /* Peeling (Sec. IV "Do not waste guesses"): while some CN has exactly one
  * active VN, that VN must equal the CN's current syndrome.  A CN left with no
  * active VN and syndrome 1 is a contradiction (appendix "GDG implementation").
- * Returns the number of peeled VNs, or -1 on contradiction. */
+ * READING: the paper fixes no order; CNs are peeled one at a time, always the
+ * lowest-index degree-one CN, after checking every CN for a contradiction.
+ * Without a contradiction the result does not depend on the order (the forced
+ * values are unique); with one, this order makes the killed path's partial
+ * state well defined.  Returns the number of peeled VNs, or -1. */
 static int peel(const graph_t* g, state_t* s) {
-  int n = 0, changed = 1;
-  while (changed) {
-    changed = 0;
+  int n = 0;
+  for (;;) {
+    int jmin = -1;
     for (int j = 0; j < g->nr; ++j) {
-      if (s->deg[j] == 0) {
-        if (s->sp[j]) return -1;
-      } else if (s->deg[j] == 1) {
-        int i = -1;
-        for (int q = g->row_ptr[j]; q < g->row_ptr[j + 1]; ++q) {
-          int c = g->edge_col[g->row_edges[q]];
-          if (s->status[c] == -1) { i = c; break; }
-        }
-        decimate(g, s, i, s->sp[j]);
-        ++n;
-        changed = 1;
-      }
+      if (s->deg[j] == 0 && s->sp[j]) return -1;
+      if (s->deg[j] == 1 && jmin < 0) jmin = j;
     }
+    if (jmin < 0) return n;
+    int i = -1;
+    for (int q = g->row_ptr[jmin]; q < g->row_ptr[jmin + 1]; ++q) {
+      int c = g->edge_col[g->row_edges[q]];
+      if (s->status[c] == -1) { i = c; break; }
+    }
+    decimate(g, s, i, s->sp[jmin]);
+    ++n;
   }
-  return n;
 }
 
 /* Alg. 3, AGG-DEC.  "hist < P" means all four entries.  Returns 1, 0 or -1. */

@@ -259,7 +259,7 @@ class OracleDEM:
                       branches=[(b.status, b.depth, b.iters, b.pm) for b in br],
                       steps=[[(s.g, s.value, s.n_agg, s.n_peel) for s in steps[i * dmx:(i + 1) * dmx]]
                              for i in range(nb)],
-                      final_status=fst.reshape(nb, win["n_cols"])[:, :ns].copy())
+                      final_status=fst[:nb * ns].reshape(nb, ns).copy())
         else:
             lib().qdo_decode_window(self.h, C.byref(P), k, _ptr(synd), _ptr(corr), _ptr(info),
                                     None, None, None, None)

@@ -1,0 +1,418 @@
+// qdec_api.cu -- the C ABI of libqdec (see include/qdec.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "gdg_kernel.cuh"
+#include "qdec_internal.h"
+
+namespace qd {
+static thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+}  // namespace qd
+
+using qd::set_error;
+
+#define QD_CK(call)                                                                   \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+      return QD_ECUDA;                                                                \
+    }                                                                                 \
+  } while (0)
+
+#define QD_REQ(cond, msg)    \
+  do {                       \
+    if (!(cond)) {           \
+      set_error(msg);        \
+      return QD_EINVAL;      \
+    }                        \
+  } while (0)
+
+struct qd_dem {
+  qd::DemHost h;
+  // device copies, uploaded on first device use (so that the host-side
+  // queries work on a machine without a GPU)
+  mutable int* d_cptr = nullptr;
+  mutable int* d_cdet = nullptr;
+  mutable uint32_t* d_cobs = nullptr;
+  mutable uint32_t* d_thr = nullptr;
+};
+
+namespace {
+
+struct WinGpu {
+  qd::WindowHost h;
+  qd::WinDev dv{};
+  qd::Layout L{};
+  void* d_graph = nullptr;
+  int* d_ccptr = nullptr;  // committed columns: CSR of their global detector ids
+  int* d_ccdet = nullptr;
+  uint32_t* d_ccobs = nullptr;
+  int threads = 0, grid_per_sm = 1;
+};
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& v) {
+  size_t n = std::max<size_t>(v.size(), 1);
+  cudaError_t e = cudaMalloc((void**)dst, n * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if (!v.empty()) e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+qd_status ensure_device(const qd_dem* d) {
+  if (d->d_thr) return QD_OK;
+  QD_CK(upload(&d->d_cptr, d->h.col_ptr));
+  QD_CK(upload(&d->d_cdet, d->h.col_dets));
+  QD_CK(upload(&d->d_cobs, d->h.col_obs));
+  QD_CK(upload(&d->d_thr, d->h.col_thr));
+  return QD_OK;
+}
+
+}  // namespace
+
+struct qd_decoder {
+  const qd_dem* dem = nullptr;
+  qd_gdg_params P{};
+  qd::KParams kp{};
+  long long max_shots = 0;
+  std::vector<WinGpu> wins;
+  int corr_words = 0, dmx = 0, ns_max = 0, sm_count = 0;
+  size_t trace_bytes = 0, smem_max = 0;
+  int* d_work = nullptr;
+  long long* d_counters = nullptr;
+  uint32_t* d_corr = nullptr;
+  uint32_t *d_det = nullptr, *d_obs = nullptr, *d_pred = nullptr, *d_fail = nullptr, *d_resid = nullptr;
+  long long* d_nfail = nullptr;
+};
+
+extern "C" {
+
+const char* qd_last_error_message(void) { return qd::g_err.c_str(); }
+
+qd_status qd_build_dem(const qd_bb_code* code, const qd_noise* noise, qd_dem** out) {
+  QD_REQ(code && noise && out, "qd_build_dem: null argument");
+  QD_REQ(code->l >= 1 && code->m >= 1 && code->l * code->m <= 4096, "qd_build_dem: bad l, m");
+  QD_REQ(noise->rounds >= 1 && noise->rounds <= 1000, "qd_build_dem: bad rounds");
+  QD_REQ(noise->p > 0.0 && noise->p < 0.5, "qd_build_dem: p outside (0, 0.5)");
+  std::unique_ptr<qd_dem> d(new (std::nothrow) qd_dem());
+  if (!d) return QD_ENOMEM;
+  if (!qd::build_dem_host(*code, *noise, d->h)) return QD_EINVAL;
+  for (float l : d->h.col_llr)
+    if (!(l > std::ldexp(1.0f, -15) && l < 16.0f)) {
+      set_error("qd_build_dem: prior LLR outside (2^-15, 16); Eq. (5) would not be exact");
+      return QD_EUNSUPPORTED;
+    }
+  *out = d.release();
+  return QD_OK;
+}
+
+qd_status qd_dem_info(const qd_dem* d, qd_dem_info_t* o) {
+  QD_REQ(d && o, "qd_dem_info: null argument");
+  o->n_det = d->h.n_det;
+  o->n_cols = d->h.n_cols;
+  o->n_obs = d->h.K;
+  o->n_blocks = d->h.R + 1;
+  o->w = d->h.w;
+  o->det_words = (d->h.n_det + 31) / 32;
+  o->n_edges = (int)d->h.col_dets.size();
+  return QD_OK;
+}
+
+qd_status qd_dem_columns(const qd_dem* d, int* col_ptr, int* col_dets, uint32_t* obs, double* prob,
+                         float* llr) {
+  QD_REQ(d, "qd_dem_columns: null dem");
+  const auto& h = d->h;
+  if (col_ptr) std::copy(h.col_ptr.begin(), h.col_ptr.end(), col_ptr);
+  if (col_dets) std::copy(h.col_dets.begin(), h.col_dets.end(), col_dets);
+  if (obs) std::copy(h.col_obs.begin(), h.col_obs.end(), obs);
+  if (prob) std::copy(h.col_p.begin(), h.col_p.end(), prob);
+  if (llr) std::copy(h.col_llr.begin(), h.col_llr.end(), llr);
+  return QD_OK;
+}
+
+qd_status qd_dem_destroy(qd_dem* d) {
+  if (!d) return QD_OK;
+  if (d->d_thr) {
+    cudaFree(d->d_cptr);
+    cudaFree(d->d_cdet);
+    cudaFree(d->d_cobs);
+    cudaFree(d->d_thr);
+  }
+  delete d;
+  return QD_OK;
+}
+
+qd_status qd_sample_shots(const qd_dem* d, uint64_t seed, uint64_t shot_offset, int64_t n_shots,
+                          uint32_t* det_bits, uint32_t* obs_bits, qd_stream_t stream) {
+  QD_REQ(d && det_bits && obs_bits, "qd_sample_shots: null argument");
+  QD_REQ(n_shots >= 0, "qd_sample_shots: n_shots < 0");
+  if (qd_status st = ensure_device(d)) return st;
+  QD_CK(qd::launch_sample((cudaStream_t)stream, d->h.n_cols, d->d_thr, d->d_cptr, d->d_cdet, d->d_cobs,
+                          (d->h.n_det + 31) / 32, seed, shot_offset, n_shots, det_bits, obs_bits));
+  return QD_OK;
+}
+
+qd_status qd_decoder_destroy(qd_decoder* dec) {
+  if (!dec) return QD_OK;
+  for (auto& w : dec->wins) {
+    cudaFree(w.d_graph);
+    cudaFree(w.d_ccptr);
+    cudaFree(w.d_ccdet);
+    cudaFree(w.d_ccobs);
+  }
+  cudaFree(dec->d_work);
+  cudaFree(dec->d_counters);
+  cudaFree(dec->d_corr);
+  cudaFree(dec->d_det);
+  cudaFree(dec->d_obs);
+  cudaFree(dec->d_pred);
+  cudaFree(dec->d_fail);
+  cudaFree(dec->d_resid);
+  cudaFree(dec->d_nfail);
+  delete dec;
+  return QD_OK;
+}
+
+qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t max_shots,
+                            qd_decoder** out) {
+  QD_REQ(dem && p && out, "qd_decoder_create: null argument");
+  QD_REQ(max_shots >= 1, "qd_decoder_create: max_shots < 1");
+  QD_REQ(p->W >= 1 && p->F >= 1 && p->F <= p->W, "qd_decoder_create: need 1 <= F <= W");
+  QD_REQ(p->n_pre >= 0 && p->iters_per_step >= 1 && p->d_max_main >= 1 && p->d_max_other >= 1,
+         "qd_decoder_create: bad iteration counts");
+  QD_REQ(p->alpha > 0.0f && p->clip > 0.0f, "qd_decoder_create: alpha and clip must be positive");
+  if (p->iters_per_step < 4) {
+    set_error("qd_decoder_create: iters_per_step < 4 is not implemented on the GPU");
+    return QD_EUNSUPPORTED;
+  }
+  if (p->k_guess < 0 || p->k_guess > 5) {
+    set_error("qd_decoder_create: k_guess must be in [0, 5]");
+    return QD_EUNSUPPORTED;
+  }
+  if (qd_status st = ensure_device(dem)) return st;
+  std::unique_ptr<qd_decoder> dec(new (std::nothrow) qd_decoder());
+  if (!dec) return QD_ENOMEM;
+  dec->dem = dem;
+  dec->P = *p;
+  dec->max_shots = max_shots;
+  qd::KParams& k = dec->kp;
+  k.alpha = p->alpha;
+  k.clip = p->clip;
+  k.pa_main = p->pa_main;
+  k.pa_other = p->pa_other;
+  k.pb_main = p->pb_main;
+  k.pb_other = p->pb_other;
+  k.pb_d1 = p->pb_d1;
+  k.pc = p->pc;
+  k.pd = p->pd;
+  k.n_pre = p->n_pre;
+  k.ips = p->iters_per_step;
+  k.dmax_main = p->d_max_main;
+  k.dmax_other = p->d_max_other;
+  k.k = p->k_guess;
+  k.low_err = p->low_error_mode;
+  k.peel_init = p->peel_at_init;
+  k.pc_max_depth = p->pc_max_depth;
+  k.n_unsat_min = p->n_unsat_min;
+  k.nb = 1 << p->k_guess;
+  dec->dmx = std::max(p->d_max_main, p->d_max_other);
+
+  int dev = 0, optin = 0;
+  QD_CK(cudaGetDevice(&dev));
+  QD_CK(cudaDeviceGetAttribute(&dec->sm_count, cudaDevAttrMultiProcessorCount, dev));
+  QD_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+
+  const int nwin = qd::n_windows(dem->h, p->W, p->F);
+  const int nwarps = std::min(16, std::max(4, k.nb));
+  dec->wins.resize(nwin);
+  for (int w = 0; w < nwin; ++w) {
+    WinGpu& g = dec->wins[w];
+    if (!qd::build_window(dem->h, p->W, p->F, w, p->shorten != 0, g.h)) return QD_EINVAL;
+    const auto& h = g.h;
+    dec->corr_words = std::max(dec->corr_words, (h.n_cols + 31) / 32);
+    dec->ns_max = std::max(dec->ns_max, h.n_short);
+    g.L = qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, k.nb, nwarps);
+    g.threads = 32 * nwarps;
+    if (g.L.total > (unsigned)optin) {
+      set_error("qd_decoder_create: window " + std::to_string(w) + " needs " +
+                std::to_string(g.L.total) + " B of shared memory (limit " + std::to_string(optin) + ")");
+      return QD_EUNSUPPORTED;
+    }
+    dec->smem_max = std::max<size_t>(dec->smem_max, g.L.total);
+    // graph arrays in one allocation
+    size_t o_cp = 0, o_cr = o_cp + 2 * h.col_ptr.size(), o_rp = o_cr + 2 * h.col_rows.size(),
+           o_re = o_rp + 2 * h.row_ptr.size(), o_ec = o_re + 2 * h.row_edges.size(),
+           o_ll = (o_ec + 2 * h.edge_col.size() + 15) & ~(size_t)15, tot = o_ll + 4 * h.llr.size();
+    std::vector<char> blob(tot);
+    memcpy(blob.data() + o_cp, h.col_ptr.data(), 2 * h.col_ptr.size());
+    memcpy(blob.data() + o_cr, h.col_rows.data(), 2 * h.col_rows.size());
+    memcpy(blob.data() + o_rp, h.row_ptr.data(), 2 * h.row_ptr.size());
+    memcpy(blob.data() + o_re, h.row_edges.data(), 2 * h.row_edges.size());
+    memcpy(blob.data() + o_ec, h.edge_col.data(), 2 * h.edge_col.size());
+    memcpy(blob.data() + o_ll, h.llr.data(), 4 * h.llr.size());
+    QD_CK(cudaMalloc(&g.d_graph, tot));
+    QD_CK(cudaMemcpy(g.d_graph, blob.data(), tot, cudaMemcpyHostToDevice));
+    char* b = (char*)g.d_graph;
+    g.dv = qd::WinDev{h.n_rows, h.n_cols, h.n_edges, h.row0, h.n_short, h.short_edges_max,
+                      (const uint16_t*)(b + o_cp), (const uint16_t*)(b + o_cr), (const uint16_t*)(b + o_rp),
+                      (const uint16_t*)(b + o_re), (const uint16_t*)(b + o_ec), (const float*)(b + o_ll)};
+    // committed columns: their full detector sets and observables
+    std::vector<int> cc_ptr(1, 0), cc_det;
+    std::vector<uint32_t> cc_obs;
+    for (int c = 0; c < h.n_commit; ++c) {
+      int gc = h.gcols[c];
+      for (int e = dem->h.col_ptr[gc]; e < dem->h.col_ptr[gc + 1]; ++e) cc_det.push_back(dem->h.col_dets[e]);
+      cc_ptr.push_back((int)cc_det.size());
+      cc_obs.push_back(dem->h.col_obs[gc]);
+    }
+    QD_CK(upload(&g.d_ccptr, cc_ptr));
+    QD_CK(upload(&g.d_ccdet, cc_det));
+    QD_CK(upload(&g.d_ccobs, cc_obs));
+  }
+  QD_CK(qd::set_decode_smem(dec->smem_max));
+  for (auto& g : dec->wins) {
+    int blocks = 0;
+    QD_CK(qd::decode_occupancy(g.threads, g.L.total, &blocks));
+    g.grid_per_sm = std::max(1, blocks);
+  }
+  dec->trace_bytes = qd::trace_bytes_per_shot(k.nb, dec->dmx, dec->ns_max);
+  QD_CK(cudaMalloc(&dec->d_work, sizeof(int) * (nwin + 1)));
+  QD_CK(cudaMalloc(&dec->d_counters, sizeof(long long) * 4));
+  QD_CK(cudaMemset(dec->d_counters, 0, sizeof(long long) * 4));
+  const int dw = (dem->h.n_det + 31) / 32;
+  QD_CK(cudaMalloc(&dec->d_corr, sizeof(uint32_t) * (size_t)max_shots * dec->corr_words));
+  QD_CK(cudaMalloc(&dec->d_det, sizeof(uint32_t) * (size_t)max_shots * dw));
+  QD_CK(cudaMalloc(&dec->d_obs, sizeof(uint32_t) * (size_t)max_shots));
+  QD_CK(cudaMalloc(&dec->d_pred, sizeof(uint32_t) * (size_t)max_shots));
+  QD_CK(cudaMalloc(&dec->d_fail, sizeof(uint32_t) * (size_t)max_shots));
+  QD_CK(cudaMalloc(&dec->d_resid, sizeof(uint32_t) * (size_t)max_shots));
+  QD_CK(cudaMalloc(&dec->d_nfail, sizeof(long long)));
+  *out = dec.release();
+  return QD_OK;
+}
+
+qd_status qd_decoder_n_windows(const qd_decoder* dec, int* n) {
+  QD_REQ(dec && n, "null argument");
+  *n = (int)dec->wins.size();
+  return QD_OK;
+}
+
+qd_status qd_decoder_corr_words(const qd_decoder* dec, int* cw) {
+  QD_REQ(dec && cw, "null argument");
+  *cw = dec->corr_words;
+  return QD_OK;
+}
+
+qd_status qd_decoder_trace_bytes(const qd_decoder* dec, size_t* b) {
+  QD_REQ(dec && b, "null argument");
+  *b = dec->trace_bytes;
+  return QD_OK;
+}
+
+qd_status qd_window_info(const qd_decoder* dec, int k, qd_window_info_t* o, int* gcols) {
+  QD_REQ(dec && o, "null argument");
+  QD_REQ(k >= 0 && k < (int)dec->wins.size(), "qd_window_info: window out of range");
+  const auto& h = dec->wins[k].h;
+  *o = qd_window_info_t{h.r0, h.n_blocks, h.n_rows, h.n_cols, h.n_edges, h.n_commit, h.last, h.n_short};
+  if (gcols) std::copy(h.gcols.begin(), h.gcols.end(), gcols);
+  return QD_OK;
+}
+
+qd_status qd_decode_windows(qd_decoder* dec, int k, const uint32_t* det_bits, int64_t n_shots,
+                            uint32_t* win_correction, int32_t* status, void* trace, qd_stream_t stream) {
+  QD_REQ(dec && det_bits && win_correction, "qd_decode_windows: null argument");
+  QD_REQ(k >= 0 && k < (int)dec->wins.size(), "qd_decode_windows: window out of range");
+  QD_REQ(n_shots >= 0 && n_shots <= dec->max_shots, "qd_decode_windows: n_shots outside [0, max_shots]");
+  if (n_shots == 0) return QD_OK;
+  const WinGpu& g = dec->wins[k];
+  cudaStream_t st = (cudaStream_t)stream;
+  QD_CK(cudaMemsetAsync(dec->d_work + k, 0, sizeof(int), st));
+  long long grid = std::min<long long>(n_shots, (long long)dec->sm_count * g.grid_per_sm);
+  QD_CK(qd::launch_decode((int)grid, g.threads, g.L.total, st, dec->kp, g.dv, g.L, det_bits,
+                          (dec->dem->h.n_det + 31) / 32, n_shots, win_correction, dec->corr_words, status,
+                          (char*)trace, dec->trace_bytes, dec->dmx, dec->ns_max, dec->d_work + k,
+                          dec->d_counters));
+  return QD_OK;
+}
+
+qd_status qd_commit_and_slide(qd_decoder* dec, int k, const uint32_t* win_correction, int64_t n_shots,
+                              uint32_t* det_bits, uint32_t* obs_pred, uint32_t* residue_fail,
+                              qd_stream_t stream) {
+  QD_REQ(dec && win_correction && det_bits && obs_pred && residue_fail, "qd_commit_and_slide: null argument");
+  QD_REQ(k >= 0 && k < (int)dec->wins.size(), "qd_commit_and_slide: window out of range");
+  QD_REQ(n_shots >= 0, "qd_commit_and_slide: n_shots < 0");
+  const WinGpu& g = dec->wins[k];
+  const int w = dec->dem->h.w;
+  QD_CK(qd::launch_commit((cudaStream_t)stream, g.h.n_commit, g.d_ccptr, g.d_ccdet, g.d_ccobs,
+                          dec->corr_words, win_correction, n_shots, det_bits, (dec->dem->h.n_det + 31) / 32,
+                          obs_pred, residue_fail, g.h.r0 * w, g.h.commit_b1 * w));
+  return QD_OK;
+}
+
+qd_status qd_evaluate(const uint32_t* obs_pred, const uint32_t* obs_true, const uint32_t* residue_fail,
+                      int64_t n_shots, uint32_t* fail, long long* n_fail, qd_stream_t stream) {
+  QD_REQ(obs_pred && obs_true && residue_fail, "qd_evaluate: null argument");
+  QD_REQ(n_shots >= 0, "qd_evaluate: n_shots < 0");
+  QD_CK(qd::launch_evaluate((cudaStream_t)stream, obs_pred, obs_true, residue_fail, n_shots, fail, n_fail));
+  return QD_OK;
+}
+
+qd_status qd_decode_all(qd_decoder* dec, uint32_t* det_bits, const uint32_t* obs_true, int64_t n_shots,
+                        uint32_t* obs_pred, uint32_t* fail, long long* n_fail, qd_stream_t stream) {
+  QD_REQ(dec && det_bits && obs_true && obs_pred, "qd_decode_all: null argument");
+  QD_REQ(n_shots >= 0 && n_shots <= dec->max_shots, "qd_decode_all: n_shots outside [0, max_shots]");
+  if (n_shots == 0) return QD_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  QD_CK(cudaMemsetAsync(obs_pred, 0, sizeof(uint32_t) * n_shots, st));
+  QD_CK(cudaMemsetAsync(dec->d_resid, 0, sizeof(uint32_t) * n_shots, st));
+  for (int k = 0; k < (int)dec->wins.size(); ++k) {
+    qd_status s = qd_decode_windows(dec, k, det_bits, n_shots, dec->d_corr, nullptr, nullptr, stream);
+    if (s != QD_OK) return s;
+    s = qd_commit_and_slide(dec, k, dec->d_corr, n_shots, det_bits, obs_pred, dec->d_resid, stream);
+    if (s != QD_OK) return s;
+  }
+  return qd_evaluate(obs_pred, obs_true, dec->d_resid, n_shots, fail, n_fail, stream);
+}
+
+qd_status qd_decode_shots_host(qd_decoder* dec, const uint32_t* det_bits, const uint32_t* obs_true,
+                               int64_t n_shots, uint32_t* obs_pred, uint32_t* fail, long long* n_fail,
+                               qd_stream_t stream) {
+  QD_REQ(dec && det_bits && obs_true, "qd_decode_shots_host: null argument");
+  QD_REQ(n_shots >= 0 && n_shots <= dec->max_shots, "qd_decode_shots_host: n_shots outside [0, max_shots]");
+  if (n_shots == 0) return QD_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t dw = (dec->dem->h.n_det + 31) / 32;
+  QD_CK(cudaMemcpyAsync(dec->d_det, det_bits, sizeof(uint32_t) * dw * n_shots, cudaMemcpyHostToDevice, st));
+  QD_CK(cudaMemcpyAsync(dec->d_obs, obs_true, sizeof(uint32_t) * n_shots, cudaMemcpyHostToDevice, st));
+  QD_CK(cudaMemsetAsync(dec->d_nfail, 0, sizeof(long long), st));
+  qd_status s = qd_decode_all(dec, dec->d_det, dec->d_obs, n_shots, dec->d_pred, dec->d_fail, dec->d_nfail, stream);
+  if (s != QD_OK) return s;
+  if (obs_pred)
+    QD_CK(cudaMemcpyAsync(obs_pred, dec->d_pred, sizeof(uint32_t) * n_shots, cudaMemcpyDeviceToHost, st));
+  if (fail) QD_CK(cudaMemcpyAsync(fail, dec->d_fail, sizeof(uint32_t) * n_shots, cudaMemcpyDeviceToHost, st));
+  if (n_fail) QD_CK(cudaMemcpyAsync(n_fail, dec->d_nfail, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  QD_CK(cudaStreamSynchronize(st));
+  return QD_OK;
+}
+
+qd_status qd_decoder_counters(qd_decoder* dec, long long out[4]) {
+  QD_REQ(dec && out, "null argument");
+  QD_CK(cudaMemcpy(out, dec->d_counters, sizeof(long long) * 4, cudaMemcpyDeviceToHost));
+  return QD_OK;
+}
+
+qd_status qd_decoder_reset_counters(qd_decoder* dec, qd_stream_t stream) {
+  QD_REQ(dec, "null argument");
+  QD_CK(cudaMemsetAsync(dec->d_counters, 0, sizeof(long long) * 4, (cudaStream_t)stream));
+  return QD_OK;
+}
+
+}  // extern "C"

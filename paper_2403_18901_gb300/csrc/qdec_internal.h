@@ -1,0 +1,67 @@
+// qdec_internal.h -- host-side data structures of libqdec (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qdec.h"
+
+namespace qd {
+
+void set_error(const std::string& msg);
+
+// One window of the (W,F) schedule (Sec. III, Eq. (8)), host copy.
+struct WindowHost {
+  int k = 0, r0 = 0, n_blocks = 0, n_rows = 0, n_cols = 0, n_edges = 0, n_commit = 0, last = 0;
+  int n_short = 0;        // columns GDG runs on
+  int short_edges_max = 0;  // bound on the edges of the shortened matrix
+  int row0 = 0;           // first detector id of the window
+  int commit_b1 = 0;      // committed blocks are [r0, commit_b1)
+  std::vector<int> gcols;                 // window column -> DEM column
+  std::vector<uint16_t> col_ptr, col_rows;  // CSC over window rows (ascending)
+  std::vector<uint16_t> row_ptr, row_edges; // CSR listing CSC edge ids
+  std::vector<uint16_t> edge_col;           // CSC edge id -> window column
+  std::vector<float> llr;
+};
+
+struct DemHost {
+  qd_bb_code code{};
+  qd_noise noise{};
+  int w = 0, R = 0, K = 0, n_det = 0, n_cols = 0;
+  std::vector<int> col_ptr, col_dets;
+  std::vector<uint32_t> col_obs;
+  std::vector<double> col_p;
+  std::vector<float> col_llr;
+  std::vector<uint32_t> col_thr;  // sampling threshold round(p 2^32)
+};
+
+struct KParams;
+struct WinDev;
+struct Layout;
+
+// Build the merged DEM (backward sensitivity sweep over the circuit).
+bool build_dem_host(const qd_bb_code& code, const qd_noise& noise, DemHost& out);
+int n_windows(const DemHost& d, int W, int F);
+bool build_window(const DemHost& d, int W, int F, int k, bool shorten, WindowHost& out);
+
+size_t trace_bytes_per_shot(int nb, int dmx, int ns_max);
+cudaError_t set_decode_smem(size_t bytes);
+cudaError_t decode_occupancy(int threads, size_t smem, int* blocks);
+cudaError_t launch_decode(int grid, int threads, size_t smem, cudaStream_t st, const KParams& P,
+                          const WinDev& W, const Layout& L, const uint32_t* det, int det_words,
+                          long long n, uint32_t* corr, int corr_words, int32_t* status, char* trace,
+                          size_t tr_bytes, int dmx, int ns_max, int* work, long long* counters);
+cudaError_t launch_sample(cudaStream_t st, int n_cols, const uint32_t* thr, const int* cptr,
+                          const int* cdet, const uint32_t* cobs, int det_words,
+                          unsigned long long seed, unsigned long long off, long long n, uint32_t* det,
+                          uint32_t* obs);
+cudaError_t launch_commit(cudaStream_t st, int n_commit, const int* cptr, const int* cdet,
+                          const uint32_t* cobs, int corr_words, const uint32_t* corr, long long n,
+                          uint32_t* det, int det_words, uint32_t* obs_pred, uint32_t* resid, int b0,
+                          int b1);
+cudaError_t launch_evaluate(cudaStream_t st, const uint32_t* pred, const uint32_t* obs,
+                            const uint32_t* resid, long long n, uint32_t* fail, long long* n_fail);
+
+}  // namespace qd

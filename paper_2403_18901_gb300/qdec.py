@@ -1,0 +1,260 @@
+"""Python binding of libqdec (argument marshalling only).
+
+Every step of the decoder runs in the CUDA library; this module converts
+torch tensors to raw pointers, numpy arrays to host pointers and C status
+codes to exceptions.  There is no fallback: if libqdec.so is missing or a
+call fails, it raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libqdec.so")
+
+QD_OK, QD_EINVAL, QD_ENOMEM, QD_ECUDA, QD_ETIMEOUT, QD_EUNSUPPORTED = range(6)
+_NAMES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EUNSUPPORTED"}
+
+
+class QdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libqdec {_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class BBCode(C.Structure):
+    _fields_ = [("l", C.c_int), ("m", C.c_int), ("a_x", C.c_int * 3), ("a_y", C.c_int * 3),
+                ("b_x", C.c_int * 3), ("b_y", C.c_int * 3)]
+
+
+class Noise(C.Structure):
+    _fields_ = [("p", C.c_double), ("rounds", C.c_int)]
+
+
+class GdgParams(C.Structure):
+    _fields_ = [("W", C.c_int), ("F", C.c_int), ("alpha", C.c_float), ("n_pre", C.c_int),
+                ("iters_per_step", C.c_int), ("d_max_main", C.c_int), ("d_max_other", C.c_int),
+                ("k_guess", C.c_int), ("low_error_mode", C.c_int), ("peel_at_init", C.c_int),
+                ("shorten", C.c_int), ("clip", C.c_float), ("pa_main", C.c_float),
+                ("pa_other", C.c_float), ("pb_main", C.c_float), ("pb_other", C.c_float),
+                ("pb_d1", C.c_float), ("pc", C.c_float), ("pd", C.c_float),
+                ("pc_max_depth", C.c_int), ("n_unsat_min", C.c_int)]
+
+
+class DemInfo(C.Structure):
+    _fields_ = [(n, C.c_int) for n in ("n_det", "n_cols", "n_obs", "n_blocks", "w", "det_words",
+                                       "n_edges")]
+
+
+class WindowInfo(C.Structure):
+    _fields_ = [(n, C.c_int) for n in ("r0", "n_blocks", "n_rows", "n_cols", "n_edges", "n_commit",
+                                       "is_last", "n_short")]
+
+
+# symbol -> (restype, argtypes)
+_VP, _I, _I64, _U64, _SZ = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_size_t
+_SIGS = {
+    "qd_last_error_message": (C.c_char_p, []),
+    "qd_build_dem": (_I, [C.POINTER(BBCode), C.POINTER(Noise), C.POINTER(_VP)]),
+    "qd_dem_info": (_I, [_VP, C.POINTER(DemInfo)]),
+    "qd_dem_columns": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "qd_dem_destroy": (_I, [_VP]),
+    "qd_sample_shots": (_I, [_VP, _U64, _U64, _I64, _VP, _VP, _VP]),
+    "qd_decoder_create": (_I, [_VP, C.POINTER(GdgParams), _I64, C.POINTER(_VP)]),
+    "qd_decoder_destroy": (_I, [_VP]),
+    "qd_decoder_n_windows": (_I, [_VP, C.POINTER(_I)]),
+    "qd_decoder_corr_words": (_I, [_VP, C.POINTER(_I)]),
+    "qd_window_info": (_I, [_VP, _I, C.POINTER(WindowInfo), _VP]),
+    "qd_decoder_trace_bytes": (_I, [_VP, C.POINTER(_SZ)]),
+    "qd_decode_windows": (_I, [_VP, _I, _VP, _I64, _VP, _VP, _VP, _VP]),
+    "qd_commit_and_slide": (_I, [_VP, _I, _VP, _I64, _VP, _VP, _VP, _VP]),
+    "qd_evaluate": (_I, [_VP, _VP, _VP, _I64, _VP, _VP, _VP]),
+    "qd_decode_all": (_I, [_VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP]),
+    "qd_decode_shots_host": (_I, [_VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP]),
+    "qd_decoder_counters": (_I, [_VP, _VP]),
+    "qd_decoder_reset_counters": (_I, [_VP, _VP]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libqdec.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libqdec.so not built ({LIB_PATH}); run paper_2403_18901_gb300/build.py")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code != QD_OK:
+        raise QdError(code, lib().qd_last_error_message().decode(errors="replace"))
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor (device or host) or numpy array; None passes through."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data_as(C.c_void_p)
+    assert x.is_contiguous()
+    return C.c_void_p(x.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def make_code(code):
+    c = BBCode()
+    c.l, c.m = code["l"], code["m"]
+    for k in range(3):
+        c.a_x[k], c.a_y[k] = code["A"][k]
+        c.b_x[k], c.b_y[k] = code["B"][k]
+    return c
+
+
+def make_params(p):
+    q = GdgParams()
+    for name, _ in GdgParams._fields_:
+        setattr(q, name, p[name])
+    return q
+
+
+class Dem:
+    """Detector error model of the Z-basis memory experiment (qd_build_dem)."""
+
+    def __init__(self, code, p, rounds):
+        self.code, self.p, self.rounds = code, p, rounds
+        h = C.c_void_p()
+        _check(lib().qd_build_dem(C.byref(make_code(code)), C.byref(Noise(p, rounds)), C.byref(h)))
+        self.h = h
+        inf = DemInfo()
+        _check(lib().qd_dem_info(self.h, C.byref(inf)))
+        self.info = inf
+        self.n_det, self.n_cols, self.K = inf.n_det, inf.n_cols, inf.n_obs
+        self.w, self.det_words, self.n_blocks = inf.w, inf.det_words, inf.n_blocks
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.qd_dem_destroy(self.h)
+            self.h = None
+
+    def columns(self):
+        cp = np.zeros(self.n_cols + 1, np.int32)
+        cd = np.zeros(max(self.info.n_edges, 1), np.int32)
+        ob = np.zeros(self.n_cols, np.uint32)
+        pr = np.zeros(self.n_cols, np.float64)
+        ll = np.zeros(self.n_cols, np.float32)
+        _check(lib().qd_dem_columns(self.h, _ptr(cp), _ptr(cd), _ptr(ob), _ptr(pr), _ptr(ll)))
+        return dict(col_ptr=cp, col_dets=cd[:self.info.n_edges], obs=ob, prob=pr, llr=ll)
+
+    def sample(self, seed, shot_offset, n_shots, det=None, obs=None, stream=None):
+        import torch
+        if det is None:
+            det = torch.empty((n_shots, self.det_words), dtype=torch.int32, device="cuda")
+        if obs is None:
+            obs = torch.empty((n_shots,), dtype=torch.int32, device="cuda")
+        _check(lib().qd_sample_shots(self.h, seed, shot_offset, n_shots, _ptr(det), _ptr(obs),
+                                     _stream(stream)))
+        return det, obs
+
+
+class Decoder:
+    """Sliding-window GDG decoder on the GPU (qd_decoder_create)."""
+
+    def __init__(self, dem, params, max_shots):
+        self.dem, self.params, self.max_shots = dem, dict(params), max_shots
+        h = C.c_void_p()
+        _check(lib().qd_decoder_create(dem.h, C.byref(make_params(params)), max_shots, C.byref(h)))
+        self.h = h
+        n = C.c_int()
+        _check(lib().qd_decoder_n_windows(self.h, C.byref(n)))
+        self.n_windows = n.value
+        _check(lib().qd_decoder_corr_words(self.h, C.byref(n)))
+        self.corr_words = n.value
+        b = C.c_size_t()
+        _check(lib().qd_decoder_trace_bytes(self.h, C.byref(b)))
+        self.trace_bytes = b.value
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.qd_decoder_destroy(self.h)
+            self.h = None
+
+    def window_info(self, k):
+        wi = WindowInfo()
+        _check(lib().qd_window_info(self.h, k, C.byref(wi), None))
+        g = np.zeros(wi.n_cols, np.int32)
+        _check(lib().qd_window_info(self.h, k, C.byref(wi), _ptr(g)))
+        return dict(r0=wi.r0, n_blocks=wi.n_blocks, n_rows=wi.n_rows, n_cols=wi.n_cols,
+                    n_edges=wi.n_edges, n_commit=wi.n_commit, last=bool(wi.is_last),
+                    n_short=wi.n_short, gcols=g)
+
+    def decode_window(self, k, det, n_shots, corr, status=None, trace=None, stream=None):
+        _check(lib().qd_decode_windows(self.h, k, _ptr(det), n_shots, _ptr(corr), _ptr(status),
+                                       _ptr(trace), _stream(stream)))
+
+    def commit(self, k, corr, n_shots, det, obs_pred, resid, stream=None):
+        _check(lib().qd_commit_and_slide(self.h, k, _ptr(corr), n_shots, _ptr(det), _ptr(obs_pred),
+                                         _ptr(resid), _stream(stream)))
+
+    def decode_all(self, det, obs, n_shots, obs_pred, fail, n_fail=None, stream=None):
+        _check(lib().qd_decode_all(self.h, _ptr(det), _ptr(obs), n_shots, _ptr(obs_pred),
+                                   _ptr(fail), _ptr(n_fail), _stream(stream)))
+
+    def decode_host(self, det, obs, stream=None):
+        """Host numpy buffers in and out (qd_decode_shots_host)."""
+        det = np.ascontiguousarray(det, np.uint32)
+        obs = np.ascontiguousarray(obs, np.uint32)
+        n = det.shape[0]
+        pred = np.zeros(n, np.uint32)
+        fail = np.zeros(n, np.uint32)
+        nf = np.zeros(1, np.int64)
+        _check(lib().qd_decode_shots_host(self.h, _ptr(det), _ptr(obs), n, _ptr(pred), _ptr(fail),
+                                          _ptr(nf), _stream(stream)))
+        return pred, fail, int(nf[0])
+
+    def counters(self):
+        out = np.zeros(4, np.int64)
+        _check(lib().qd_decoder_counters(self.h, _ptr(out)))
+        return out
+
+    def reset_counters(self, stream=None):
+        _check(lib().qd_decoder_reset_counters(self.h, _stream(stream)))
+
+    # ---- trace decoding (layout of the per-shot trace buffer) ----
+    def parse_trace(self, buf):
+        """buf: numpy uint8 [trace_bytes] of one shot."""
+        nb = 1 << self.params["k_guess"]
+        dmx = max(self.params["d_max_main"], self.params["d_max_other"])
+        ns_max = self._ns_max()
+        head = np.frombuffer(buf[:16].tobytes(), np.int32)
+        br_dt = np.dtype([("status", "<i4"), ("depth", "<i4"), ("iters", "<i4"), ("pad", "<i4"),
+                          ("pm", "<f8")])
+        st_dt = np.dtype([("g", "<i2"), ("value", "i1"), ("pad", "i1"), ("n_agg", "<i2"),
+                          ("n_peel", "<i2")])
+        o = 16
+        br = np.frombuffer(buf[o:o + 24 * nb].tobytes(), br_dt)
+        o += 24 * nb
+        st = np.frombuffer(buf[o:o + 8 * nb * dmx].tobytes(), st_dt).reshape(nb, dmx)
+        o += 8 * nb * dmx
+        fs = np.frombuffer(buf[o:o + nb * ns_max].tobytes(), np.int8).reshape(nb, ns_max)
+        o = (o + nb * ns_max + 1) & ~1
+        sel = np.frombuffer(buf[o:o + 2 * ns_max].tobytes(), np.uint16)
+        return dict(head=head, branches=br, steps=st, final_status=fs, short_cols=sel)
+
+    def _ns_max(self):
+        return max(self.window_info(k)["n_short"] for k in range(self.n_windows))

@@ -1,0 +1,78 @@
+"""Host-side checks of libqdec (no GPU needed): the library loads, exports
+every entry point include/qdec.h declares, and its detector error model --
+built by a backward sensitivity sweep -- equals the oracle's, which simulates
+every fault directly (Sec. II-B)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT, oracle_dem
+from paper_2403_18901_gb300 import build as qbuild
+from paper_2403_18901_gb300 import qdec
+from paper_2403_18901_gb300.workloads import CODES
+
+
+@pytest.fixture(scope="module")
+def lib():
+    qbuild.build()
+    return qdec.lib()
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "qdec.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qd_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    syms = _declared_symbols()
+    assert len(syms) >= 19
+    raw = ctypes.CDLL(qdec.LIB_PATH)
+    for s in syms:
+        assert hasattr(raw, s), s
+    assert set(syms) == set(qdec._SIGS), "binding and header disagree"
+
+
+def test_invalid_arguments_are_rejected(lib):
+    with pytest.raises(qdec.QdError) as e:
+        qdec.Dem(dict(CODES["72"]), 0.7, 6)
+    assert e.value.code == qdec.QD_EINVAL
+    with pytest.raises(qdec.QdError):
+        qdec.Dem(dict(CODES["72"]), 0.003, 0)
+
+
+@pytest.mark.parametrize("key,R,p", [("72", 6, 0.003), ("144", 12, 0.003), ("90", 4, 0.002),
+                                     ("108", 3, 0.004), ("288", 3, 0.002)])
+def test_dem_equals_oracle(lib, key, R, p):
+    d = qdec.Dem(CODES[key], p, R)
+    o = oracle_dem(key, p, R)
+    c = d.columns()
+    assert d.n_cols == o.n_cols and d.n_det == o.n_det and d.K == o.K
+    assert (c["col_ptr"] == o.col_ptr).all()
+    assert (c["col_dets"] == o.col_dets[:len(c["col_dets"])]).all()
+    assert (c["obs"] == o.col_obs).all()
+    assert (c["prob"] == o.col_p).all()  # bit-identical doubles
+    assert (c["llr"] == o.col_llr).all()
+
+
+def test_every_single_fault_is_a_dem_column(lib):
+    """Fault by fault: the direct Pauli-frame simulation of every single fault
+    (oracle) lands on a column of the library's merged DEM."""
+    d = qdec.Dem(CODES["72"], 0.003, 3)
+    o = oracle_dem("72", 0.003, 3)
+    c = d.columns()
+    cols = set()
+    for i in range(d.n_cols):
+        cols.add((tuple(c["col_dets"][c["col_ptr"][i]:c["col_ptr"][i + 1]].tolist()), int(c["obs"][i])))
+    n = 0
+    for loc in range(o.n_fault_locations()):
+        _, _, info = o.fault_effect(loc, 1)
+        for pat in range(1, info[1] + 1):
+            dets, obs, _ = o.fault_effect(loc, pat)
+            if dets or obs:
+                assert (dets, obs) in cols
+                n += 1
+    assert n > 1000

@@ -1,0 +1,226 @@
+"""GPU parity: the CUDA library against the CPU oracle, through the C ABI.
+
+Plain GDG is bit-exact by construction (FP32 with fixed per-node summation
+order, no FMA, lexicographic argmin ties, one fixed peeling order, exact
+FP64 path metrics), so every comparison below is exact: sampled shots,
+per-window corrections, winning path, per-path status / depth / iterations /
+path metric, the per-step decision log (selected VN, value, aggressive and
+peeled counts), every path's final VN status, the ranked short columns, the
+observable predictions and the failure flags.
+"""
+import numpy as np
+import pytest
+
+from conftest import oracle_dem
+from paper_2403_18901_gb300 import build as qbuild
+from paper_2403_18901_gb300 import qdec
+from paper_2403_18901_gb300.workloads import CODES, preset
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    qbuild.build()
+    qdec.lib()
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def _to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+
+
+def _bits(words, n):
+    idx = np.arange(n)
+    return ((words[..., idx // 32] >> (idx % 32).astype(np.uint32)) & 1).astype(np.uint8)
+
+
+def _apply_commit(det_row, o, win, corr_bits):
+    """Test-side commit (Eq. (10)) with the oracle's DEM columns."""
+    for i in np.nonzero(corr_bits[:win["n_commit"]])[0]:
+        c = win["gcols"][i]
+        for d in o.col_dets[o.col_ptr[c]:o.col_ptr[c + 1]]:
+            det_row[d >> 5] ^= np.uint32(1) << np.uint32(d & 31)
+
+
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("key,R,n,off", [("72", 6, 3000, 0), ("144", 12, 700, 12345)])
+def test_sampler_bit_exact(key, R, n, off):
+    d = qdec.Dem(CODES[key], 0.003, R)
+    o = oracle_dem(key, 0.003, R)
+    det, obs = d.sample(seed=2024, shot_offset=off, n_shots=n)
+    torch.cuda.synchronize()
+    od, oo = o.sample(2024, off, n)
+    assert (_u32(det) == od).all()
+    assert (_u32(obs) == oo).all()
+
+
+def _pipeline(key, R, p, params, n, seed, trace_windows=()):
+    """Run both implementations window by window on the same oracle-sampled
+    shots; compare everything.  Returns (oracle fail, gpu fail)."""
+    o = oracle_dem(key, p, R)
+    d = qdec.Dem(CODES[key], p, R)
+    dec = qdec.Decoder(d, params, max_shots=n)
+    det0, obs0 = o.sample(seed, 0, n)
+    ofail, opred, ocorr = o.run_shots(params, det0, obs0, threads=8, want_corr=True)
+    det = _to_dev(det0)
+    obs = _to_dev(obs0)
+    corr = torch.zeros((n, dec.corr_words), dtype=torch.int32, device="cuda")
+    status = torch.zeros(n, dtype=torch.int32, device="cuda")
+    pred = torch.zeros(n, dtype=torch.int32, device="cuda")
+    resid = torch.zeros(n, dtype=torch.int32, device="cuda")
+    fail = torch.zeros(n, dtype=torch.int32, device="cuda")
+    host_det = det0.copy()
+    for k in range(dec.n_windows):
+        win = dec.window_info(k)
+        owin = o.window(params["W"], params["F"], k)
+        assert (win["gcols"] == owin["gcols"]).all()
+        assert win["n_commit"] == owin["n_commit"]
+        tr = None
+        if k in trace_windows:
+            tr = torch.zeros((n, dec.trace_bytes), dtype=torch.uint8, device="cuda")
+        dec.decode_window(k, det, n, corr, status, tr)
+        g = _u32(corr)
+        cw_o = ocorr.shape[2]
+        if tr is not None:
+            trn = tr.cpu().numpy()
+            st = status.cpu().numpy()
+            s_all = _bits(host_det, o.n_det)
+            n_gdg = 0
+            for sh in range(n):
+                synd = s_all[sh, win["r0"] * o.w: win["r0"] * o.w + win["n_rows"]]
+                oc, oinfo, otr = o.decode_window(params, k, synd, trace=True)
+                gt = dec.parse_trace(trn[sh])
+                assert gt["head"][0] == int(oinfo["prebp_converged"])
+                assert gt["head"][3] == oinfo["prebp_iters"]
+                if oinfo["prebp_converged"]:
+                    assert st[sh] == -1
+                    continue
+                n_gdg += 1
+                ns = oinfo["n_short"]
+                assert gt["head"][1] == oinfo["winner"] and gt["head"][2] == ns
+                assert st[sh] == (oinfo["winner"] if oinfo["winner"] >= 0 else -2)
+                assert (gt["short_cols"][:ns] == otr["short_cols"]).all()
+                for b, ob in enumerate(otr["branches"]):
+                    gb = gt["branches"][b]
+                    assert (gb["status"], gb["depth"], gb["iters"]) == ob[:3], (sh, b)
+                    assert gb["pm"] == ob[3] or (np.isinf(gb["pm"]) and np.isinf(ob[3]))
+                    ost = otr["steps"][b]
+                    for D, rec in enumerate(ost):
+                        grec = gt["steps"][b][D]
+                        assert (grec["g"], grec["value"], grec["n_agg"], grec["n_peel"]) == rec, (sh, b, D)
+                    assert (gt["final_status"][b][:ns] == otr["final_status"][b]).all(), (sh, b)
+            assert n_gdg > 0, "no window ran GDG; pick another seed"
+        assert (g[:, :cw_o] == ocorr[:, k, :]).all(), f"window {k}: corrections differ"
+        dec.commit(k, corr, n, det, pred, resid)
+        gbits = _bits(g, win["n_cols"])
+        for sh in range(n):
+            _apply_commit(host_det[sh], o, owin, gbits[sh])
+    torch.cuda.synchronize()
+    assert (_u32(det) == host_det).all(), "committed syndromes differ"
+    qdec._check(qdec.lib().qd_evaluate(qdec._ptr(pred), qdec._ptr(obs), qdec._ptr(resid), n,
+                                       qdec._ptr(fail), None, qdec._stream(None)))
+    gfail = _u32(fail)
+    assert (_u32(pred) == opred).all()
+    assert (gfail == ofail).all()
+    return ofail, gfail
+
+
+@pytest.mark.parametrize("pname", ["configured", "paper"])
+def test_bb72_pipeline_bit_exact(pname):
+    params = preset(pname, k_guess=3)
+    _pipeline("72", 6, 0.003, params, n=400, seed=72_003, trace_windows=(0, 2, 4))
+
+
+def test_bb72_low_error_mode_and_k0():
+    params = preset("paper", k_guess=0, p=0.002)
+    assert params["low_error_mode"] == 1
+    _pipeline("72", 6, 0.002, params, n=300, seed=72_002, trace_windows=(1,))
+    params = preset("configured", k_guess=2, low_error_mode=1, peel_at_init=0)
+    _pipeline("72", 6, 0.003, params, n=200, seed=72_004, trace_windows=(3,))
+
+
+def test_bb144_pipeline_bit_exact():
+    params = preset("configured", k_guess=4)
+    _pipeline("144", 12, 0.003, params, n=150, seed=144_003, trace_windows=(0, 5, 10))
+
+
+def test_bb144_paper_preset_k5_bit_exact():
+    params = preset("paper", k_guess=5)
+    _pipeline("144", 12, 0.004, params, n=60, seed=144_004, trace_windows=tuple(range(11)))
+
+
+def test_other_window_shapes():
+    # (4,2) windows on [[90]] and a single global window on [[72]]
+    _pipeline("90", 4, 0.003, preset("paper", k_guess=2, W=4, F=2), n=60, seed=90_003,
+              trace_windows=(0,))
+    _pipeline("72", 3, 0.003, preset("paper", k_guess=1, W=4, F=1), n=60, seed=72_005,
+              trace_windows=(0,))
+
+
+def test_host_buffer_path_equals_device_path():
+    params = preset("configured", k_guess=3)
+    o = oracle_dem("72", 0.003, 6)
+    d = qdec.Dem(CODES["72"], 0.003, 6)
+    n = 257  # ragged batch
+    dec = qdec.Decoder(d, params, max_shots=512)
+    det0, obs0 = o.sample(99, 0, n)
+    ofail, opred, _ = o.run_shots(params, det0, obs0, threads=8)
+    pred, fail, nf = dec.decode_host(det0, obs0)
+    assert (pred == opred).all() and (fail == ofail).all()
+    assert nf == int((ofail > 0).sum())
+    # device path with the library's own scratch
+    det = _to_dev(det0)
+    obs = _to_dev(obs0)
+    pr = torch.zeros(n, dtype=torch.int32, device="cuda")
+    fl = torch.zeros(n, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    dec.decode_all(det, obs, n, pr, fl, cnt)
+    torch.cuda.synchronize()
+    assert (_u32(pr) == opred).all() and (_u32(fl) == ofail).all()
+    assert int(cnt.item()) == nf
+
+
+def test_edge_cases():
+    params = preset("configured", k_guess=3)
+    d = qdec.Dem(CODES["72"], 0.003, 6)
+    dec = qdec.Decoder(d, params, max_shots=64)
+    # empty batch is a no-op
+    pred, fail, nf = dec.decode_host(np.zeros((0, d.det_words), np.uint32), np.zeros(0, np.uint32))
+    assert len(pred) == 0 and nf == 0
+    # all-zero syndromes: zero corrections, no failures
+    det = np.zeros((64, d.det_words), np.uint32)
+    pred, fail, nf = dec.decode_host(det, np.zeros(64, np.uint32))
+    assert (pred == 0).all() and (fail == 0).all() and nf == 0
+    # one shot
+    o = oracle_dem("72", 0.003, 6)
+    det1, obs1 = o.sample(5, 7, 1)
+    ofail, opred, _ = o.run_shots(params, det1, obs1)
+    pred, fail, _ = dec.decode_host(det1, obs1)
+    assert (pred == opred).all() and (fail == ofail).all()
+    # batch above max_shots is refused
+    with pytest.raises(qdec.QdError) as e:
+        dec.decode_host(np.zeros((65, d.det_words), np.uint32), np.zeros(65, np.uint32))
+    assert e.value.code == qdec.QD_EINVAL
+    # unsupported parameters are refused at create time
+    with pytest.raises(qdec.QdError) as e:
+        qdec.Decoder(d, dict(params, iters_per_step=3), 8)
+    assert e.value.code == qdec.QD_EUNSUPPORTED
+
+
+def test_repeatable():
+    """Same inputs twice -> identical outputs (no races in the peel / argmin)."""
+    params = preset("configured", k_guess=4)
+    o = oracle_dem("144", 0.003, 12)
+    d = qdec.Dem(CODES["144"], 0.003, 12)
+    dec = qdec.Decoder(d, params, max_shots=300)
+    det0, obs0 = o.sample(31337, 0, 300)
+    a = dec.decode_host(det0, obs0)
+    b = dec.decode_host(det0, obs0)
+    assert (a[0] == b[0]).all() and (a[1] == b[1]).all()
