@@ -220,6 +220,37 @@ qd_status qd_decode_shots_host(qd_decoder* dec, const uint32_t* det_bits, const 
                                int64_t n_shots, uint32_t* obs_pred, uint32_t* fail,
                                long long* n_fail, qd_stream_t stream);
 
+/*
+ * Decode window k and commit it without any device allocation, for callers
+ * that cannot call cudaMalloc between decoder set-up and the end of the run:
+ * a real-time decoding loop in which an allocation (or the device-wide
+ * synchronisation cudaFree implies) would stall the stream, or a host
+ * framework that owns all device memory and forbids the runtime allocator.
+ * The paper has no counterpart; this is a packaging of qd_decode_windows
+ * followed by qd_commit_and_slide.
+ *
+ * The window corrections and the work counter, which qd_decode_windows keeps
+ * in caller or decoder buffers, live in one fixed array of
+ * QD_STATIC_SCRATCH_BYTES compiled into the library (every GPU that loads it
+ * holds that memory until the process exits).  Limit: n_shots * corr_words * 4
+ * + 256 <= QD_STATIC_SCRATCH_BYTES (30839 shots for [[144,12,12]] with
+ * (3,1) windows, 68 correction words per shot); larger batches return QD_EINVAL with the limit in the
+ * message.
+ *   det_bits     device [n_shots][det_words], updated in place (Eq. (10))
+ *   obs_pred     device [n_shots], updated in place
+ *   residue_fail device [n_shots], updated in place (Eq. (11))
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array and it keeps the previous call's
+ * contents: two calls whose work can overlap on the same GPU (for example
+ * calls on two different streams, or on two decoders) race with each other;
+ * issue them on one stream per device.  Allocates nothing and makes no
+ * allocating library call.
+ */
+#define QD_STATIC_SCRATCH_BYTES (8u << 20)
+qd_status qd_decode_commit_static(qd_decoder* dec, int k, uint32_t* det_bits, int64_t n_shots,
+                                  uint32_t* obs_pred, uint32_t* residue_fail, qd_stream_t stream);
+
 /* Counters of the last qd_decode_windows call of window k, summed over shots:
  * out[0] pre-BP edge-iterations, out[1] GDG edge-iterations, out[2] windows
  * whose pre-BP converged, out[3] windows that ran GDG.  Synchronous. */

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -416,3 +417,71 @@ qd_status qd_decoder_reset_counters(qd_decoder* dec, qd_stream_t stream) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free decode + commit (qd_decode_commit_static).
+//
+// The per-shot window corrections and the work-queue counter that
+// qd_decode_windows / qd_commit_and_slide keep in decoder-owned or
+// caller-owned device buffers live here in one fixed array that is part of
+// the library image.  Every GPU that loads the library holds these
+// QD_STATIC_SCRATCH_BYTES until the process exits.
+namespace {
+constexpr size_t kStaticScratchBytes = QD_STATIC_SCRATCH_BYTES;
+constexpr size_t kStaticHeader = 256;  // work counter + statistics, before the corrections
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void* g_static_addr[256] = {};  // device address of g_static_scratch, per device ordinal
+
+// The array's name in host code is only a host-side stand-in; the device
+// address must come from the runtime, once per device, with that device current.
+qd_status static_scratch_address(void** out) {
+  int dev = 0;
+  QD_CK(cudaGetDevice(&dev));
+  QD_REQ(dev >= 0 && dev < 256, "qd_decode_commit_static: device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    QD_CK(cudaGetSymbolAddress(&p, g_static_scratch));
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return QD_OK;
+}
+}  // namespace
+
+extern "C" qd_status qd_decode_commit_static(qd_decoder* dec, int k, uint32_t* det_bits, int64_t n_shots,
+                                             uint32_t* obs_pred, uint32_t* residue_fail,
+                                             qd_stream_t stream) {
+  QD_REQ(dec && det_bits && obs_pred && residue_fail, "qd_decode_commit_static: null argument");
+  QD_REQ(k >= 0 && k < (int)dec->wins.size(), "qd_decode_commit_static: window out of range");
+  QD_REQ(n_shots >= 0, "qd_decode_commit_static: n_shots < 0");
+  const size_t need = kStaticHeader + sizeof(uint32_t) * (size_t)n_shots * dec->corr_words;
+  if (need > kStaticScratchBytes) {
+    set_error("qd_decode_commit_static: " + std::to_string(n_shots) + " shots need " +
+              std::to_string(need) + " B of static scratch, more than the library's fixed " +
+              std::to_string(kStaticScratchBytes) + " B; use at most " +
+              std::to_string((kStaticScratchBytes - kStaticHeader) / (sizeof(uint32_t) * dec->corr_words)) +
+              " shots per call");
+    return QD_EINVAL;
+  }
+  if (n_shots == 0) return QD_OK;
+  void* base = nullptr;
+  if (qd_status st = static_scratch_address(&base)) return st;
+  int* work = (int*)base;
+  long long* stats = (long long*)((char*)base + 64);
+  uint32_t* corr = (uint32_t*)((char*)base + kStaticHeader);
+  const WinGpu& g = dec->wins[k];
+  cudaStream_t st = (cudaStream_t)stream;
+  // the array keeps the previous call's contents: the counters must restart at 0
+  QD_CK(cudaMemsetAsync(base, 0, kStaticHeader, st));
+  long long grid = std::min<long long>(n_shots, (long long)dec->sm_count * g.grid_per_sm);
+  const int dw = (dec->dem->h.n_det + 31) / 32;
+  QD_CK(qd::launch_decode((int)grid, g.threads, g.L.total, st, dec->kp, g.dv, g.L, det_bits, dw, n_shots,
+                          corr, dec->corr_words, nullptr, nullptr, 0, dec->dmx, dec->ns_max, work, stats));
+  const int w = dec->dem->h.w;
+  QD_CK(qd::launch_commit(st, g.h.n_commit, g.d_ccptr, g.d_ccdet, g.d_ccobs, dec->corr_words, corr, n_shots,
+                          det_bits, dw, obs_pred, residue_fail, g.h.r0 * w, g.h.commit_b1 * w));
+  return QD_OK;
+}

@@ -72,6 +72,7 @@ _SIGS = {
     "qd_evaluate": (_I, [_VP, _VP, _VP, _I64, _VP, _VP, _VP]),
     "qd_decode_all": (_I, [_VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP]),
     "qd_decode_shots_host": (_I, [_VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP]),
+    "qd_decode_commit_static": (_I, [_VP, _I, _VP, _I64, _VP, _VP, _VP]),
     "qd_decoder_counters": (_I, [_VP, _VP]),
     "qd_decoder_reset_counters": (_I, [_VP, _VP]),
 }
@@ -210,6 +211,12 @@ class Decoder:
     def commit(self, k, corr, n_shots, det, obs_pred, resid, stream=None):
         _check(lib().qd_commit_and_slide(self.h, k, _ptr(corr), n_shots, _ptr(det), _ptr(obs_pred),
                                          _ptr(resid), _stream(stream)))
+
+    def decode_commit_static(self, k, det, n_shots, obs_pred, resid, stream=None):
+        """Decode + commit window k using the library's fixed scratch array
+        (no device allocation; see qd_decode_commit_static)."""
+        _check(lib().qd_decode_commit_static(self.h, k, _ptr(det), n_shots, _ptr(obs_pred),
+                                             _ptr(resid), _stream(stream)))
 
     def decode_all(self, det, obs, n_shots, obs_pred, fail, n_fail=None, stream=None):
         _check(lib().qd_decode_all(self.h, _ptr(det), _ptr(obs), n_shots, _ptr(obs_pred),
