@@ -251,6 +251,13 @@ qd_status qd_decode_shots_host(qd_decoder* dec, const uint32_t* det_bits, const 
 qd_status qd_decode_commit_static(qd_decoder* dec, int k, uint32_t* det_bits, int64_t n_shots,
                                   uint32_t* obs_pred, uint32_t* residue_fail, qd_stream_t stream);
 
+/* Launch shape of qd_decode_windows (results are identical in every shape):
+ * 0 automatic (default): path mode for batches that leave most SMs idle,
+ * otherwise shot mode; 1 shot mode: persistent CTAs, one warp per decision
+ * path; 2 path mode: one CTA per (shot, decision path) for the lowest
+ * latency, at most 64 shots per call (larger batches fall back to shot mode). */
+qd_status qd_decoder_set_launch(qd_decoder* dec, int mode);
+
 /* Counters of the last qd_decode_windows call of window k, summed over shots:
  * out[0] pre-BP edge-iterations, out[1] GDG edge-iterations, out[2] windows
  * whose pre-BP converged, out[3] windows that ran GDG.  Synchronous. */

@@ -346,13 +346,10 @@ bool build_window(const DemHost& d, int W, int F, int k, bool shorten, WindowHos
   for (uint16_t r : o.col_rows) o.row_ptr[r + 1]++;
   for (int j = 0; j < o.n_rows; ++j) o.row_ptr[j + 1] += o.row_ptr[j];
   std::vector<int> fill(o.row_ptr.begin(), o.row_ptr.end() - 1);
-  o.row_edges.assign(o.n_edges, 0);
-  o.edge_col.assign(o.n_edges, 0);
+  o.row_ent.assign(o.n_edges, 0);
   for (int c = 0; c < o.n_cols; ++c)
-    for (int e = o.col_ptr[c]; e < o.col_ptr[c + 1]; ++e) {
-      o.edge_col[e] = (uint16_t)c;
-      o.row_edges[fill[o.col_rows[e]]++] = (uint16_t)e;
-    }
+    for (int e = o.col_ptr[c]; e < o.col_ptr[c + 1]; ++e)
+      o.row_ent[fill[o.col_rows[e]]++] = (uint32_t)e | ((uint32_t)c << 16);
   o.n_short = (shorten && o.n_cols > 2 * o.n_rows) ? 2 * o.n_rows : o.n_cols;
   std::vector<int> deg(o.n_cols);
   for (int c = 0; c < o.n_cols; ++c) deg[c] = o.col_ptr[c + 1] - o.col_ptr[c];

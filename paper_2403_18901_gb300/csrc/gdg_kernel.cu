@@ -1,6 +1,6 @@
 // gdg_kernel.cu -- the window decoder, sampler, commit and evaluation kernels.
 //
-// decode (one persistent launch per window step; CTA = one shot at a time):
+// decode, per shot:
 //   a1  window syndrome: bits [row0, row0 + n_rows) of the shot's detectors
 //   a2  pre-BP: n_pre flooding min-sum iterations on the full window
 //       (Eq. (1)-(4)), whole CTA; check node j by one warp, variable node i
@@ -8,13 +8,22 @@
 //   a3  ranking key ((h0+h1)+h2)+h3 of the last four posteriors, bitonic sort
 //       of (key, column) ascending, first 2w' columns kept (Sec. III); the
 //       shortened matrix is rebuilt in shared memory
-//   a4-a7 GDG: warp w runs decision paths w, w+NW, ... (Alg. 2 on the 2^k
-//       tree): BP steps of iters_per_step iterations, SELECT-VN (Alg. 1) with
-//       aggressive decimation (Alg. 3), guess value by the path id, peeling
+//   a4-a7 GDG decision paths (Alg. 2 on the 2^k tree): BP steps of
+//       iters_per_step iterations, SELECT-VN (Alg. 1) with aggressive
+//       decimation (Alg. 3), guess value by the path id, peeling
 //   a8  minimum path metric Eq. (5) over converged paths, ties to the lowest id
-// Every wait is a __syncthreads/__syncwarp of this CTA; nothing spins.
+//
+// Two launch shapes run the same path code:
+//   shot mode (throughput): persistent CTAs of 8 warps take shots from a work
+//     counter; after the CTA-wide pre-BP the warps take decision paths from a
+//     shared-memory queue, path 0 (the longest, D_max 25) first, one warp per
+//     path;
+//   path mode (latency, small batches): one CTA per (shot, path); every CTA
+//     repeats the cheap pre-BP and ranking, runs its one path with all its
+//     threads, stores the result in global scratch, and the last CTA of the
+//     shot to arrive (atomic counter, no waiting) picks the winner.
+// Every wait is a CTA or warp barrier; nothing spins.
 #include <cuda_runtime.h>
-
 #include <math_constants.h>
 
 #include <cfloat>
@@ -27,16 +36,16 @@ namespace dev {
 
 constexpr unsigned FULL = 0xffffffffu;
 enum { BR_CONVERGED = 0, BR_MAXDEPTH = 1, BR_CONTRADICTION = 2, BR_NOCAND = 3, BR_INTERNAL = 4 };
+constexpr int kNone = 0x7fffffff;
 
 __device__ __forceinline__ float clipf(float x, float c) { return x > c ? c : (x < -c ? -c : x); }
 
 // mu_{j->i} from the check's compressed state (see gdg_kernel.cuh).
-__device__ __forceinline__ float c2v_msg(float alpha, float clip, float m1, float m2, uint16_t am,
-                                         uint8_t cfl, int e, uint8_t sg) {
-  float m = ((uint16_t)e == am) ? m2 : m1;
-  if (cfl & 2) m = clip;  // single active VN: minimum over the empty set = clip
-  float mag = __fmul_rn(alpha, m);
-  return (((cfl & 1u) ^ sg) != 0) ? -mag : mag;
+__device__ __forceinline__ float c2v_msg(float alpha, float clip, const CNState& c, int e, uint32_t sg) {
+  float m = ((c.ac & 0xFFFFu) == (uint32_t)e) ? c.m2 : c.m1;
+  if (c.ac & (2u << 16)) m = clip;  // single active VN: minimum over the empty set = clip
+  const float mag = __fmul_rn(alpha, m);
+  return ((((c.ac >> 16) & 1u) ^ sg) != 0) ? -mag : mag;
 }
 
 __device__ __forceinline__ uint32_t bit_of(const uint32_t* w, int j) { return (w[j >> 5] >> (j & 31)) & 1u; }
@@ -44,16 +53,16 @@ __device__ __forceinline__ uint32_t bit_of(const uint32_t* w, int j) { return (w
 // order-preserving map of a float to uint32 (-0 and +0 equal)
 __device__ __forceinline__ uint32_t ordkey(float f) {
   if (f == 0.0f) f = 0.0f;
-  uint32_t u = __float_as_uint(f);
+  const uint32_t u = __float_as_uint(f);
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
 __device__ __forceinline__ void warp_min2(float& m1, float& m2, int& am) {
 #pragma unroll
   for (int off = 16; off; off >>= 1) {
-    float x1 = __shfl_xor_sync(FULL, m1, off);
-    float x2 = __shfl_xor_sync(FULL, m2, off);
-    int xa = __shfl_xor_sync(FULL, am, off);
+    const float x1 = __shfl_xor_sync(FULL, m1, off);
+    const float x2 = __shfl_xor_sync(FULL, m2, off);
+    const int xa = __shfl_xor_sync(FULL, am, off);
     if (x1 < m1 || (x1 == m1 && xa < am)) {
       m2 = fminf(m1, x2);
       m1 = x1;
@@ -64,12 +73,36 @@ __device__ __forceinline__ void warp_min2(float& m1, float& m2, int& am) {
   }
 }
 
+// (min1, min2, argmin) and sign parity over aligned groups of tpc lanes
+// (tpc a power of two <= 32); every lane of a group ends with the result.
+__device__ __forceinline__ void group_min2(float& m1, float& m2, int& am, uint32_t& neg, int tpc) {
+  for (int off = tpc >> 1; off; off >>= 1) {
+    const float x1 = __shfl_xor_sync(FULL, m1, off);
+    const float x2 = __shfl_xor_sync(FULL, m2, off);
+    const int xa = __shfl_xor_sync(FULL, am, off);
+    neg ^= __shfl_xor_sync(FULL, neg, off);
+    if (x1 < m1 || (x1 == m1 && xa < am)) {
+      m2 = fminf(m1, x2);
+      m1 = x1;
+      am = xa;
+    } else {
+      m2 = fminf(m2, x1);
+    }
+  }
+}
+
+__host__ __device__ inline int lanes_per_check(int threads, int n_checks) {
+  int t = 1;
+  while (t < 8 && 2 * t * n_checks <= threads) t <<= 1;
+  return t;
+}
+
 // lexicographic (value, index) minimum over the warp
 __device__ __forceinline__ void warp_argmin(float& v, int& k) {
 #pragma unroll
   for (int off = 16; off; off >>= 1) {
-    float xv = __shfl_xor_sync(FULL, v, off);
-    int xk = __shfl_xor_sync(FULL, k, off);
+    const float xv = __shfl_xor_sync(FULL, v, off);
+    const int xk = __shfl_xor_sync(FULL, k, off);
     if (xv < v || (xv == v && xk < k)) {
       v = xv;
       k = xk;
@@ -79,49 +112,161 @@ __device__ __forceinline__ void warp_argmin(float& v, int& k) {
 
 // Exclusive scan of a[0..n) in place, by one warp; returns the total.
 __device__ int warp_scan_excl(int* a, int n, int lane) {
-  int chunk = (n + 31) / 32;
-  int beg = lane * chunk, end = min(n, beg + chunk);
+  const int chunk = (n + 31) / 32;
+  const int beg = lane * chunk, end = min(n, beg + chunk);
   int s = 0;
   for (int i = beg; i < end; ++i) s += a[i];
   int incl = s;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
-    int y = __shfl_up_sync(FULL, incl, off);
+    const int y = __shfl_up_sync(FULL, incl, off);
     if (lane >= off) incl += y;
   }
   int run = incl - s;
   for (int i = beg; i < end; ++i) {
-    int v = a[i];
+    const int v = a[i];
     a[i] = run;
     run += v;
   }
   return __shfl_sync(FULL, incl, 31);
 }
 
+// ---- cooperative groups of threads that run one decision path ----
+struct WarpGrp {  // one warp
+  int rank;
+  static constexpr int size = 32;
+  __device__ void sync() const { __syncwarp(); }
+  __device__ bool all(bool p) const { return __all_sync(FULL, p); }
+  __device__ bool any(bool p) const { return __any_sync(FULL, p); }
+  __device__ unsigned min_u(unsigned v) const { return __reduce_min_sync(FULL, v); }
+  __device__ int sum_i(int v) const { return (int)__reduce_add_sync(FULL, (unsigned)v); }
+  __device__ long long sum_ll(long long v) const {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    return v;
+  }
+  __device__ double sum_d(double v) const {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    return v;
+  }
+  __device__ void argmin(float& v, int& k) const { warp_argmin(v, k); }
+};
+
+struct CtaGrp {  // the whole CTA; every member must call every primitive
+  int rank, size;
+  char* red;  // >= 32 * 16 bytes of shared memory
+  __device__ void sync() const { __syncthreads(); }
+  __device__ bool all(bool p) const { return __syncthreads_and(p) != 0; }
+  __device__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
+  __device__ unsigned min_u(unsigned v) const {
+    v = __reduce_min_sync(FULL, v);
+    unsigned* r = (unsigned*)red;
+    __syncthreads();
+    if ((rank & 31) == 0) r[rank >> 5] = v;
+    __syncthreads();
+    unsigned m = r[0];
+    for (int i = 1; i < (size >> 5); ++i) m = min(m, r[i]);
+    return m;
+  }
+  __device__ int sum_i(int v) const {
+    v = (int)__reduce_add_sync(FULL, (unsigned)v);
+    int* r = (int*)red;
+    __syncthreads();
+    if ((rank & 31) == 0) r[rank >> 5] = v;
+    __syncthreads();
+    int s = 0;
+    for (int i = 0; i < (size >> 5); ++i) s += r[i];
+    return s;
+  }
+  __device__ long long sum_ll(long long v) const {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    long long* r = (long long*)red;
+    __syncthreads();
+    if ((rank & 31) == 0) r[rank >> 5] = v;
+    __syncthreads();
+    long long s = 0;
+    for (int i = 0; i < (size >> 5); ++i) s += r[i];
+    return s;
+  }
+  __device__ double sum_d(double v) const {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    double* r = (double*)red;
+    __syncthreads();
+    if ((rank & 31) == 0) r[rank >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int i = 0; i < (size >> 5); ++i) s += r[i];
+    return s;
+  }
+  __device__ void argmin(float& v, int& k) const {
+    warp_argmin(v, k);
+    float* rv = (float*)red;
+    int* rk = (int*)(red + 4 * 32);
+    __syncthreads();
+    if ((rank & 31) == 0) {
+      rv[rank >> 5] = v;
+      rk[rank >> 5] = k;
+    }
+    __syncthreads();
+    v = rv[0];
+    k = rk[0];
+    for (int i = 1; i < (size >> 5); ++i)
+      if (rv[i] < v || (rv[i] == v && rk[i] < k)) {
+        v = rv[i];
+        k = rk[i];
+      }
+  }
+};
+
 struct ShortG {
   int nr, ns, rw;
-  const uint16_t *colptr, *colrows, *rowptr, *rowedges, *edgecol;
+  const uint16_t *colptr, *colrows, *rowptr;
+  const uint32_t* rowent;  // CSR entry: edge id | (short column << 16)
   const float* llr;
   const uint8_t* vdeg;
   const uint32_t* sbits;
 };
 
-struct BrPtr {
+struct Slot {
   float *post, *acc;
-  uint8_t *hfl, *sign, *cfl;
+  uint8_t *hfl, *sign;
   int8_t* status;
-  float *min1, *min2;
-  uint16_t* amin;
+  CNState* cns;
   int* deg;
   uint32_t *sp, *par, *unsat;
 };
 
-__device__ __forceinline__ void decimate_atomic(const ShortG& G, const BrPtr& B, int k, int v) {
+__device__ __forceinline__ Slot make_slot(char* base, const Layout& L) {
+  return Slot{(float*)(base + L.b_post),   (float*)(base + L.b_acc),     (uint8_t*)(base + L.b_hfl),
+              (uint8_t*)(base + L.b_sign), (int8_t*)(base + L.b_status), (CNState*)(base + L.b_cns),
+              (int*)(base + L.b_deg),      (uint32_t*)(base + L.b_sp),   (uint32_t*)(base + L.b_par),
+              (uint32_t*)(base + L.b_unsat)};
+}
+
+// Posterior of a decimated VN: a NaN, so the check-node pass recognises a
+// stale edge from the posterior it loads anyway.
+__device__ __forceinline__ float stale() { return __int_as_float(0x7fffffff); }
+
+__device__ __forceinline__ void decimate_atomic(const ShortG& G, const Slot& B, int k, int v) {
   B.status[k] = (int8_t)v;
+  B.post[k] = stale();
   for (int e = G.colptr[k]; e < G.colptr[k + 1]; ++e) {
-    int j = G.colrows[e];
+    const int j = G.colrows[e];
     atomicSub(&B.deg[j], 1);
     if (v) atomicXor(&B.sp[j >> 5], 1u << (j & 31));
+  }
+}
+
+__device__ __forceinline__ void decimate_one(const ShortG& G, const Slot& B, int k, int v) {
+  B.status[k] = (int8_t)v;
+  B.post[k] = stale();
+  for (int e = G.colptr[k]; e < G.colptr[k + 1]; ++e) {
+    const int r = G.colrows[e];
+    B.deg[r] -= 1;
+    if (v) B.sp[r >> 5] ^= 1u << (r & 31);
   }
 }
 
@@ -130,69 +275,76 @@ __device__ __forceinline__ void decimate_atomic(const ShortG& G, const BrPtr& B,
 // syndrome 1 is a contradiction.  One check at a time, always the lowest-index
 // degree-one check, after testing every check for a contradiction (this order
 // also fixes the partial state of a path killed by a contradiction).
-// Returns #peeled or -1 (contradiction), -2 on an inconsistent degree count
-// (internal error).
-__device__ int peel(const ShortG& G, const BrPtr& B, int lane) {
+// Returns #peeled, -1 (contradiction) or -2 (inconsistent degree count).
+template <class Grp>
+__device__ int peel(const ShortG& G, const Slot& B, const Grp& g) {
   int npeel = 0;
   for (int guard = 0; guard <= G.ns + 1; ++guard) {
     bool contra = false;
-    int cand = 0x7fffffff;
-    for (int j = lane; j < G.nr; j += 32) {
-      int d = B.deg[j];
+    int cand = kNone;
+    for (int j = g.rank; j < G.nr; j += g.size) {
+      const int d = B.deg[j];
       if (d == 0) {
         if (bit_of(B.sp, j)) contra = true;
-      } else if (d == 1 && cand == 0x7fffffff) {
+      } else if (d == 1 && cand == kNone) {
         cand = j;
       }
     }
-    if (__any_sync(FULL, contra)) return -1;
-    const int j = (int)__reduce_min_sync(FULL, (unsigned)cand);
-    if (j == 0x7fffffff) return npeel;
-    int found = -1;
-    for (int q = G.rowptr[j] + lane; q < G.rowptr[j + 1]; q += 32) {
-      int i = G.edgecol[G.rowedges[q]];
+    if (g.any(contra)) return -1;
+    const int j = (int)g.min_u((unsigned)cand);
+    if (j == kNone) return npeel;
+    int found = kNone;
+    for (int q = G.rowptr[j] + g.rank; q < G.rowptr[j + 1]; q += g.size) {
+      const int i = (int)(G.rowent[q] >> 16);
       if (B.status[i] == -1) found = i;
     }
-    unsigned fm = __ballot_sync(FULL, found >= 0);
-    if (!fm) return -2;
-    int i = __shfl_sync(FULL, found, __ffs(fm) - 1);
-    int v = (int)bit_of(B.sp, j);
-    __syncwarp();
-    if (lane == 0) {
-      B.status[i] = (int8_t)v;
-      for (int e = G.colptr[i]; e < G.colptr[i + 1]; ++e) {
-        int r = G.colrows[e];
-        B.deg[r] -= 1;
-        if (v) B.sp[r >> 5] ^= 1u << (r & 31);
-      }
-    }
-    __syncwarp();
+    const int i = (int)g.min_u((unsigned)found);
+    if (i == kNone) return -2;
+    const int v = (int)bit_of(B.sp, j);
+    g.sync();
+    if (g.rank == 0) decimate_one(G, B, i, v);
+    g.sync();
     ++npeel;
   }
   return -2;
 }
 
-// One decision path of Alg. 2 on the shortened window, run by one warp.
-__device__ void run_branch(const KParams& P, const ShortG& G, const BrPtr& B, int id, int lane,
-                           int* out_status, double* out_pm, uint32_t* out_ebits, BranchTrace* btr,
-                           StepTrace* st, int dmx, int8_t* fstat, long long* edge_visits) {
-  const int nr = G.nr, ns = G.ns, rw = G.rw;
+struct PathOut {
+  int* status;
+  double* pm;
+  uint32_t* ebits;
+  BranchTrace* btr;
+  StepTrace* st;
+  int8_t* fstat;
+  long long* visits;  // accumulates active edge visits
+};
+
+// One decision path of Alg. 2 on the shortened window, run by group g.
+template <class Grp>
+__device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int id, const Grp& g,
+                         const PathOut& out, int dmx) {
+  const int nr = G.nr, ns = G.ns, rw = G.rw, R = g.rank, S = g.size;
+  const int tpc = lanes_per_check(S, nr), sub = R & (tpc - 1);
+  const int nr_rounds = (nr + S / tpc - 1) / (S / tpc) * (S / tpc);
   const bool mainb = (id == 0);
   const int dmax = mainb ? P.dmax_main : P.dmax_other;
   const float PA = mainb ? P.pa_main : P.pa_other;
-  float PB = mainb ? P.pb_main : P.pb_other;
-  for (int k = lane; k < ns; k += 32) B.status[k] = -1;
-  for (int j = lane; j < nr; j += 32) B.deg[j] = G.rowptr[j + 1] - G.rowptr[j];
-  for (int x = lane; x < rw; x += 32) B.sp[x] = G.sbits[x];
-  if (st)
-    for (int q = lane; q < dmx; q += 32) st[q] = StepTrace{-2, -1, 0, 0, 0};
-  __syncwarp();
+  const float PB = mainb ? P.pb_main : P.pb_other;
+  for (int k = R; k < ns; k += S) {
+    B.status[k] = -1;
+    B.post[k] = G.llr[k];  // t = 0: mu_{i->j} = Lambda_i (Sec. II-A)
+  }
+  for (int j = R; j < nr; j += S) B.deg[j] = G.rowptr[j + 1] - G.rowptr[j];
+  for (int x = R; x < rw; x += S) B.sp[x] = G.sbits[x];
+  if (out.st)
+    for (int q = R; q < dmx; q += S) out.st[q] = StepTrace{-2, -1, 0, 0, 0};
+  g.sync();
   int status = BR_MAXDEPTH, depth = 0, iters = 0;
-  long long visits = 0;  // active edges touched by the check-node passes
+  long long visits = 0;
   double pm = CUDART_INF;
   bool first = true;
   if (P.peel_init) {
-    int np = peel(G, B, lane);
+    const int np = peel(G, B, g);
     if (np < 0) {
       status = np == -1 ? BR_CONTRADICTION : BR_INTERNAL;
       goto done;
@@ -202,60 +354,72 @@ __device__ void run_branch(const KParams& P, const ShortG& G, const BrPtr& B, in
     depth = D;
     for (int it = 1; it <= P.ips; ++it) {
       uint32_t* par = B.par + (iters & 1) * rw;
-      for (int x = lane; x < rw; x += 32) par[x] = 0;
-      // ---- check-node update, Eq. (1), over active VNs ----
-      for (int j = lane; j < nr; j += 32) {
-        const int d = B.deg[j];
-        if (d == 0) continue;
-        const float om1 = B.min1[j], om2 = B.min2[j];
-        const uint16_t oam = B.amin[j];
-        const uint8_t ocfl = B.cfl[j];
-        float m1 = FLT_MAX * 2.0f, m2 = FLT_MAX * 2.0f;
+      for (int x = R; x < rw; x += S) par[x] = 0;
+      // ---- check-node update, Eq. (1), over active VNs; tpc lanes per check ----
+      for (int j0 = R / tpc; j0 < nr_rounds; j0 += S / tpc) {
+        const int j = j0 < nr ? j0 : nr - 1;
+        const int d = j0 < nr ? B.deg[j] : 0;
+        if (tpc == 1 && d == 0) continue;  // no shuffle partner waits for this lane
+        const CNState oc = B.cns[j];
+        float m1 = CUDART_INF_F, m2 = CUDART_INF_F;
         int am = 0xFFFF;
-        unsigned neg = 0;
-        const int qe = G.rowptr[j + 1];
-        for (int q = G.rowptr[j]; q < qe; ++q) {
-          const int e = G.rowedges[q];
-          const int i = G.edgecol[e];
-          if (B.status[i] != -1) continue;  // stale message of a decimated VN
-          ++visits;
-          float v = first ? G.llr[i]
-                          : clipf(__fsub_rn(B.post[i], c2v_msg(P.alpha, P.clip, om1, om2, oam, ocfl,
-                                                              e, B.sign[e])),
-                                  P.clip);
-          float a = fabsf(v);
-          if (a < m1) {
-            m2 = m1;
-            m1 = a;
-            am = e;
-          } else if (a < m2) {
-            m2 = a;
+        uint32_t neg = 0;
+        const int qe = d ? G.rowptr[j + 1] : 0;
+        for (int q = (d ? G.rowptr[j] : 0) + 4 * sub; q < qe; q += 4 * tpc) {
+          uint32_t ent[4];
+          float pv[4];
+          uint32_t sg[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) ent[u] = (q + u < qe) ? G.rowent[q + u] : 0u;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            pv[u] = B.post[ent[u] >> 16];
+            sg[u] = B.sign[ent[u] & 0xFFFFu];
           }
-          unsigned s = v < 0.0f;
-          neg ^= s;
-          B.sign[e] = (uint8_t)s;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (q + u >= qe) break;
+            if (pv[u] != pv[u]) continue;  // stale message of a decimated VN
+            const int e = (int)(ent[u] & 0xFFFFu);
+            ++visits;
+            const float v = first ? pv[u] : clipf(__fsub_rn(pv[u], c2v_msg(P.alpha, P.clip, oc, e, sg[u])), P.clip);
+            const float a = fabsf(v);
+            if (a < m1) {
+              m2 = m1;
+              m1 = a;
+              am = e;
+            } else if (a < m2) {
+              m2 = a;
+            }
+            const uint32_t sgn = v < 0.0f;
+            neg ^= sgn;
+            B.sign[e] = (uint8_t)sgn;
+          }
         }
-        B.min1[j] = m1;
-        B.min2[j] = m2;
-        B.amin[j] = (uint16_t)am;
-        B.cfl[j] = (uint8_t)((neg ^ bit_of(B.sp, j)) | ((d == 1) << 1));
+        if (tpc > 1) group_min2(m1, m2, am, neg, tpc);
+        if (sub == 0 && d > 0)
+          B.cns[j] = CNState{m1, m2, (uint32_t)am | ((neg ^ bit_of(B.sp, j)) << 16) | ((uint32_t)(d == 1) << 17), 0u};
       }
-      __syncwarp();
+      g.sync();
       // ---- variable-node update, Eq. (2)-(3); history of Sec. IV-A ----
       const bool hist = it > P.ips - 4;
       const bool hist0 = it == P.ips - 3;
-      for (int k = lane; k < ns; k += 32) {
+      for (int k = R; k < ns; k += S) {
         if (B.status[k] != -1) continue;
         float p = G.llr[k];
-        const int ee = G.colptr[k + 1];
-        for (int e = G.colptr[k]; e < ee; ++e) {
-          const int j = G.colrows[e];
-          p = __fadd_rn(p, c2v_msg(P.alpha, P.clip, B.min1[j], B.min2[j], B.amin[j], B.cfl[j], e,
-                                   B.sign[e]));
+        const int eb = G.colptr[k], ee = G.colptr[k + 1];
+        for (int e0 = eb; e0 < ee; e0 += 8) {
+          float c[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (e0 + u < ee) c[u] = c2v_msg(P.alpha, P.clip, B.cns[G.colrows[e0 + u]], e0 + u, B.sign[e0 + u]);
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (e0 + u < ee) p = __fadd_rn(p, c[u]);  // ascending check order (Eq. (2))
         }
         B.post[k] = p;
         if (hist) {
-          uint8_t f = (uint8_t)((p <= 0.0f) | ((p < PA) << 1) | ((p > P.pc) << 2) | ((p > P.pd) << 3));
+          const uint8_t f = (uint8_t)((p <= 0.0f) | ((p < PA) << 1) | ((p > P.pc) << 2) | ((p > P.pd) << 3));
           if (hist0) {
             B.acc[k] = p;
             B.hfl[k] = f;
@@ -270,22 +434,19 @@ __device__ void run_branch(const KParams& P, const ShortG& G, const BrPtr& B, in
             atomicXor(&par[j >> 5], 1u << (j & 31));
           }
       }
-      __syncwarp();
+      g.sync();
       ++iters;
       first = false;
       bool ok = true;
-      for (int x = lane; x < rw; x += 32) ok &= (par[x] == B.sp[x]);
-      if (__all_sync(FULL, ok)) {
+      for (int x = R; x < rw; x += S) ok &= (par[x] == B.sp[x]);
+      if (g.all(ok)) {
         status = BR_CONVERGED;
         double s = 0.0;
-        for (int k = lane; k < ns; k += 32) {
-          int st8 = B.status[k];
-          bool one = st8 == 1 || (st8 == -1 && B.post[k] <= 0.0f);
-          if (one) s += (double)G.llr[k];
+        for (int k = R; k < ns; k += S) {
+          const int st8 = B.status[k];
+          if (st8 == 1 || (st8 == -1 && B.post[k] <= 0.0f)) s += (double)G.llr[k];
         }
-#pragma unroll
-        for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(FULL, s, off);
-        pm = s;
+        pm = g.sum_d(s);
         goto done;
       }
     }
@@ -294,12 +455,12 @@ __device__ void run_branch(const KParams& P, const ShortG& G, const BrPtr& B, in
       // ---- SELECT-VN (Alg. 1) with AGG-DEC (Alg. 3) ----
       const uint32_t* lastpar = B.par + ((iters - 1) & 1) * rw;
       if (!P.low_err)
-        for (int x = lane; x < rw; x += 32) B.unsat[x] = lastpar[x] ^ B.sp[x];
-      __syncwarp();
+        for (int x = R; x < rw; x += S) B.unsat[x] = lastpar[x] ^ B.sp[x];
+      g.sync();
       const float PBd = (D == 1) ? P.pb_d1 : PB;
       float bL = CUDART_INF_F, tL = CUDART_INF_F;
-      int bk = 0x7fffffff, tk = 0x7fffffff, nagg = 0;
-      for (int k = lane; k < ns; k += 32) {
+      int bk = kNone, tk = kNone, nagg = 0;
+      for (int k = R; k < ns; k += S) {
         if (B.status[k] != -1 || G.vdeg[k] <= 2) continue;
         const float L = B.acc[k];
         const uint8_t fl = B.hfl[k];
@@ -324,36 +485,29 @@ __device__ void run_branch(const KParams& P, const ShortG& G, const BrPtr& B, in
           tk = k;
         }
       }
-      warp_argmin(bL, bk);
-      warp_argmin(tL, tk);
-#pragma unroll
-      for (int off = 16; off; off >>= 1) nagg += __shfl_xor_sync(FULL, nagg, off);
-      __syncwarp();
-      int g, f;
-      if (tk != 0x7fffffff) {
-        g = tk;
+      g.argmin(bL, bk);
+      g.argmin(tL, tk);
+      nagg = g.sum_i(nagg);
+      g.sync();
+      int gsel, f;
+      if (tk != kNone) {
+        gsel = tk;
         f = 1;
-      } else if (bk != 0x7fffffff) {
-        g = bk;
+      } else if (bk != kNone) {
+        gsel = bk;
         f = bL <= 0.0f ? 1 : 0;
       } else {
-        if (st && lane == 0) st[D - 1] = StepTrace{-1, -1, 0, (int16_t)nagg, 0};
+        if (out.st && R == 0) out.st[D - 1] = StepTrace{-1, -1, 0, (int16_t)nagg, 0};
         status = BR_NOCAND;
         goto done;
       }
       int v = f;
       if (D <= P.k) v = ((id >> (P.k - D)) & 1) ? 1 - f : f;  // b + (-1)^b f
-      if (lane == 0) {
-        B.status[g] = (int8_t)v;
-        for (int e = G.colptr[g]; e < G.colptr[g + 1]; ++e) {
-          int r = G.colrows[e];
-          B.deg[r] -= 1;
-          if (v) B.sp[r >> 5] ^= 1u << (r & 31);
-        }
-      }
-      __syncwarp();
-      int np = peel(G, B, lane);
-      if (st && lane == 0) st[D - 1] = StepTrace{(int16_t)g, (int8_t)v, 0, (int16_t)nagg, (int16_t)(np < 0 ? -1 : np)};
+      if (R == 0) decimate_one(G, B, gsel, v);
+      g.sync();
+      const int np = peel(G, B, g);
+      if (out.st && R == 0)
+        out.st[D - 1] = StepTrace{(int16_t)gsel, (int8_t)v, 0, (int16_t)nagg, (int16_t)(np < 0 ? -1 : np)};
       if (np < 0) {
         status = np == -1 ? BR_CONTRADICTION : BR_INTERNAL;
         goto done;
@@ -361,27 +515,27 @@ __device__ void run_branch(const KParams& P, const ShortG& G, const BrPtr& B, in
     }
   }
 done:
-  __syncwarp();
-  for (int base = 0; base < ns; base += 32) {
-    int k = base + lane;
+  g.sync();
+  for (int base = 0; base < ns; base += S) {
+    const int k = base + R;
     bool one = false;
     if (k < ns) {
-      int s8 = B.status[k];
+      const int s8 = B.status[k];
       one = s8 == 1 || (s8 == -1 && B.post[k] <= 0.0f);
-      if (fstat) fstat[k] = (int8_t)s8;
+      if (out.fstat) out.fstat[k] = (int8_t)s8;
     }
-    unsigned m = __ballot_sync(FULL, one);
-    if (lane == 0) out_ebits[base >> 5] = m;
+    const unsigned m = __ballot_sync(FULL, one);
+    const int w0 = base + (R & ~31);
+    if ((R & 31) == 0 && w0 < ns) out.ebits[w0 >> 5] = m;
   }
-#pragma unroll
-  for (int off = 16; off; off >>= 1) visits += __shfl_xor_sync(FULL, visits, off);
-  if (lane == 0) {
-    *out_status = status;
-    *out_pm = status == BR_CONVERGED ? pm : CUDART_INF;
-    if (btr) *btr = BranchTrace{status, depth, iters, 0, status == BR_CONVERGED ? pm : CUDART_INF};
-    atomicAdd((unsigned long long*)edge_visits, (unsigned long long)visits);
+  visits = g.sum_ll(visits);
+  if (R == 0) {
+    *out.status = status;
+    *out.pm = status == BR_CONVERGED ? pm : CUDART_INF;
+    if (out.btr) *out.btr = BranchTrace{status, depth, iters, 0, status == BR_CONVERGED ? pm : CUDART_INF};
+    atomicAdd((unsigned long long*)out.visits, (unsigned long long)visits);
   }
-  __syncwarp();
+  g.sync();
 }
 
 // Trace layout of one shot: int32 head[4]; BranchTrace[nb]; StepTrace[nb][dmx];
@@ -398,95 +552,112 @@ __host__ __device__ inline size_t trace_bytes(int nb, int dmx, int nsm) {
   return (trace_off_sel(nb, dmx, nsm) + 2 * (size_t)nsm + 15) & ~(size_t)15;
 }
 
-__global__ void __launch_bounds__(512, 1)
-    decode_window_kernel(KParams P, WinDev W, Layout L, const uint32_t* __restrict__ det,
-                         int det_words, long long n_shots, uint32_t* __restrict__ corr, int corr_words,
-                         int32_t* __restrict__ status_out, char* __restrict__ trace, size_t tr_bytes,
-                         int dmx, int ns_max, int* __restrict__ work, long long* __restrict__ counters) {
-  extern __shared__ __align__(16) char sm[];
-  const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, NW = NT >> 5;
+struct DecodeArgs {
+  KParams P;
+  WinDev W;
+  Layout L;
+  const uint32_t* det;
+  int det_words;
+  long long n_shots;
+  uint32_t* corr;
+  int corr_words;
+  int32_t* status_out;
+  char* trace;
+  size_t tr_bytes;
+  int dmx, ns_max;
+  int* work;            // shot mode: work counter
+  long long* counters;  // [0] pre-BP edge-iterations, [1] GDG edge visits, [2] pre-BP converged, [3] GDG windows
+  char* path_res;       // path mode: results [shot][path]
+  int* arrive;          // path mode: per-shot arrival counters (0 between launches)
+  int sw_max;
+};
+
+// a1 + a2 (+ a3 when not converged): the shared prefix of both launch shapes.
+// Returns true when the pre-BP converged (cbits then hold its decision).
+__device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, long long shot, int* t_run_out) {
+  const KParams& P = A.P;
+  const Layout& L = A.L;
+  const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int nr = W.n_rows, nc = W.n_cols;
   uint32_t* sbits = (uint32_t*)(sm + L.sbits);
   uint32_t* cbits = (uint32_t*)(sm + L.cbits);
   uint16_t* sel = (uint16_t*)(sm + L.sel);
-  int* misc = (int*)(sm + L.misc);
   char* U = sm + L.U;
   float* post = (float*)(U + L.p_post);
   float* key = (float*)(U + L.p_key);
-  float* min1 = (float*)(U + L.p_min1);
-  float* min2 = (float*)(U + L.p_min2);
-  uint16_t* amin = (uint16_t*)(U + L.p_amin);
-  uint8_t* cfl = (uint8_t*)(U + L.p_cfl);
+  CNState* cns = (CNState*)(U + L.p_cns);
   uint8_t* sign = (uint8_t*)(U + L.p_sign);
   uint32_t* parb = (uint32_t*)(U + L.p_par);
   unsigned long long* sortb = (unsigned long long*)(U + L.p_sort);
 
-  while (true) {
-    __syncthreads();
-    if (tid == 0) misc[0] = atomicAdd(work, 1);
-    __syncthreads();
-    const long long shot = misc[0];
-    if (shot >= n_shots) break;
-    char* tr = trace ? trace + (size_t)shot * tr_bytes : nullptr;
+  // ---- a1: window syndrome ----
+  const uint32_t* dp = A.det + (size_t)shot * A.det_words;
+  for (int x = tid; x < L.rw; x += NT) {
+    const int b0 = W.row0 + 32 * x;
+    const uint32_t lo = dp[b0 >> 5];
+    const uint32_t hi = ((b0 >> 5) + 1 < A.det_words) ? dp[(b0 >> 5) + 1] : 0u;
+    const int sh = b0 & 31;
+    uint32_t v = sh ? ((lo >> sh) | (hi << (32 - sh))) : lo;
+    const int rem = nr - 32 * x;
+    if (rem < 32) v &= (1u << rem) - 1u;
+    sbits[x] = v;
+  }
+  for (int x = tid; x < L.cw; x += NT) cbits[x] = 0;
+  __syncthreads();
 
-    // ---- a1: window syndrome ----
-    const uint32_t* dp = det + (size_t)shot * det_words;
-    for (int x = tid; x < L.rw; x += NT) {
-      int b0 = W.row0 + 32 * x;
-      uint32_t lo = dp[b0 >> 5];
-      uint32_t hi = ((b0 >> 5) + 1 < det_words) ? dp[(b0 >> 5) + 1] : 0u;
-      int sh = b0 & 31;
-      uint32_t v = sh ? ((lo >> sh) | (hi << (32 - sh))) : lo;
-      int rem = nr - 32 * x;
-      if (rem < 32) v &= (1u << rem) - 1u;
-      sbits[x] = v;
-    }
-    for (int x = tid; x < L.cw; x += NT) cbits[x] = 0;
+  // ---- a2: pre-BP on the full window ----
+  const int tpc_pre = lanes_per_check(NT, nr), sub_pre = tid & (tpc_pre - 1);
+  const int nr_rounds = (nr + NT / tpc_pre - 1) / (NT / tpc_pre) * (NT / tpc_pre);
+  bool conv = false;
+  int t = 0;
+  const int tk0 = P.n_pre - 3 > 1 ? P.n_pre - 3 : 1;
+  if (P.n_pre == 0) {
+    uint32_t* pb = parb;
+    for (int x = tid; x < L.rw; x += NT) pb[x] = 0;
     __syncthreads();
-
-    // ---- a2: pre-BP on the full window ----
-    bool conv = false;
-    int t = 0;
-    const int tk0 = P.n_pre - 3 > 1 ? P.n_pre - 3 : 1;
-    if (P.n_pre == 0) {
-      // decision from the priors alone; key = 4 Lambda
-      uint32_t* pb = parb;
-      for (int x = tid; x < L.rw; x += NT) pb[x] = 0;
-      __syncthreads();
-      for (int i = tid; i < nc; i += NT) {
-        float li = W.llr[i];
-        post[i] = li;
-        key[i] = __fadd_rn(__fadd_rn(__fadd_rn(li, li), li), li);
-        if (li <= 0.0f)
-          for (int e = W.col_ptr[i]; e < W.col_ptr[i + 1]; ++e) {
-            int j = W.col_rows[e];
-            atomicXor(&pb[j >> 5], 1u << (j & 31));
-          }
-      }
-      __syncthreads();
-      bool ok = true;
-      for (int x = 0; x < L.rw; ++x) ok &= (pb[x] == sbits[x]);
-      conv = ok;
+    for (int i = tid; i < nc; i += NT) {
+      const float li = W.llr[i];
+      post[i] = li;
+      key[i] = __fadd_rn(__fadd_rn(__fadd_rn(li, li), li), li);
+      if (li <= 0.0f)
+        for (int e = W.col_ptr[i]; e < W.col_ptr[i + 1]; ++e) {
+          const int j = W.col_rows[e];
+          atomicXor(&pb[j >> 5], 1u << (j & 31));
+        }
     }
-    for (t = 1; t <= P.n_pre; ++t) {
-      uint32_t* pb = parb + (t & 1) * L.rw;
-      for (int x = tid; x < L.rw; x += NT) pb[x] = 0;
-      for (int j = warp; j < nr; j += NW) {
-        const int beg = W.row_ptr[j], end = W.row_ptr[j + 1];
-        const float om1 = min1[j], om2 = min2[j];
-        const uint16_t oam = amin[j];
-        const uint8_t ocfl = cfl[j];
-        float m1 = FLT_MAX * 2.0f, m2 = FLT_MAX * 2.0f;
-        int am = 0xFFFF;
-        unsigned neg = 0;
-        for (int q = beg + lane; q < end; q += 32) {
-          const int e = W.row_edges[q];
-          const int i = W.edge_col[e];
-          float v = (t == 1) ? W.llr[i]
-                             : clipf(__fsub_rn(post[i], c2v_msg(P.alpha, P.clip, om1, om2, oam, ocfl,
-                                                               e, sign[e])),
-                                     P.clip);
-          float a = fabsf(v);
+    __syncthreads();
+    bool ok = true;
+    for (int x = 0; x < L.rw; ++x) ok &= (pb[x] == sbits[x]);
+    conv = ok;
+  }
+  for (t = 1; t <= P.n_pre; ++t) {
+    uint32_t* pb = parb + (t & 1) * L.rw;
+    for (int x = tid; x < L.rw; x += NT) pb[x] = 0;
+    for (int j0 = tid / tpc_pre; j0 < nr_rounds; j0 += NT / tpc_pre) {
+      const int j = j0 < nr ? j0 : nr - 1;
+      const int beg = W.row_ptr[j], end = j0 < nr ? W.row_ptr[j + 1] : beg;
+      const CNState oc = cns[j];
+      float m1 = CUDART_INF_F, m2 = CUDART_INF_F;
+      int am = 0xFFFF;
+      uint32_t neg = 0;
+      for (int q = beg + 4 * sub_pre; q < end; q += 4 * tpc_pre) {
+        uint32_t ent[4];
+        float pv[4];
+        uint32_t sg[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ent[u] = (q + u < end) ? W.row_ent[q + u] : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = (int)(ent[u] >> 16), e = (int)(ent[u] & 0xFFFFu);
+          pv[u] = (t == 1) ? W.llr[i] : post[i];
+          sg[u] = sign[e];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (q + u >= end) break;
+          const int e = (int)(ent[u] & 0xFFFFu);
+          const float v = (t == 1) ? pv[u] : clipf(__fsub_rn(pv[u], c2v_msg(P.alpha, P.clip, oc, e, sg[u])), P.clip);
+          const float a = fabsf(v);
           if (a < m1) {
             m2 = m1;
             m1 = a;
@@ -494,208 +665,340 @@ __global__ void __launch_bounds__(512, 1)
           } else if (a < m2) {
             m2 = a;
           }
-          unsigned s = v < 0.0f;
-          neg ^= s;
-          sign[e] = (uint8_t)s;
-        }
-        warp_min2(m1, m2, am);
-        neg = __reduce_xor_sync(FULL, neg);
-        __syncwarp();
-        if (lane == 0) {
-          min1[j] = m1;
-          min2[j] = m2;
-          amin[j] = (uint16_t)am;
-          cfl[j] = (uint8_t)((neg ^ bit_of(sbits, j)) | ((end - beg == 1) << 1));
+          const uint32_t sgn = v < 0.0f;
+          neg ^= sgn;
+          sign[e] = (uint8_t)sgn;
         }
       }
-      __syncthreads();
-      const bool kacc = t >= tk0;
-      for (int i = tid; i < nc; i += NT) {
-        float p = W.llr[i];
-        const int eb = W.col_ptr[i], ee = W.col_ptr[i + 1];
+      if (tpc_pre > 1) group_min2(m1, m2, am, neg, tpc_pre);
+      if (sub_pre == 0 && j0 < nr)
+        cns[j] = CNState{m1, m2,
+                         (uint32_t)am | ((neg ^ bit_of(sbits, j)) << 16) | ((uint32_t)(end - beg == 1) << 17), 0u};
+    }
+    __syncthreads();
+    const bool kacc = t >= tk0;
+    for (int i = tid; i < nc; i += NT) {
+      float p = W.llr[i];
+      const int eb = W.col_ptr[i], ee = W.col_ptr[i + 1];
+      for (int e0 = eb; e0 < ee; e0 += 8) {
+        float c[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (e0 + u < ee) c[u] = c2v_msg(P.alpha, P.clip, cns[W.col_rows[e0 + u]], e0 + u, sign[e0 + u]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (e0 + u < ee) p = __fadd_rn(p, c[u]);  // ascending check order (Eq. (2))
+      }
+      post[i] = p;
+      if (kacc) {
+        float kv;
+        if (t == tk0) {
+          if (P.n_pre < 4) {
+            const float li = W.llr[i];
+            float s = li;
+            for (int r = 1; r < 4 - P.n_pre; ++r) s = __fadd_rn(s, li);
+            kv = __fadd_rn(s, p);
+          } else {
+            kv = p;
+          }
+        } else {
+          kv = __fadd_rn(key[i], p);
+        }
+        key[i] = kv;
+      }
+      if (p <= 0.0f)
         for (int e = eb; e < ee; ++e) {
           const int j = W.col_rows[e];
-          p = __fadd_rn(p, c2v_msg(P.alpha, P.clip, min1[j], min2[j], amin[j], cfl[j], e, sign[e]));
+          atomicXor(&pb[j >> 5], 1u << (j & 31));
         }
-        post[i] = p;
-        if (kacc) {
-          float kv;
-          if (t == tk0) {
-            if (P.n_pre < 4) {
-              float li = W.llr[i], s = li;
-              for (int r = 1; r < 4 - P.n_pre; ++r) s = __fadd_rn(s, li);
-              kv = __fadd_rn(s, p);
-            } else {
-              kv = p;
-            }
-          } else {
-            kv = __fadd_rn(key[i], p);
-          }
-          key[i] = kv;
-        }
-        if (p <= 0.0f)
-          for (int e = eb; e < ee; ++e) {
-            const int j = W.col_rows[e];
-            atomicXor(&pb[j >> 5], 1u << (j & 31));
-          }
-      }
-      __syncthreads();
-      bool ok = true;
-      for (int x = 0; x < L.rw; ++x) ok &= (pb[x] == sbits[x]);
-      if (ok) {
-        conv = true;
-        break;
-      }
     }
-    const int t_run = conv ? (P.n_pre == 0 ? 0 : t) : P.n_pre;
-    if (tid == 0) atomicAdd((unsigned long long*)&counters[0], (unsigned long long)t_run * W.n_edges);
+    __syncthreads();
+    bool ok = true;
+    for (int x = 0; x < L.rw; ++x) ok &= (pb[x] == sbits[x]);
+    if (ok) {
+      conv = true;
+      break;
+    }
+  }
+  *t_run_out = conv ? (P.n_pre == 0 ? 0 : t) : P.n_pre;
+  if (conv) {
+    for (int base = warp * 32; base < nc; base += NT) {
+      const int i = base + lane;
+      const bool one = i < nc && post[i] <= 0.0f;
+      const unsigned m = __ballot_sync(FULL, one);
+      if (lane == 0) cbits[base >> 5] = m;
+    }
+    __syncthreads();
+    return true;
+  }
 
-    int winner = -1, n_short = 0;
-    if (conv) {
-      for (int base = warp * 32; base < nc; base += NT) {
-        int i = base + lane;
-        bool one = i < nc && post[i] <= 0.0f;
-        unsigned m = __ballot_sync(FULL, one);
-        if (lane == 0) cbits[base >> 5] = m;
-      }
-      if (tid == 0) atomicAdd((unsigned long long*)&counters[2], 1ull);
-    } else {
-      // ---- a3: rank by the four-iteration sum, keep the first n_short ----
-      n_short = W.n_short;
-      for (int i = tid; i < L.sortn; i += NT)
-        sortb[i] = i < nc ? (((unsigned long long)ordkey(key[i]) << 32) | (unsigned)i) : ~0ull;
-      __syncthreads();
-      for (int kk = 2; kk <= L.sortn; kk <<= 1)
-        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-          for (int i = tid; i < L.sortn; i += NT) {
-            int ixj = i ^ jj;
-            if (ixj > i) {
-              unsigned long long a = sortb[i], b = sortb[ixj];
-              bool up = (i & kk) == 0;
-              if ((a > b) == up) {
-                sortb[i] = b;
-                sortb[ixj] = a;
-              }
-            }
+  // ---- a3: rank by the four-iteration sum, keep the first n_short ----
+  const int n_short = W.n_short;
+  for (int i = tid; i < L.sortn; i += NT)
+    sortb[i] = i < nc ? (((unsigned long long)ordkey(key[i]) << 32) | (unsigned)i) : ~0ull;
+  __syncthreads();
+  for (int kk = 2; kk <= L.sortn; kk <<= 1)
+    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+      for (int i = tid; i < L.sortn; i += NT) {
+        const int ixj = i ^ jj;
+        if (ixj > i) {
+          const unsigned long long a = sortb[i], b = sortb[ixj];
+          const bool up = (i & kk) == 0;
+          if ((a > b) == up) {
+            sortb[i] = b;
+            sortb[ixj] = a;
           }
-          __syncthreads();
-        }
-      for (int k = tid; k < n_short; k += NT) sel[k] = (uint16_t)(sortb[k] & 0xFFFFu);
-      __syncthreads();
-      // ---- shortened matrix in shared memory ----
-      uint16_t* scp = (uint16_t*)(sm + L.s_colptr);
-      uint16_t* scr = (uint16_t*)(sm + L.s_colrows);
-      uint16_t* srp = (uint16_t*)(sm + L.s_rowptr);
-      uint16_t* sre = (uint16_t*)(sm + L.s_rowedges);
-      uint16_t* sec = (uint16_t*)(sm + L.s_edgecol);
-      float* sllr = (float*)(sm + L.s_llr);
-      uint8_t* svd = (uint8_t*)(sm + L.s_vdeg);
-      int* rc = (int*)(sm + L.rowcnt);
-      int* tmp = (int*)sortb;  // sort buffer is free now
-      for (int k = tid; k < n_short; k += NT) {
-        int c = sel[k];
-        int d = W.col_ptr[c + 1] - W.col_ptr[c];
-        tmp[k] = d;
-        sllr[k] = W.llr[c];
-        svd[k] = (uint8_t)d;
-      }
-      for (int j = tid; j <= nr; j += NT) rc[j] = 0;
-      __syncthreads();
-      if (warp == 0) {
-        int tot = warp_scan_excl(tmp, n_short, lane);
-        if (lane == 0) tmp[n_short] = tot;
-      }
-      __syncthreads();
-      for (int k = tid; k <= n_short; k += NT) scp[k] = (uint16_t)tmp[k];
-      for (int k = tid; k < n_short; k += NT) {
-        int c = sel[k], o = tmp[k];
-        for (int e = W.col_ptr[c]; e < W.col_ptr[c + 1]; ++e, ++o) {
-          int r = W.col_rows[e];
-          scr[o] = (uint16_t)r;
-          sec[o] = (uint16_t)k;
-          atomicAdd(&rc[r], 1);
         }
       }
       __syncthreads();
-      if (warp == 0) {
-        int tot = warp_scan_excl(rc, nr, lane);
-        if (lane == 0) rc[nr] = tot;
-      }
-      __syncthreads();
-      for (int j = tid; j <= nr; j += NT) srp[j] = (uint16_t)rc[j];
-      __syncthreads();
-      const int es = scp[n_short];
-      for (int e = tid; e < es; e += NT) {
-        int r = scr[e];
-        int pos = atomicAdd(&rc[r], 1);
-        sre[pos] = (uint16_t)e;
-      }
-      __syncthreads();
-      // ---- a4-a7: GDG, one decision path per warp ----
-      ShortG G{nr, n_short, L.rw, scp, scr, srp, sre, sec, sllr, svd, sbits};
-      int* res_status = (int*)(sm + L.res_status);
-      double* res_pm = (double*)(sm + L.res_pm);
-      uint32_t* res_e = (uint32_t*)(sm + L.res_ebits);
-      char* slot = U + (size_t)warp * L.b_size;
-      BrPtr B{(float*)(slot + L.b_post),    (float*)(slot + L.b_acc),    (uint8_t*)(slot + L.b_hfl),
-              (uint8_t*)(slot + L.b_sign),  (uint8_t*)(slot + L.b_cfl),  (int8_t*)(slot + L.b_status),
-              (float*)(slot + L.b_min1),    (float*)(slot + L.b_min2),   (uint16_t*)(slot + L.b_amin),
-              (int*)(slot + L.b_deg),       (uint32_t*)(slot + L.b_sp),  (uint32_t*)(slot + L.b_par),
-              (uint32_t*)(slot + L.b_unsat)};
-      long long* gdg_it = (long long*)(sm + L.misc + 16);
-      if (tid == 0) *gdg_it = 0;
-      __syncthreads();
-      for (int id = warp; id < P.nb; id += NW) {
-        BranchTrace* btr = tr ? (BranchTrace*)(tr + trace_off_br()) + id : nullptr;
-        StepTrace* st = tr ? (StepTrace*)(tr + trace_off_st(P.nb)) + (size_t)id * dmx : nullptr;
-        int8_t* fs = tr ? (int8_t*)(tr + trace_off_fs(P.nb, dmx)) + (size_t)id * ns_max : nullptr;
-        run_branch(P, G, B, id, lane, &res_status[id], &res_pm[id], res_e + (size_t)id * L.sw, btr, st,
-                   dmx, fs, gdg_it);
+    }
+  for (int k = tid; k < n_short; k += NT) sel[k] = (uint16_t)(sortb[k] & 0xFFFFu);
+  __syncthreads();
+  // ---- shortened matrix in shared memory ----
+  uint16_t* scp = (uint16_t*)(sm + L.s_colptr);
+  uint16_t* scr = (uint16_t*)(sm + L.s_colrows);
+  uint16_t* srp = (uint16_t*)(sm + L.s_rowptr);
+  uint32_t* sre = (uint32_t*)(sm + L.s_rowent);
+  float* sllr = (float*)(sm + L.s_llr);
+  uint8_t* svd = (uint8_t*)(sm + L.s_vdeg);
+  int* rc = (int*)(sm + L.rowcnt);
+  int* tmp = (int*)sortb;  // the sort buffer is free now
+  for (int k = tid; k < n_short; k += NT) {
+    const int c = sel[k];
+    const int d = W.col_ptr[c + 1] - W.col_ptr[c];
+    tmp[k] = d;
+    sllr[k] = W.llr[c];
+    svd[k] = (uint8_t)d;
+  }
+  for (int j = tid; j <= nr; j += NT) rc[j] = 0;
+  __syncthreads();
+  if (warp == 0) {
+    const int tot = warp_scan_excl(tmp, n_short, lane);
+    if (lane == 0) tmp[n_short] = tot;
+  }
+  __syncthreads();
+  for (int k = tid; k <= n_short; k += NT) scp[k] = (uint16_t)tmp[k];
+  for (int k = tid; k < n_short; k += NT) {
+    const int c = sel[k];
+    int o = tmp[k];
+    for (int e = W.col_ptr[c]; e < W.col_ptr[c + 1]; ++e, ++o) {
+      const int r = W.col_rows[e];
+      scr[o] = (uint16_t)r;
+      atomicAdd(&rc[r], 1);
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int tot = warp_scan_excl(rc, nr, lane);
+    if (lane == 0) rc[nr] = tot;
+  }
+  __syncthreads();
+  for (int j = tid; j <= nr; j += NT) srp[j] = (uint16_t)rc[j];
+  __syncthreads();
+  for (int k = tid; k < n_short; k += NT)
+    for (int e = scp[k]; e < scp[k + 1]; ++e) {
+      const int pos = atomicAdd(&rc[scr[e]], 1);
+      sre[pos] = (uint32_t)e | ((uint32_t)k << 16);
+    }
+  __syncthreads();
+  return false;
+}
+
+__device__ __forceinline__ ShortG short_graph(char* sm, const Layout& L, int nr, int ns) {
+  return ShortG{nr, ns, L.rw,
+                (const uint16_t*)(sm + L.s_colptr), (const uint16_t*)(sm + L.s_colrows),
+                (const uint16_t*)(sm + L.s_rowptr), (const uint32_t*)(sm + L.s_rowent),
+                (const float*)(sm + L.s_llr),       (const uint8_t*)(sm + L.s_vdeg),
+                (const uint32_t*)(sm + L.sbits)};
+}
+
+__device__ __forceinline__ PathOut trace_out(const DecodeArgs& A, char* tr, int id) {
+  PathOut o{};
+  if (tr) {
+    o.btr = (BranchTrace*)(tr + trace_off_br()) + id;
+    o.st = (StepTrace*)(tr + trace_off_st(A.P.nb)) + (size_t)id * A.dmx;
+    o.fstat = (int8_t*)(tr + trace_off_fs(A.P.nb, A.dmx)) + (size_t)id * A.ns_max;
+  }
+  o.visits = &A.counters[1];
+  return o;
+}
+
+__device__ void write_outputs(const DecodeArgs& A, char* sm, long long shot, bool conv, int winner,
+                              int n_short, int t_run, char* tr) {
+  const Layout& L = A.L;
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const uint32_t* cbits = (const uint32_t*)(sm + L.cbits);
+  uint32_t* co = A.corr + (size_t)shot * A.corr_words;
+  for (int x = tid; x < A.corr_words; x += NT) co[x] = x < L.cw ? cbits[x] : 0u;
+  if (tr && !conv)
+    for (int k = tid; k < n_short; k += NT)
+      ((uint16_t*)(tr + trace_off_sel(A.P.nb, A.dmx, A.ns_max)))[k] = ((const uint16_t*)(sm + L.sel))[k];
+  if (tid == 0) {
+    if (A.status_out) A.status_out[shot] = conv ? -1 : (winner >= 0 ? winner : -2);
+    if (tr) {
+      int32_t* h = (int32_t*)tr;
+      h[0] = conv ? 1 : 0;
+      h[1] = conv ? -1 : winner;
+      h[2] = conv ? 0 : n_short;
+      h[3] = t_run;
+    }
+    atomicAdd((unsigned long long*)&A.counters[0], (unsigned long long)t_run * A.W.n_edges);
+    atomicAdd((unsigned long long*)&A.counters[conv ? 2 : 3], 1ull);
+  }
+}
+
+// ---- shot mode: persistent CTAs of 8 warps, one warp per decision path ----
+__global__ void __launch_bounds__(256, 2) decode_shot_kernel(DecodeArgs A) {
+  extern __shared__ __align__(16) char sm[];
+  const Layout& L = A.L;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int* misc = (int*)(sm + L.misc);
+  int* res_status = (int*)(sm + L.res_status);
+  double* res_pm = (double*)(sm + L.res_pm);
+  uint32_t* res_e = (uint32_t*)(sm + L.res_ebits);
+  uint32_t* cbits = (uint32_t*)(sm + L.cbits);
+  const uint16_t* sel = (const uint16_t*)(sm + L.sel);
+  while (true) {
+    __syncthreads();
+    if (tid == 0) {
+      misc[0] = atomicAdd(A.work, 1);
+      misc[2] = 0;  // decision-path queue, path 0 first
+    }
+    __syncthreads();
+    const long long shot = misc[0];
+    if (shot >= A.n_shots) break;
+    char* tr = A.trace ? A.trace + (size_t)shot * A.tr_bytes : nullptr;
+    int t_run = 0;
+    const bool conv = window_prefix(A, A.W, sm, shot, &t_run);
+    int winner = -1;
+    const int n_short = conv ? 0 : A.W.n_short;
+    if (!conv) {
+      const ShortG G = short_graph(sm, L, A.W.n_rows, n_short);
+      const Slot B = make_slot(sm + L.U + (size_t)warp * L.b_size, L);
+      const WarpGrp g{lane};
+      while (true) {
+        int id = 0;
+        if (lane == 0) id = atomicAdd(&misc[2], 1);
+        id = __shfl_sync(FULL, id, 0);
+        if (id >= A.P.nb) break;
+        PathOut o = trace_out(A, tr, id);
+        o.status = &res_status[id];
+        o.pm = &res_pm[id];
+        o.ebits = res_e + (size_t)id * L.sw;
+        run_path(A.P, G, B, id, g, o, A.dmx);
       }
       __syncthreads();
       // ---- a8: least path metric, ties to the lowest id ----
       if (tid == 0) {
         int best = -1;
         double bp = CUDART_INF;
-        for (int id = 0; id < P.nb; ++id)
+        for (int id = 0; id < A.P.nb; ++id)
           if (res_status[id] == BR_CONVERGED && res_pm[id] < bp) {
             bp = res_pm[id];
             best = id;
           }
         misc[1] = best;
-        atomicAdd((unsigned long long*)&counters[1], (unsigned long long)(*gdg_it));
-        atomicAdd((unsigned long long*)&counters[3], 1ull);
       }
       __syncthreads();
       winner = misc[1];
       const uint32_t* eb = res_e + (size_t)(winner >= 0 ? winner : 0) * L.sw;
-      for (int k = tid; k < n_short; k += NT)
+      for (int k = tid; k < n_short; k += blockDim.x)
         if ((eb[k >> 5] >> (k & 31)) & 1u) atomicOr(&cbits[sel[k] >> 5], 1u << (sel[k] & 31));
-      if (tr)
-        for (int k = tid; k < n_short; k += NT) ((uint16_t*)(tr + trace_off_sel(P.nb, dmx, ns_max)))[k] = sel[k];
+      __syncthreads();
     }
+    write_outputs(A, sm, shot, conv, winner, n_short, t_run, tr);
+  }
+}
+
+// ---- path mode: one CTA per (shot, path); the last CTA of a shot decides ----
+__global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
+  extern __shared__ __align__(16) char sm[];
+  const Layout& L = A.L;
+  const int tid = threadIdx.x;
+  const int nb = A.P.nb;
+  const long long shot = blockIdx.x / nb;
+  const int id = blockIdx.x % nb;
+  int* misc = (int*)(sm + L.misc);
+  char* tr = A.trace ? A.trace + (size_t)shot * A.tr_bytes : nullptr;
+  // stage the window graph in shared memory (one CTA per SM in this mode)
+  WinDev W = A.W;
+  {
+    const WinDev& G = A.W;
+    uint16_t* cp = (uint16_t*)(sm + L.g_colptr);
+    uint16_t* cr = (uint16_t*)(sm + L.g_colrows);
+    uint16_t* rp = (uint16_t*)(sm + L.g_rowptr);
+    uint32_t* re = (uint32_t*)(sm + L.g_rowent);
+    float* ll = (float*)(sm + L.g_llr);
+    for (int x = tid; x <= G.n_cols; x += blockDim.x) cp[x] = G.col_ptr[x];
+    for (int x = tid; x <= G.n_rows; x += blockDim.x) rp[x] = G.row_ptr[x];
+    for (int x = tid; x < G.n_edges; x += blockDim.x) {
+      cr[x] = G.col_rows[x];
+      re[x] = G.row_ent[x];
+    }
+    for (int x = tid; x < G.n_cols; x += blockDim.x) ll[x] = G.llr[x];
+    W.col_ptr = cp;
+    W.col_rows = cr;
+    W.row_ptr = rp;
+    W.row_ent = re;
+    W.llr = ll;
     __syncthreads();
-    uint32_t* co = corr + (size_t)shot * corr_words;
-    for (int x = tid; x < corr_words; x += NT) co[x] = x < L.cw ? cbits[x] : 0u;
-    if (tid == 0) {
-      if (status_out) status_out[shot] = conv ? -1 : (winner >= 0 ? winner : -2);
-      if (tr) {
-        int32_t* h = (int32_t*)tr;
-        h[0] = conv ? 1 : 0;
-        h[1] = conv ? -1 : winner;
-        h[2] = n_short;
-        h[3] = t_run;
+  }
+  int t_run = 0;
+  const bool conv = window_prefix(A, W, sm, shot, &t_run);
+  if (conv) {
+    if (id == 0) write_outputs(A, sm, shot, true, -1, 0, t_run, tr);
+    return;
+  }
+  const int n_short = A.W.n_short;
+  const ShortG G = short_graph(sm, L, A.W.n_rows, n_short);
+  const Slot B = make_slot(sm + L.U, L);
+  const CtaGrp g{tid, (int)blockDim.x, sm + L.red};
+  const size_t rb = path_result_bytes(A.sw_max);
+  char* mine = A.path_res + ((size_t)shot * nb + id) * rb;
+  PathOut o = trace_out(A, tr, id);
+  o.status = (int*)mine;
+  o.pm = (double*)(mine + 8);
+  o.ebits = (uint32_t*)(mine + 16);
+  run_path(A.P, G, B, id, g, o, A.dmx);
+  // publish, then count arrivals; the last CTA of the shot reduces
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) misc[3] = (atomicAdd(&A.arrive[shot], 1) == nb - 1);
+  __syncthreads();
+  if (!misc[3]) return;
+  __threadfence();
+  if (tid == 0) {
+    int best = -1;
+    double bp = CUDART_INF;
+    for (int q = 0; q < nb; ++q) {
+      const char* r = A.path_res + ((size_t)shot * nb + q) * rb;
+      const int st = __ldcg((const int*)r);
+      const double pm = __ldcg((const double*)(r + 8));
+      if (st == BR_CONVERGED && pm < bp) {
+        bp = pm;
+        best = q;
       }
     }
+    misc[1] = best;
+    A.arrive[shot] = 0;  // ready for the next launch
   }
+  __syncthreads();
+  const int winner = misc[1];
+  const uint32_t* eb = (const uint32_t*)(A.path_res + ((size_t)shot * nb + (winner >= 0 ? winner : 0)) * rb + 16);
+  uint32_t* cbits = (uint32_t*)(sm + L.cbits);
+  const uint16_t* sel = (const uint16_t*)(sm + L.sel);
+  for (int k = tid; k < n_short; k += blockDim.x)
+    if ((__ldcg(&eb[k >> 5]) >> (k & 31)) & 1u) atomicOr(&cbits[sel[k] >> 5], 1u << (sel[k] & 31));
+  __syncthreads();
+  write_outputs(A, sm, shot, false, winner, n_short, t_run, tr);
 }
 
 // ---- Philox4x32-10 (Salmon et al., SC'11) ----
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
     c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
     k.x += 0x9E3779B9u;
     k.y += 0xBB67AE85u;
@@ -721,14 +1024,14 @@ __global__ void sample_kernel(int n_cols, const uint32_t* __restrict__ thr, cons
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     const int ng = (n_cols + 3) >> 2;
     for (int g = lane; g < ng; g += 32) {
-      uint4 u = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)shot, (uint32_t)(shot >> 32), 0u), key);
-      uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+      const uint4 u = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)shot, (uint32_t)(shot >> 32), 0u), key);
+      const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        int c = 4 * g + r;
+        const int c = 4 * g + r;
         if (c < n_cols && uu[r] < thr[c]) {
           for (int e = cptr[c]; e < cptr[c + 1]; ++e) {
-            int d = cdet[e];
+            const int d = cdet[e];
             atomicXor(&row[d >> 5], 1u << (d & 31));
           }
           ob ^= cobs[c];
@@ -758,14 +1061,14 @@ __global__ void commit_kernel(int n_commit, const int* __restrict__ cptr, const 
   const int nw = (n_commit + 31) >> 5;
   for (int x = 0; x < nw; ++x) {
     uint32_t m = c[x];
-    int rem = n_commit - 32 * x;
+    const int rem = n_commit - 32 * x;
     if (rem < 32) m &= (1u << rem) - 1u;
     while (m) {
-      int b = __ffs(m) - 1;
+      const int b = __ffs(m) - 1;
       m &= m - 1;
-      int col = 32 * x + b;
+      const int col = 32 * x + b;
       for (int e = cptr[col]; e < cptr[col + 1]; ++e) {
-        int q = cdet[e];
+        const int q = cdet[e];
         d[q >> 5] ^= 1u << (q & 31);
       }
       ob ^= cobs[col];
@@ -774,10 +1077,10 @@ __global__ void commit_kernel(int n_commit, const int* __restrict__ cptr, const 
   obs_pred[s] ^= ob;
   uint32_t bad = 0;
   for (int q = res_b0; q < res_b1;) {
-    int wq = q >> 5, lo = q & 31;
-    int hiq = min(res_b1, (wq + 1) * 32);
+    const int wq = q >> 5, lo = q & 31;
+    const int hiq = min(res_b1, (wq + 1) * 32);
     uint32_t m = d[wq] >> lo;
-    int nb = hiq - q;
+    const int nb = hiq - q;
     if (nb < 32) m &= (1u << nb) - 1u;
     bad |= m;
     q = hiq;
@@ -794,63 +1097,66 @@ __global__ void evaluate_kernel(const uint32_t* __restrict__ pred, const uint32_
     f = (resid[s] & 1u) | ((pred[s] != obs[s]) ? 2u : 0u);
     if (fail) fail[s] = f;
   }
-  unsigned m = __ballot_sync(FULL, f != 0);
+  const unsigned m = __ballot_sync(FULL, f != 0);
   if (n_fail && (threadIdx.x & 31) == 0 && m) atomicAdd((unsigned long long*)n_fail, (unsigned long long)__popc(m));
 }
 
 }  // namespace dev
-}  // namespace qd
 
 // ---------------------------------------------------------------------------
 // Host-side launch wrappers (declared in qdec_internal.h).
-namespace qd {
 
 size_t trace_bytes_per_shot(int nb, int dmx, int ns_max) { return dev::trace_bytes(nb, dmx, ns_max); }
 
 cudaError_t set_decode_smem(size_t bytes) {
-  return cudaFuncSetAttribute(dev::decode_window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)bytes);
+  cudaError_t e =
+      cudaFuncSetAttribute(dev::decode_shot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(dev::decode_path_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-cudaError_t decode_occupancy(int threads, size_t smem, int* blocks) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::decode_window_kernel, threads, smem);
+cudaError_t decode_occupancy(int mode, int threads, size_t smem, int* blocks) {
+  if (mode == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::decode_path_kernel, threads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::decode_shot_kernel, threads, smem);
 }
 
-cudaError_t launch_decode(int grid, int threads, size_t smem, cudaStream_t st, const KParams& P,
-                          const WinDev& W, const Layout& L, const uint32_t* det, int det_words,
-                          long long n, uint32_t* corr, int corr_words, int32_t* status, char* trace,
-                          size_t tr_bytes, int dmx, int ns_max, int* work, long long* counters) {
-  dev::decode_window_kernel<<<grid, threads, smem, st>>>(P, W, L, det, det_words, n, corr, corr_words,
-                                                         status, trace, tr_bytes, dmx, ns_max, work,
-                                                         counters);
+cudaError_t launch_decode(int mode, int grid, int threads, size_t smem, cudaStream_t st, const KParams& P,
+                          const WinDev& W, const Layout& L, const uint32_t* det, int det_words, long long n,
+                          uint32_t* corr, int corr_words, int32_t* status, char* trace, size_t tr_bytes, int dmx,
+                          int ns_max, int* work, long long* counters, char* path_res, int* arrive, int sw_max) {
+  const dev::DecodeArgs A{P,     W,        L,     det,      det_words, n,     corr,     corr_words, status,
+                          trace, tr_bytes, dmx,   ns_max,   work,      counters, path_res, arrive,     sw_max};
+  if (mode == 1)
+    dev::decode_path_kernel<<<grid, threads, smem, st>>>(A);
+  else
+    dev::decode_shot_kernel<<<grid, threads, smem, st>>>(A);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sample(cudaStream_t st, int n_cols, const uint32_t* thr, const int* cptr,
-                          const int* cdet, const uint32_t* cobs, int det_words,
-                          unsigned long long seed, unsigned long long off, long long n, uint32_t* det,
-                          uint32_t* obs) {
+cudaError_t launch_sample(cudaStream_t st, int n_cols, const uint32_t* thr, const int* cptr, const int* cdet,
+                          const uint32_t* cobs, int det_words, unsigned long long seed, unsigned long long off,
+                          long long n, uint32_t* det, uint32_t* obs) {
   if (n <= 0) return cudaSuccess;
   const int wpb = 8;
-  long long blocks = (n + wpb - 1) / wpb;
+  const long long blocks = (n + wpb - 1) / wpb;
   dev::sample_kernel<<<(unsigned)blocks, 32 * wpb, sizeof(uint32_t) * wpb * det_words, st>>>(
       n_cols, thr, cptr, cdet, cobs, det_words, seed, off, n, det, obs);
   return cudaGetLastError();
 }
 
-cudaError_t launch_commit(cudaStream_t st, int n_commit, const int* cptr, const int* cdet,
-                          const uint32_t* cobs, int corr_words, const uint32_t* corr, long long n,
-                          uint32_t* det, int det_words, uint32_t* obs_pred, uint32_t* resid, int b0,
-                          int b1) {
+cudaError_t launch_commit(cudaStream_t st, int n_commit, const int* cptr, const int* cdet, const uint32_t* cobs,
+                          int corr_words, const uint32_t* corr, long long n, uint32_t* det, int det_words,
+                          uint32_t* obs_pred, uint32_t* resid, int b0, int b1) {
   if (n <= 0) return cudaSuccess;
   const int tpb = 128;
-  dev::commit_kernel<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, st>>>(
-      n_commit, cptr, cdet, cobs, corr_words, corr, n, det, det_words, obs_pred, resid, b0, b1);
+  dev::commit_kernel<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, st>>>(n_commit, cptr, cdet, cobs, corr_words,
+                                                                      corr, n, det, det_words, obs_pred, resid,
+                                                                      b0, b1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_evaluate(cudaStream_t st, const uint32_t* pred, const uint32_t* obs,
-                            const uint32_t* resid, long long n, uint32_t* fail, long long* n_fail) {
+cudaError_t launch_evaluate(cudaStream_t st, const uint32_t* pred, const uint32_t* obs, const uint32_t* resid,
+                            long long n, uint32_t* fail, long long* n_fail) {
   if (n <= 0) return cudaSuccess;
   const int tpb = 256;
   dev::evaluate_kernel<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, st>>>(pred, obs, resid, n, fail, n_fail);

@@ -1,15 +1,15 @@
-// gdg_kernel.cuh -- device code of the window decoder (one CTA per shot).
+// gdg_kernel.cuh -- shared definitions of the window decoder (host and device).
 //
 // Message representation.  Min-sum (Eq. (1)) sends from check j to variable i
 //   mu_{j->i} = (-1)^{s_j} * (alpha * min_{i' != i} |mu_{i'->j}|) * prod_{i' != i} sign(mu_{i'->j})
 // which only depends on the check's two smallest |mu| (min1, min2), the edge
 // holding min1 (amin), the sign parity of all its inputs xor s_j, and the sign
 // of the receiving edge's own input.  The kernel keeps exactly that per check
-// plus one sign byte per edge, instead of two FP32 messages per edge.  The
-// VN->CN message of Eq. (3) is recomputed where it is needed as
-// clip(Lambda_i^(t) - mu_{j->i}), the same FP32 operations the explicit
-// form performs, so every value is bit-identical to it.  All FP32 operations
-// are __fadd_rn / __fmul_rn (never contracted into FMA).
+// (one 16-byte record) plus one sign byte per edge, instead of two FP32
+// messages per edge.  The VN->CN message of Eq. (3) is recomputed where it is
+// needed as clip(Lambda_i^(t) - mu_{j->i}), the same FP32 operations the
+// explicit form performs, so every value is bit-identical to it.  All FP32
+// operations are __fadd_rn / __fsub_rn / __fmul_rn (never contracted).
 #pragma once
 #include <cstdint>
 
@@ -24,8 +24,17 @@ struct KParams {
 // One window's Tanner graph in global memory (read-only for all shots).
 struct WinDev {
   int n_rows, n_cols, n_edges, row0, n_short, es_max;
-  const uint16_t *col_ptr, *col_rows, *row_ptr, *row_edges, *edge_col;
+  const uint16_t *col_ptr, *col_rows, *row_ptr;
+  const uint32_t* row_ent;  // CSR entry: CSC edge id | (column << 16)
   const float* llr;
+};
+
+// Compressed state of one check node: two smallest |input|, the edge holding
+// the smallest (low 16 bits of ac) and flags (bit 16: sign parity xor s_j,
+// bit 17: exactly one active input).
+struct __align__(16) CNState {
+  float m1, m2;
+  uint32_t ac, pad;
 };
 
 struct BranchTrace {
@@ -38,29 +47,34 @@ struct StepTrace {
   int16_t n_agg, n_peel;
 };
 
+// Result of one decision path in the path-per-CTA launch (global scratch).
+__host__ __device__ inline size_t path_result_bytes(int sw) { return (16 + 4 * (size_t)sw + 15) & ~(size_t)15; }
+
 // Shared-memory layout of one CTA (byte offsets), identical on host and device.
 struct Layout {
   // persistent
-  unsigned sbits, cbits, sel, s_colptr, s_colrows, s_rowptr, s_rowedges, s_edgecol, s_llr, s_vdeg,
-      rowcnt, res_status, res_pm, res_ebits, misc;
+  unsigned sbits, cbits, sel, s_colptr, s_colrows, s_rowptr, s_rowent, s_llr, s_vdeg, rowcnt,
+      res_status, res_pm, res_ebits, red, misc;
+  // window graph staged in shared memory (path mode only; 0 bytes otherwise)
+  unsigned g_colptr, g_colrows, g_rowptr, g_rowent, g_llr, g_bytes;
   unsigned U;  // start of the union region
   // pre-BP (relative to U)
-  unsigned p_post, p_key, p_min1, p_min2, p_amin, p_cfl, p_sign, p_par, p_sort, p_end;
-  // one branch slot (relative to the slot base)
-  unsigned b_post, b_acc, b_hfl, b_status, b_sign, b_min1, b_min2, b_amin, b_cfl, b_deg, b_sp,
-      b_par, b_unsat, b_size;
+  unsigned p_post, p_key, p_cns, p_sign, p_par, p_sort, p_end;
+  // one path slot (relative to the slot base)
+  unsigned b_post, b_acc, b_hfl, b_status, b_sign, b_cns, b_deg, b_sp, b_par, b_unsat, b_size;
   unsigned total;
-  int rw, cw, sw, sortn;
+  int rw, cw, sw, sortn, nslots;
 };
 
 __host__ __device__ inline unsigned al16(unsigned x) { return (x + 15u) & ~15u; }
 
 __host__ __device__ inline Layout make_layout(int nr, int nc, int ne, int ns, int es, int nb,
-                                              int nwarps) {
+                                              int nslots, bool stage_graph = false) {
   Layout L{};
   L.rw = (nr + 31) / 32;
   L.cw = (nc + 31) / 32;
   L.sw = (ns + 31) / 32;
+  L.nslots = nslots;
   int sn = 1;
   while (sn < nc) sn <<= 1;
   L.sortn = sn;
@@ -71,23 +85,29 @@ __host__ __device__ inline Layout make_layout(int nr, int nc, int ne, int ns, in
   L.s_colptr = o; o = al16(o + 2u * (ns + 1));
   L.s_colrows = o; o = al16(o + 2u * es);
   L.s_rowptr = o; o = al16(o + 2u * (nr + 1));
-  L.s_rowedges = o; o = al16(o + 2u * es);
-  L.s_edgecol = o; o = al16(o + 2u * es);
+  L.s_rowent = o; o = al16(o + 4u * es);
   L.s_llr = o; o = al16(o + 4u * ns);
   L.s_vdeg = o; o = al16(o + 1u * ns);
   L.rowcnt = o; o = al16(o + 4u * (nr + 1));
   L.res_status = o; o = al16(o + 4u * nb);
   L.res_pm = o; o = al16(o + 8u * nb);
   L.res_ebits = o; o = al16(o + 4u * L.sw * nb);
+  L.red = o; o = al16(o + 16u * 32);
   L.misc = o; o = al16(o + 64u);
+  const unsigned g0 = o;
+  if (stage_graph) {
+    L.g_colptr = o; o = al16(o + 2u * (nc + 1));
+    L.g_colrows = o; o = al16(o + 2u * ne);
+    L.g_rowptr = o; o = al16(o + 2u * (nr + 1));
+    L.g_rowent = o; o = al16(o + 4u * ne);
+    L.g_llr = o; o = al16(o + 4u * nc);
+  }
+  L.g_bytes = o - g0;
   L.U = o;
   unsigned u = 0;
   L.p_post = u; u = al16(u + 4u * nc);
   L.p_key = u; u = al16(u + 4u * nc);
-  L.p_min1 = u; u = al16(u + 4u * nr);
-  L.p_min2 = u; u = al16(u + 4u * nr);
-  L.p_amin = u; u = al16(u + 2u * nr);
-  L.p_cfl = u; u = al16(u + 1u * nr);
+  L.p_cns = u; u = al16(u + 16u * nr);
   L.p_sign = u; u = al16(u + 1u * ne);
   L.p_par = u; u = al16(u + 8u * L.rw);
   L.p_sort = u; u = al16(u + 8u * sn);
@@ -98,16 +118,13 @@ __host__ __device__ inline Layout make_layout(int nr, int nc, int ne, int ns, in
   L.b_hfl = b; b = al16(b + 1u * ns);
   L.b_status = b; b = al16(b + 1u * ns);
   L.b_sign = b; b = al16(b + 1u * es);
-  L.b_min1 = b; b = al16(b + 4u * nr);
-  L.b_min2 = b; b = al16(b + 4u * nr);
-  L.b_amin = b; b = al16(b + 2u * nr);
-  L.b_cfl = b; b = al16(b + 1u * nr);
+  L.b_cns = b; b = al16(b + 16u * nr);
   L.b_deg = b; b = al16(b + 4u * nr);
   L.b_sp = b; b = al16(b + 4u * L.rw);
   L.b_par = b; b = al16(b + 8u * L.rw);
   L.b_unsat = b; b = al16(b + 4u * L.rw);
   L.b_size = b;
-  unsigned ub = L.p_end > b * (unsigned)nwarps ? L.p_end : b * (unsigned)nwarps;
+  unsigned ub = L.p_end > b * (unsigned)nslots ? L.p_end : b * (unsigned)nslots;
   L.total = L.U + ub;
   return L;
 }

@@ -48,15 +48,23 @@ struct qd_dem {
 
 namespace {
 
+// Launch shapes of the decode kernel: shot mode (persistent CTAs of
+// kShotWarps warps, one warp per decision path) and path mode (one CTA of
+// kPathThreads threads per (shot, path)).
+constexpr int kShotWarps = 8;
+constexpr int kPathThreads = 512;
+constexpr long long kPathModeMaxShots = 64;
+
 struct WinGpu {
   qd::WindowHost h;
   qd::WinDev dv{};
-  qd::Layout L{};
+  qd::Layout L{};   // shot mode
+  qd::Layout Lp{};  // path mode
   void* d_graph = nullptr;
   int* d_ccptr = nullptr;  // committed columns: CSR of their global detector ids
   int* d_ccdet = nullptr;
   uint32_t* d_ccobs = nullptr;
-  int threads = 0, grid_per_sm = 1;
+  int grid_per_sm = 1;
 };
 
 template <class T>
@@ -85,7 +93,10 @@ struct qd_decoder {
   qd::KParams kp{};
   long long max_shots = 0;
   std::vector<WinGpu> wins;
-  int corr_words = 0, dmx = 0, ns_max = 0, sm_count = 0;
+  int corr_words = 0, dmx = 0, ns_max = 0, sm_count = 0, sw_max = 0;
+  int launch_mode = 0;  // 0 automatic, 1 shot mode, 2 path mode
+  char* d_path_res = nullptr;
+  int* d_arrive = nullptr;
   size_t trace_bytes = 0, smem_max = 0;
   int* d_work = nullptr;
   long long* d_counters = nullptr;
@@ -170,6 +181,8 @@ qd_status qd_decoder_destroy(qd_decoder* dec) {
     cudaFree(w.d_ccobs);
   }
   cudaFree(dec->d_work);
+  cudaFree(dec->d_path_res);
+  cudaFree(dec->d_arrive);
   cudaFree(dec->d_counters);
   cudaFree(dec->d_corr);
   cudaFree(dec->d_det);
@@ -232,7 +245,6 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
   QD_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
 
   const int nwin = qd::n_windows(dem->h, p->W, p->F);
-  const int nwarps = std::min(16, std::max(4, k.nb));
   dec->wins.resize(nwin);
   for (int w = 0; w < nwin; ++w) {
     WinGpu& g = dec->wins[w];
@@ -240,31 +252,32 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
     const auto& h = g.h;
     dec->corr_words = std::max(dec->corr_words, (h.n_cols + 31) / 32);
     dec->ns_max = std::max(dec->ns_max, h.n_short);
-    g.L = qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, k.nb, nwarps);
-    g.threads = 32 * nwarps;
-    if (g.L.total > (unsigned)optin) {
+    dec->sw_max = std::max(dec->sw_max, (h.n_short + 31) / 32);
+    g.L = qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, k.nb, kShotWarps);
+    g.Lp = qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, k.nb, 1, true);
+    if (g.L.total > (unsigned)optin || g.Lp.total > (unsigned)optin) {
       set_error("qd_decoder_create: window " + std::to_string(w) + " needs " +
-                std::to_string(g.L.total) + " B of shared memory (limit " + std::to_string(optin) + ")");
+                std::to_string(std::max(g.L.total, g.Lp.total)) + " B of shared memory (limit " +
+                std::to_string(optin) + ")");
       return QD_EUNSUPPORTED;
     }
-    dec->smem_max = std::max<size_t>(dec->smem_max, g.L.total);
+    dec->smem_max = std::max<size_t>(dec->smem_max, std::max(g.L.total, g.Lp.total));
     // graph arrays in one allocation
     size_t o_cp = 0, o_cr = o_cp + 2 * h.col_ptr.size(), o_rp = o_cr + 2 * h.col_rows.size(),
-           o_re = o_rp + 2 * h.row_ptr.size(), o_ec = o_re + 2 * h.row_edges.size(),
-           o_ll = (o_ec + 2 * h.edge_col.size() + 15) & ~(size_t)15, tot = o_ll + 4 * h.llr.size();
+           o_re = (o_rp + 2 * h.row_ptr.size() + 15) & ~(size_t)15, o_ll = o_re + 4 * h.row_ent.size(),
+           tot = o_ll + 4 * h.llr.size();
     std::vector<char> blob(tot);
     memcpy(blob.data() + o_cp, h.col_ptr.data(), 2 * h.col_ptr.size());
     memcpy(blob.data() + o_cr, h.col_rows.data(), 2 * h.col_rows.size());
     memcpy(blob.data() + o_rp, h.row_ptr.data(), 2 * h.row_ptr.size());
-    memcpy(blob.data() + o_re, h.row_edges.data(), 2 * h.row_edges.size());
-    memcpy(blob.data() + o_ec, h.edge_col.data(), 2 * h.edge_col.size());
+    memcpy(blob.data() + o_re, h.row_ent.data(), 4 * h.row_ent.size());
     memcpy(blob.data() + o_ll, h.llr.data(), 4 * h.llr.size());
     QD_CK(cudaMalloc(&g.d_graph, tot));
     QD_CK(cudaMemcpy(g.d_graph, blob.data(), tot, cudaMemcpyHostToDevice));
     char* b = (char*)g.d_graph;
     g.dv = qd::WinDev{h.n_rows, h.n_cols, h.n_edges, h.row0, h.n_short, h.short_edges_max,
                       (const uint16_t*)(b + o_cp), (const uint16_t*)(b + o_cr), (const uint16_t*)(b + o_rp),
-                      (const uint16_t*)(b + o_re), (const uint16_t*)(b + o_ec), (const float*)(b + o_ll)};
+                      (const uint32_t*)(b + o_re), (const float*)(b + o_ll)};
     // committed columns: their full detector sets and observables
     std::vector<int> cc_ptr(1, 0), cc_det;
     std::vector<uint32_t> cc_obs;
@@ -281,11 +294,15 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
   QD_CK(qd::set_decode_smem(dec->smem_max));
   for (auto& g : dec->wins) {
     int blocks = 0;
-    QD_CK(qd::decode_occupancy(g.threads, g.L.total, &blocks));
+    QD_CK(qd::decode_occupancy(0, 32 * kShotWarps, g.L.total, &blocks));
     g.grid_per_sm = std::max(1, blocks);
   }
   dec->trace_bytes = qd::trace_bytes_per_shot(k.nb, dec->dmx, dec->ns_max);
   QD_CK(cudaMalloc(&dec->d_work, sizeof(int) * (nwin + 1)));
+  const long long pm_shots = std::min<long long>(max_shots, kPathModeMaxShots);
+  QD_CK(cudaMalloc(&dec->d_path_res, qd::path_result_bytes(dec->sw_max) * k.nb * pm_shots));
+  QD_CK(cudaMalloc(&dec->d_arrive, sizeof(int) * pm_shots));
+  QD_CK(cudaMemset(dec->d_arrive, 0, sizeof(int) * pm_shots));
   QD_CK(cudaMalloc(&dec->d_counters, sizeof(long long) * 4));
   QD_CK(cudaMemset(dec->d_counters, 0, sizeof(long long) * 4));
   const int dw = (dem->h.n_det + 31) / 32;
@@ -335,12 +352,23 @@ qd_status qd_decode_windows(qd_decoder* dec, int k, const uint32_t* det_bits, in
   if (n_shots == 0) return QD_OK;
   const WinGpu& g = dec->wins[k];
   cudaStream_t st = (cudaStream_t)stream;
+  const int dw = (dec->dem->h.n_det + 31) / 32;
+  // path mode while the batch leaves most SMs idle in shot mode
+  bool path_mode = dec->launch_mode == 2;
+  if (dec->launch_mode == 0) path_mode = n_shots * 4 <= dec->sm_count;
+  if (path_mode && n_shots > std::min<long long>(dec->max_shots, kPathModeMaxShots)) path_mode = false;
+  if (path_mode) {
+    QD_CK(qd::launch_decode(1, (int)(n_shots * dec->kp.nb), kPathThreads, g.Lp.total, st, dec->kp, g.dv, g.Lp,
+                            det_bits, dw, n_shots, win_correction, dec->corr_words, status, (char*)trace,
+                            dec->trace_bytes, dec->dmx, dec->ns_max, nullptr, dec->d_counters, dec->d_path_res,
+                            dec->d_arrive, dec->sw_max));
+    return QD_OK;
+  }
   QD_CK(cudaMemsetAsync(dec->d_work + k, 0, sizeof(int), st));
-  long long grid = std::min<long long>(n_shots, (long long)dec->sm_count * g.grid_per_sm);
-  QD_CK(qd::launch_decode((int)grid, g.threads, g.L.total, st, dec->kp, g.dv, g.L, det_bits,
-                          (dec->dem->h.n_det + 31) / 32, n_shots, win_correction, dec->corr_words, status,
-                          (char*)trace, dec->trace_bytes, dec->dmx, dec->ns_max, dec->d_work + k,
-                          dec->d_counters));
+  const long long grid = std::min<long long>(n_shots, (long long)dec->sm_count * g.grid_per_sm);
+  QD_CK(qd::launch_decode(0, (int)grid, 32 * kShotWarps, g.L.total, st, dec->kp, g.dv, g.L, det_bits, dw, n_shots,
+                          win_correction, dec->corr_words, status, (char*)trace, dec->trace_bytes, dec->dmx,
+                          dec->ns_max, dec->d_work + k, dec->d_counters, nullptr, nullptr, dec->sw_max));
   return QD_OK;
 }
 
@@ -401,6 +429,13 @@ qd_status qd_decode_shots_host(qd_decoder* dec, const uint32_t* det_bits, const 
   if (fail) QD_CK(cudaMemcpyAsync(fail, dec->d_fail, sizeof(uint32_t) * n_shots, cudaMemcpyDeviceToHost, st));
   if (n_fail) QD_CK(cudaMemcpyAsync(n_fail, dec->d_nfail, sizeof(long long), cudaMemcpyDeviceToHost, st));
   QD_CK(cudaStreamSynchronize(st));
+  return QD_OK;
+}
+
+qd_status qd_decoder_set_launch(qd_decoder* dec, int mode) {
+  QD_REQ(dec, "null argument");
+  QD_REQ(mode >= 0 && mode <= 2, "qd_decoder_set_launch: mode must be 0, 1 or 2");
+  dec->launch_mode = mode;
   return QD_OK;
 }
 
@@ -478,8 +513,9 @@ extern "C" qd_status qd_decode_commit_static(qd_decoder* dec, int k, uint32_t* d
   QD_CK(cudaMemsetAsync(base, 0, kStaticHeader, st));
   long long grid = std::min<long long>(n_shots, (long long)dec->sm_count * g.grid_per_sm);
   const int dw = (dec->dem->h.n_det + 31) / 32;
-  QD_CK(qd::launch_decode((int)grid, g.threads, g.L.total, st, dec->kp, g.dv, g.L, det_bits, dw, n_shots,
-                          corr, dec->corr_words, nullptr, nullptr, 0, dec->dmx, dec->ns_max, work, stats));
+  QD_CK(qd::launch_decode(0, (int)grid, 32 * kShotWarps, g.L.total, st, dec->kp, g.dv, g.L, det_bits, dw,
+                          n_shots, corr, dec->corr_words, nullptr, nullptr, 0, dec->dmx, dec->ns_max, work, stats,
+                          nullptr, nullptr, dec->sw_max));
   const int w = dec->dem->h.w;
   QD_CK(qd::launch_commit(st, g.h.n_commit, g.d_ccptr, g.d_ccdet, g.d_ccobs, dec->corr_words, corr, n_shots,
                           det_bits, dw, obs_pred, residue_fail, g.h.r0 * w, g.h.commit_b1 * w));

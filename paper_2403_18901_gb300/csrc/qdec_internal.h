@@ -21,8 +21,8 @@ struct WindowHost {
   int commit_b1 = 0;      // committed blocks are [r0, commit_b1)
   std::vector<int> gcols;                 // window column -> DEM column
   std::vector<uint16_t> col_ptr, col_rows;  // CSC over window rows (ascending)
-  std::vector<uint16_t> row_ptr, row_edges; // CSR listing CSC edge ids
-  std::vector<uint16_t> edge_col;           // CSC edge id -> window column
+  std::vector<uint16_t> row_ptr;            // CSR row pointers
+  std::vector<uint32_t> row_ent;            // CSR entries: CSC edge id | (window column << 16)
   std::vector<float> llr;
 };
 
@@ -48,11 +48,11 @@ bool build_window(const DemHost& d, int W, int F, int k, bool shorten, WindowHos
 
 size_t trace_bytes_per_shot(int nb, int dmx, int ns_max);
 cudaError_t set_decode_smem(size_t bytes);
-cudaError_t decode_occupancy(int threads, size_t smem, int* blocks);
-cudaError_t launch_decode(int grid, int threads, size_t smem, cudaStream_t st, const KParams& P,
-                          const WinDev& W, const Layout& L, const uint32_t* det, int det_words,
-                          long long n, uint32_t* corr, int corr_words, int32_t* status, char* trace,
-                          size_t tr_bytes, int dmx, int ns_max, int* work, long long* counters);
+cudaError_t decode_occupancy(int mode, int threads, size_t smem, int* blocks);
+cudaError_t launch_decode(int mode, int grid, int threads, size_t smem, cudaStream_t st, const KParams& P,
+                          const WinDev& W, const Layout& L, const uint32_t* det, int det_words, long long n,
+                          uint32_t* corr, int corr_words, int32_t* status, char* trace, size_t tr_bytes, int dmx,
+                          int ns_max, int* work, long long* counters, char* path_res, int* arrive, int sw_max);
 cudaError_t launch_sample(cudaStream_t st, int n_cols, const uint32_t* thr, const int* cptr,
                           const int* cdet, const uint32_t* cobs, int det_words,
                           unsigned long long seed, unsigned long long off, long long n, uint32_t* det,

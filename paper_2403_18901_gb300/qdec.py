@@ -73,6 +73,7 @@ _SIGS = {
     "qd_decode_all": (_I, [_VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP]),
     "qd_decode_shots_host": (_I, [_VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP]),
     "qd_decode_commit_static": (_I, [_VP, _I, _VP, _I64, _VP, _VP, _VP]),
+    "qd_decoder_set_launch": (_I, [_VP, _I]),
     "qd_decoder_counters": (_I, [_VP, _VP]),
     "qd_decoder_reset_counters": (_I, [_VP, _VP]),
 }
@@ -233,6 +234,10 @@ class Decoder:
         _check(lib().qd_decode_shots_host(self.h, _ptr(det), _ptr(obs), n, _ptr(pred), _ptr(fail),
                                           _ptr(nf), _stream(stream)))
         return pred, fail, int(nf[0])
+
+    def set_launch(self, mode):
+        """0 automatic, 1 shot mode (throughput), 2 path mode (latency)."""
+        _check(lib().qd_decoder_set_launch(self.h, int(mode)))
 
     def counters(self):
         out = np.zeros(4, np.int64)

@@ -61,12 +61,14 @@ def test_sampler_bit_exact(key, R, n, off):
     assert (_u32(obs) == oo).all()
 
 
-def _pipeline(key, R, p, params, n, seed, trace_windows=()):
+def _pipeline(key, R, p, params, n, seed, trace_windows=(), mode=0):
     """Run both implementations window by window on the same oracle-sampled
-    shots; compare everything.  Returns (oracle fail, gpu fail)."""
+    shots; compare everything.  mode: launch shape (0 automatic, 1 one warp per
+    decision path, 2 one CTA per decision path).  Returns (oracle fail, gpu fail)."""
     o = oracle_dem(key, p, R)
     d = qdec.Dem(CODES[key], p, R)
     dec = qdec.Decoder(d, params, max_shots=n)
+    dec.set_launch(mode)
     det0, obs0 = o.sample(seed, 0, n)
     ofail, opred, ocorr = o.run_shots(params, det0, obs0, threads=8, want_corr=True)
     det = _to_dev(det0)
@@ -148,7 +150,15 @@ def test_bb72_low_error_mode_and_k0():
 
 def test_bb144_pipeline_bit_exact():
     params = preset("configured", k_guess=4)
-    _pipeline("144", 12, 0.003, params, n=150, seed=144_003, trace_windows=(0, 5, 10))
+    _pipeline("144", 12, 0.003, params, n=150, seed=144_003, trace_windows=(0, 5, 10), mode=1)
+
+
+@pytest.mark.parametrize("key,R,k,pname,n", [("144", 12, 4, "configured", 40), ("72", 6, 3, "paper", 64),
+                                             ("144", 12, 5, "paper", 24)])
+def test_path_per_cta_launch_bit_exact(key, R, k, pname, n):
+    """The latency launch (one CTA per decision path, last CTA decides)."""
+    _pipeline(key, R, 0.003, preset(pname, k_guess=k), n=n, seed=5150 + n,
+              trace_windows=(0, 1, 2, 3), mode=2)
 
 
 def test_bb144_paper_preset_k5_bit_exact():
