@@ -251,6 +251,54 @@ qd_status qd_decode_shots_host(qd_decoder* dec, const uint32_t* det_bits, const 
 qd_status qd_decode_commit_static(qd_decoder* dec, int k, uint32_t* det_bits, int64_t n_shots,
                                   uint32_t* obs_pred, uint32_t* residue_fail, qd_stream_t stream);
 
+/*
+ * Learned weighted min-sum for window k (no counterpart in the paper: the
+ * fixed normalisation alpha of Eq. (1) becomes a per-edge, per-iteration
+ * weight).  w: device [T][n_edges of window k], FP32, indexed by the window's
+ * CSC edge order; iteration t (counted from message initialisation, in the
+ * pre-BP and in every decision path) uses row min(t, T) - 1, and an edge of
+ * the shortened matrix uses the weights of its full-window edge.  The caller
+ * owns w and keeps it valid while the decoder uses it; NULL restores alpha.
+ */
+qd_status qd_decoder_set_weights(qd_decoder* dec, int k, const float* w, int T);
+
+/*
+ * Training the learned weighted min-sum of window k (no counterpart in the
+ * paper).  A training sample is a window syndrome s = H_win e with every
+ * window column firing independently with its prior (the syndrome a window
+ * sees when every earlier window committed the truth).  The model is T
+ * unrolled flooding iterations of weighted min-sum on the full window, from
+ * v2c = Lambda, with w[t][e] in place of alpha in Eq. (1); the loss is the
+ * soft-syndrome binary cross entropy at t = T: P(check j odd) =
+ * (1 - prod_{i in N(j)} tanh(Lambda_i^(T) / 2)) / 2 against s_j, averaged over
+ * the window's checks.  Gradients come from a hand-written adjoint of the
+ * unrolled iterations, recomputed from message checkpoints every `ckpt`
+ * iterations.
+ *   qd_wms_create  allocates per-CTA scratch; T, ckpt as above
+ *   qd_wms_info    out[6] = rows, columns, edges, T, ckpt, syndrome words
+ *   qd_wms_sample  synd: device [n][syndrome words]; counter-based like
+ *                  qd_sample_shots, with word 3 of the counter = 1 + k
+ *   qd_wms_loss    loss: device [n] per-sample loss; post: device [n][cols]
+ *                  posteriors at t = T, or NULL
+ *   qd_wms_grad    grad_w: device [T][edges], ACCUMULATES grad_scale * dL/dw
+ *                  summed over the n samples (L = per-sample loss); loss as
+ *                  above or NULL
+ *   qd_adam_step   in-place Adam update of n parameters (bias-corrected,
+ *                  step >= 1); g, m1, m2 device arrays of n floats
+ * All device pointers are caller-owned; calls are asynchronous on the stream.
+ */
+typedef struct qd_wms qd_wms;
+qd_status qd_wms_create(const qd_decoder* dec, int k, int T, int ckpt, qd_wms** out);
+qd_status qd_wms_destroy(qd_wms* m);
+qd_status qd_wms_info(const qd_wms* m, int out[6]);
+qd_status qd_wms_sample(qd_wms* m, uint64_t seed, uint64_t offset, int64_t n, uint32_t* synd, qd_stream_t stream);
+qd_status qd_wms_loss(qd_wms* m, const float* w, const uint32_t* synd, int64_t n, float* loss, float* post,
+                      qd_stream_t stream);
+qd_status qd_wms_grad(qd_wms* m, const float* w, const uint32_t* synd, int64_t n, float grad_scale, float* grad_w,
+                      float* loss, qd_stream_t stream);
+qd_status qd_adam_step(float* w, const float* g, float* m1, float* m2, int64_t n, float lr, float beta1, float beta2,
+                       float eps, int step, qd_stream_t stream);
+
 /* Launch shape of qd_decode_windows (results are identical in every shape):
  * 0 automatic (default): path mode for batches that leave most SMs idle,
  * otherwise shot mode; 1 shot mode: persistent CTAs, one warp per decision

@@ -49,7 +49,20 @@ typedef struct {
   int *edge_col;
   float* llr;
   int* vdeg; /* static column weight */
+  /* learned weights: w[(t-1) * wE + efull[e]] for iteration t (NULL: alpha) */
+  const float* w;
+  int wT, wE;
+  const int* efull; /* edge -> full-window edge (NULL: identity) */
 } graph_t;
+
+/* The CN->VN multiplier of Eq. (1) at iteration t for edge e: alpha, or the
+ * learned weight w[min(t, T)][e] of the full-window edge. */
+static inline float edge_weight(const graph_t* g, float alpha, int t, int e) {
+  if (!g->w) return alpha;
+  int tt = t < g->wT ? t : g->wT;
+  int ef = g->efull ? g->efull[e] : e;
+  return g->w[(size_t)(tt - 1) * g->wE + ef];
+}
 
 static void graph_init(graph_t* g, int nr, int nc, const int* col_ptr, const int* col_rows,
                        const float* llr) {
@@ -66,6 +79,10 @@ static void graph_init(graph_t* g, int nr, int nc, const int* col_ptr, const int
   g->row_edges = malloc(sizeof(int) * (g->ne > 0 ? g->ne : 1));
   g->edge_col = malloc(sizeof(int) * (g->ne > 0 ? g->ne : 1));
   g->vdeg = malloc(sizeof(int) * (nc > 0 ? nc : 1));
+  g->w = NULL;
+  g->wT = 0;
+  g->wE = 0;
+  g->efull = NULL;
   for (int e = 0; e < g->ne; ++e) g->row_ptr[col_rows[e] + 1]++;
   for (int j = 0; j < nr; ++j) g->row_ptr[j + 1] += g->row_ptr[j];
   int* fill = malloc(sizeof(int) * (nr > 0 ? nr : 1));
@@ -154,7 +171,7 @@ static inline float clipf(float x, float c) {
  * for x < 0 and +1 otherwise.  READING: a CN with a single active VN sends
  * alpha * clip (minimum over the empty set taken as the clip bound).
  */
-static void bp_iteration(const graph_t* g, state_t* s, float alpha, float clip) {
+static void bp_iteration(const graph_t* g, state_t* s, float alpha, float clip, int t) {
   for (int j = 0; j < g->nr; ++j) {
     float min1 = INFINITY, min2 = INFINITY;
     int amin = -1, neg = 0, na = 0;
@@ -179,7 +196,7 @@ static void bp_iteration(const graph_t* g, state_t* s, float alpha, float clip) 
       float m = (e == amin) ? min2 : min1;
       if (na == 1) m = clip;
       int sgn = neg ^ (s->v2c[e] < 0.0f) ^ s->sp[j];
-      float mag = alpha * m;
+      float mag = edge_weight(g, alpha, t, e) * m;
       s->c2v[e] = sgn ? -mag : mag;
     }
   }
@@ -348,7 +365,7 @@ static void run_branch(const graph_t* g, const uint8_t* synd, const qdo_params* 
   for (int D = 1; D <= dmax; ++D) {
     out->depth = D;
     for (int it = 0; it < P->iters_per_step; ++it) {
-      bp_iteration(g, s, P->alpha, P->clip);
+      bp_iteration(g, s, P->alpha, P->clip, out->iters + 1);
       out->iters++;
       if (converged(g, s)) {
         out->status = BR_CONVERGED;
@@ -391,7 +408,7 @@ int qdo_bp_run(int n_rows, int n_cols, const int* col_ptr, const int* col_rows, 
   state_reset(&s, &g, synd);
   int it = 0, conv = 0;
   while (it < max_iter) {
-    bp_iteration(&g, &s, alpha, clip);
+    bp_iteration(&g, &s, alpha, clip, it + 1);
     ++it;
     if (converged(&g, &s)) {
       conv = 1;
@@ -513,12 +530,16 @@ static int decode_window_impl(const window_t* wd, const qdo_params* P, const uin
                               qdo_step_record* steps, int8_t* fstat) {
   graph_t g;
   graph_init(&g, wd->nr, wd->nc, wd->col_ptr, wd->col_rows, wd->llr);
+  const float* W = (P->wts && P->wT > 0) ? P->wts[wd->k] : NULL;
+  g.w = W;
+  g.wT = P->wT;
+  g.wE = wd->ne;
   state_t s;
   state_alloc(&s, &g);
   state_reset(&s, &g, synd);
   int conv = 0, it = 0;
   for (it = 0; it < P->n_pre;) {
-    bp_iteration(&g, &s, P->alpha, P->clip);
+    bp_iteration(&g, &s, P->alpha, P->clip, it + 1);
     ++it;
     if (converged(&g, &s)) { conv = 1; break; }
   }
@@ -545,17 +566,25 @@ static int decode_window_impl(const window_t* wd, const qdo_params* P, const uin
   /* shortened graph: kept columns in rank order, all window rows */
   int* cp = malloc(sizeof(int) * (ns + 1));
   int* cr = malloc(sizeof(int) * (wd->ne + 1));
+  int* ef = malloc(sizeof(int) * (wd->ne + 1));
   float* ll = malloc(sizeof(float) * (ns + 1));
   cp[0] = 0;
   for (int k = 0; k < ns; ++k) {
     int c = sel[k];
     int n = 0;
-    for (int e = wd->col_ptr[c]; e < wd->col_ptr[c + 1]; ++e) cr[cp[k] + n++] = wd->col_rows[e];
+    for (int e = wd->col_ptr[c]; e < wd->col_ptr[c + 1]; ++e) {
+      ef[cp[k] + n] = e; /* the shortened edge keeps its full-window edge's weights */
+      cr[cp[k] + n++] = wd->col_rows[e];
+    }
     cp[k + 1] = cp[k] + n;
     ll[k] = wd->llr[c];
   }
   graph_t gs;
   graph_init(&gs, wd->nr, ns, cp, cr, ll);
+  gs.w = W;
+  gs.wT = P->wT;
+  gs.wE = wd->ne;
+  gs.efull = ef;
   uint8_t* es = malloc(ns + 1);
   int best = gdg_all(&gs, synd, P, es, br, steps, fstat);
   memset(corr, 0, wd->nc);
@@ -566,6 +595,7 @@ static int decode_window_impl(const window_t* wd, const qdo_params* P, const uin
   graph_free(&gs);
   free(cp);
   free(cr);
+  free(ef);
   free(ll);
   free(sel);
   graph_free(&g);

@@ -26,7 +26,8 @@ class QdoParams(C.Structure):
                 ("shorten", C.c_int), ("clip", C.c_float), ("pa_main", C.c_float),
                 ("pa_other", C.c_float), ("pb_main", C.c_float), ("pb_other", C.c_float),
                 ("pb_d1", C.c_float), ("pc", C.c_float), ("pd", C.c_float),
-                ("pc_max_depth", C.c_int), ("n_unsat_min", C.c_int)]
+                ("pc_max_depth", C.c_int), ("n_unsat_min", C.c_int),
+                ("wts", C.POINTER(C.c_void_p)), ("wT", C.c_int)]
 
 
 class QdoBranch(C.Structure):
@@ -91,10 +92,29 @@ def make_code(code):
     return c
 
 
-def make_params(p):
+def make_params(p, weights=None):
+    """weights: None or {window index: float32 array [T][n_edges of the window]}."""
     q = QdoParams()
     for name, _ in QdoParams._fields_:
+        if name in ("wts", "wT"):
+            continue
         setattr(q, name, p[name])
+    q.wT = 0
+    q.wts = None
+    if weights:
+        T = {w.shape[0] for w in weights.values()}
+        assert len(T) == 1
+        n = max(weights) + 1
+        arr = (C.c_void_p * n)()
+        keep = []
+        for k in range(n):
+            if k in weights:
+                a = np.ascontiguousarray(weights[k], np.float32)
+                keep.append(a)
+                arr[k] = a.ctypes.data
+        q.wts = C.cast(arr, C.POINTER(C.c_void_p))
+        q.wT = T.pop()
+        q._keep = (arr, keep)
     return q
 
 
@@ -238,13 +258,13 @@ class OracleDEM:
         return det, obs
 
     # ---- decoding ----
-    def decode_window(self, params, k, synd, trace=False):
+    def decode_window(self, params, k, synd, trace=False, weights=None):
         W, F = params["W"], params["F"]
         win = self.window(W, F, k)
         synd = np.ascontiguousarray(synd, np.uint8)
         corr = np.zeros(win["n_cols"], np.uint8)
         info = np.zeros(4, np.int32)
-        P = make_params(params)
+        P = make_params(params, weights)
         nb = 1 << params["k_guess"]
         dmx = max(params["d_max_main"], params["d_max_other"])
         if trace:
@@ -267,7 +287,7 @@ class OracleDEM:
         return corr, dict(prebp_converged=bool(info[0]), winner=int(info[1]),
                           n_short=int(info[2]), prebp_iters=int(info[3])), tr
 
-    def run_shots(self, params, det, obs, threads=1, want_corr=False):
+    def run_shots(self, params, det, obs, threads=1, want_corr=False, weights=None):
         """Sliding-window decode of every shot.  Returns (fail, obs_pred, corr_words)."""
         det = np.ascontiguousarray(det, np.uint32)
         obs = np.ascontiguousarray(obs, np.uint32)
@@ -278,7 +298,7 @@ class OracleDEM:
         maxc = max(self.window(params["W"], params["F"], k)["n_cols"] for k in range(nwin))
         cw = (maxc + 31) // 32
         corr = np.zeros((n, nwin, cw), np.uint32) if want_corr else None
-        P = make_params(params)
+        P = make_params(params, weights)
 
         def work(a, b):
             lib().qdo_run_shots(self.h, C.byref(P), _ptr(det[a:b]), _ptr(obs[a:b]), b - a,

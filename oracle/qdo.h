@@ -44,6 +44,12 @@ typedef struct {
   float pa_main, pa_other, pb_main, pb_other, pb_d1, pc, pd; /* Alg. 3 */
   int pc_max_depth;      /* P_C test applies for D <= this (4)                 */
   int n_unsat_min;       /* unsatisfied-neighbour count of Alg. 3 (3)          */
+  /* Learned weighted min-sum (no counterpart in the paper; alpha of Eq. (1)
+   * replaced by w[t][e]): wts[k] is window k's array [wT][n_edges] over the
+   * full-window edges (CSC order), or NULL for plain alpha.  Iteration t
+   * counts from the last message (re)initialisation; t > wT uses row wT. */
+  const float* const* wts;
+  int wT;
 } qdo_params;
 
 /* Per-branch summary of one GDG decision path. */

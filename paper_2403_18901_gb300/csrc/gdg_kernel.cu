@@ -50,6 +50,13 @@ __device__ __forceinline__ float c2v_msg(float alpha, float clip, const CNState&
 
 __device__ __forceinline__ uint32_t bit_of(const uint32_t* w, int j) { return (w[j >> 5] >> (j & 31)) & 1u; }
 
+// Multiplier of Eq. (1) at iteration t >= 1 for full-window edge ef: alpha, or
+// the learned weight w[min(t, T)][ef].
+__device__ __forceinline__ float edge_weight(const float* wts, int wT, int wE, float alpha, int t, int ef) {
+  if (!wts) return alpha;
+  return wts[(size_t)((t < wT ? t : wT) - 1) * wE + ef];
+}
+
 // order-preserving map of a float to uint32 (-0 and +0 equal)
 __device__ __forceinline__ uint32_t ordkey(float f) {
   if (f == 0.0f) f = 0.0f;
@@ -228,6 +235,9 @@ struct ShortG {
   const float* llr;
   const uint8_t* vdeg;
   const uint32_t* sbits;
+  const uint16_t* efull;  // short edge -> full-window edge (learned weights)
+  const float* wts;
+  int wT, wE;
 };
 
 struct Slot {
@@ -382,7 +392,8 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
             if (pv[u] != pv[u]) continue;  // stale message of a decimated VN
             const int e = (int)(ent[u] & 0xFFFFu);
             ++visits;
-            const float v = first ? pv[u] : clipf(__fsub_rn(pv[u], c2v_msg(P.alpha, P.clip, oc, e, sg[u])), P.clip);
+            const float wprev = G.wts ? edge_weight(G.wts, G.wT, G.wE, P.alpha, iters, G.efull[e]) : P.alpha;
+            const float v = first ? pv[u] : clipf(__fsub_rn(pv[u], c2v_msg(wprev, P.clip, oc, e, sg[u])), P.clip);
             const float a = fabsf(v);
             if (a < m1) {
               m2 = m1;
@@ -412,7 +423,10 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
           float c[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u)
-            if (e0 + u < ee) c[u] = c2v_msg(P.alpha, P.clip, B.cns[G.colrows[e0 + u]], e0 + u, B.sign[e0 + u]);
+            if (e0 + u < ee) {
+              const float wt = G.wts ? edge_weight(G.wts, G.wT, G.wE, P.alpha, iters + 1, G.efull[e0 + u]) : P.alpha;
+              c[u] = c2v_msg(wt, P.clip, B.cns[G.colrows[e0 + u]], e0 + u, B.sign[e0 + u]);
+            }
 #pragma unroll
           for (int u = 0; u < 8; ++u)
             if (e0 + u < ee) p = __fadd_rn(p, c[u]);  // ascending check order (Eq. (2))
@@ -656,7 +670,8 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
         for (int u = 0; u < 4; ++u) {
           if (q + u >= end) break;
           const int e = (int)(ent[u] & 0xFFFFu);
-          const float v = (t == 1) ? pv[u] : clipf(__fsub_rn(pv[u], c2v_msg(P.alpha, P.clip, oc, e, sg[u])), P.clip);
+          const float wprev = (t > 1 && W.wts) ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t - 1, e) : P.alpha;
+          const float v = (t == 1) ? pv[u] : clipf(__fsub_rn(pv[u], c2v_msg(wprev, P.clip, oc, e, sg[u])), P.clip);
           const float a = fabsf(v);
           if (a < m1) {
             m2 = m1;
@@ -684,7 +699,10 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
         float c[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u)
-          if (e0 + u < ee) c[u] = c2v_msg(P.alpha, P.clip, cns[W.col_rows[e0 + u]], e0 + u, sign[e0 + u]);
+          if (e0 + u < ee) {
+            const float wt = W.wts ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t, e0 + u) : P.alpha;
+            c[u] = c2v_msg(wt, P.clip, cns[W.col_rows[e0 + u]], e0 + u, sign[e0 + u]);
+          }
 #pragma unroll
         for (int u = 0; u < 8; ++u)
           if (e0 + u < ee) p = __fadd_rn(p, c[u]);  // ascending check order (Eq. (2))
@@ -778,12 +796,14 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
   }
   __syncthreads();
   for (int k = tid; k <= n_short; k += NT) scp[k] = (uint16_t)tmp[k];
+  uint16_t* sef = (uint16_t*)(sm + L.s_efull);
   for (int k = tid; k < n_short; k += NT) {
     const int c = sel[k];
     int o = tmp[k];
     for (int e = W.col_ptr[c]; e < W.col_ptr[c + 1]; ++e, ++o) {
       const int r = W.col_rows[e];
       scr[o] = (uint16_t)r;
+      sef[o] = (uint16_t)e;  // the shortened edge keeps its full-window edge's weights
       atomicAdd(&rc[r], 1);
     }
   }
@@ -804,12 +824,13 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
   return false;
 }
 
-__device__ __forceinline__ ShortG short_graph(char* sm, const Layout& L, int nr, int ns) {
-  return ShortG{nr, ns, L.rw,
+__device__ __forceinline__ ShortG short_graph(char* sm, const Layout& L, const WinDev& W, int ns) {
+  return ShortG{W.n_rows, ns, L.rw,
                 (const uint16_t*)(sm + L.s_colptr), (const uint16_t*)(sm + L.s_colrows),
                 (const uint16_t*)(sm + L.s_rowptr), (const uint32_t*)(sm + L.s_rowent),
                 (const float*)(sm + L.s_llr),       (const uint8_t*)(sm + L.s_vdeg),
-                (const uint32_t*)(sm + L.sbits)};
+                (const uint32_t*)(sm + L.sbits),    (const uint16_t*)(sm + L.s_efull),
+                W.wts, W.wT, W.n_edges};
 }
 
 __device__ __forceinline__ PathOut trace_out(const DecodeArgs& A, char* tr, int id) {
@@ -873,7 +894,7 @@ __global__ void __launch_bounds__(256, 2) decode_shot_kernel(DecodeArgs A) {
     int winner = -1;
     const int n_short = conv ? 0 : A.W.n_short;
     if (!conv) {
-      const ShortG G = short_graph(sm, L, A.W.n_rows, n_short);
+      const ShortG G = short_graph(sm, L, A.W, n_short);
       const Slot B = make_slot(sm + L.U + (size_t)warp * L.b_size, L);
       const WarpGrp g{lane};
       while (true) {
@@ -950,7 +971,7 @@ __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
     return;
   }
   const int n_short = A.W.n_short;
-  const ShortG G = short_graph(sm, L, A.W.n_rows, n_short);
+  const ShortG G = short_graph(sm, L, A.W, n_short);
   const Slot B = make_slot(sm + L.U, L);
   const CtaGrp g{tid, (int)blockDim.x, sm + L.red};
   const size_t rb = path_result_bytes(A.sw_max);

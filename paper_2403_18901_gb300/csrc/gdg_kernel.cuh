@@ -27,6 +27,19 @@ struct WinDev {
   const uint16_t *col_ptr, *col_rows, *row_ptr;
   const uint32_t* row_ent;  // CSR entry: CSC edge id | (column << 16)
   const float* llr;
+  // learned weighted min-sum: wts[(min(t, wT) - 1) * n_edges + e] replaces
+  // alpha at iteration t (counted from message initialisation); NULL = alpha
+  const float* wts;
+  int wT;
+};
+
+// A window's Tanner graph for the learned weighted min-sum (training kernels).
+struct WmsGraph {
+  int nr, nc, ne, rw, T, ckpt;
+  const uint16_t *col_ptr, *col_rows, *row_ptr;
+  const uint32_t* row_ent;  // CSC edge id | column << 16
+  const float* llr;
+  float clip;
 };
 
 // Compressed state of one check node: two smallest |input|, the edge holding
@@ -53,7 +66,7 @@ __host__ __device__ inline size_t path_result_bytes(int sw) { return (16 + 4 * (
 // Shared-memory layout of one CTA (byte offsets), identical on host and device.
 struct Layout {
   // persistent
-  unsigned sbits, cbits, sel, s_colptr, s_colrows, s_rowptr, s_rowent, s_llr, s_vdeg, rowcnt,
+  unsigned sbits, cbits, sel, s_colptr, s_colrows, s_rowptr, s_rowent, s_llr, s_vdeg, s_efull, rowcnt,
       res_status, res_pm, res_ebits, red, misc;
   // window graph staged in shared memory (path mode only; 0 bytes otherwise)
   unsigned g_colptr, g_colrows, g_rowptr, g_rowent, g_llr, g_bytes;
@@ -88,6 +101,7 @@ __host__ __device__ inline Layout make_layout(int nr, int nc, int ne, int ns, in
   L.s_rowent = o; o = al16(o + 4u * es);
   L.s_llr = o; o = al16(o + 4u * ns);
   L.s_vdeg = o; o = al16(o + 1u * ns);
+  L.s_efull = o; o = al16(o + 2u * es);
   L.rowcnt = o; o = al16(o + 4u * (nr + 1));
   L.res_status = o; o = al16(o + 4u * nb);
   L.res_pm = o; o = al16(o + 8u * nb);

@@ -277,7 +277,7 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
     char* b = (char*)g.d_graph;
     g.dv = qd::WinDev{h.n_rows, h.n_cols, h.n_edges, h.row0, h.n_short, h.short_edges_max,
                       (const uint16_t*)(b + o_cp), (const uint16_t*)(b + o_cr), (const uint16_t*)(b + o_rp),
-                      (const uint32_t*)(b + o_re), (const float*)(b + o_ll)};
+                      (const uint32_t*)(b + o_re), (const float*)(b + o_ll), nullptr, 0};
     // committed columns: their full detector sets and observables
     std::vector<int> cc_ptr(1, 0), cc_det;
     std::vector<uint32_t> cc_obs;
@@ -432,6 +432,15 @@ qd_status qd_decode_shots_host(qd_decoder* dec, const uint32_t* det_bits, const 
   return QD_OK;
 }
 
+qd_status qd_decoder_set_weights(qd_decoder* dec, int k, const float* w, int T) {
+  QD_REQ(dec, "null argument");
+  QD_REQ(k >= 0 && k < (int)dec->wins.size(), "qd_decoder_set_weights: window out of range");
+  QD_REQ(w == nullptr || T >= 1, "qd_decoder_set_weights: T must be >= 1");
+  dec->wins[k].dv.wts = w;
+  dec->wins[k].dv.wT = w ? T : 0;
+  return QD_OK;
+}
+
 qd_status qd_decoder_set_launch(qd_decoder* dec, int mode) {
   QD_REQ(dec, "null argument");
   QD_REQ(mode >= 0 && mode <= 2, "qd_decoder_set_launch: mode must be 0, 1 or 2");
@@ -521,3 +530,109 @@ extern "C" qd_status qd_decode_commit_static(qd_decoder* dec, int k, uint32_t* d
                           det_bits, dw, obs_pred, residue_fail, g.h.r0 * w, g.h.commit_b1 * w));
   return QD_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Learned weighted min-sum: training on window samples.
+struct qd_wms {
+  qd::WmsGraph G{};
+  int k = 0;
+  uint32_t* d_thr = nullptr;
+  float* d_scratch = nullptr;
+  size_t scratch_per_cta = 0;
+  int* d_work = nullptr;
+  int grid = 0;
+  size_t smem = 0;
+};
+
+extern "C" {
+
+qd_status qd_wms_create(const qd_decoder* dec, int k, int T, int ckpt, qd_wms** out) {
+  QD_REQ(dec && out, "qd_wms_create: null argument");
+  QD_REQ(k >= 0 && k < (int)dec->wins.size(), "qd_wms_create: window out of range");
+  QD_REQ(T >= 1 && T <= 1000 && ckpt >= 1 && ckpt <= T, "qd_wms_create: need 1 <= ckpt <= T");
+  std::unique_ptr<qd_wms> m(new (std::nothrow) qd_wms());
+  if (!m) return QD_ENOMEM;
+  const WinGpu& g = dec->wins[k];
+  m->k = k;
+  m->G = qd::WmsGraph{g.h.n_rows, g.h.n_cols, g.h.n_edges, (g.h.n_rows + 31) / 32, T, ckpt,
+                      g.dv.col_ptr, g.dv.col_rows, g.dv.row_ptr, g.dv.row_ent, g.dv.llr, dec->P.clip};
+  std::vector<uint32_t> thr(g.h.n_cols);
+  for (int c = 0; c < g.h.n_cols; ++c) thr[c] = dec->dem->h.col_thr[g.h.gcols[c]];
+  QD_CK(upload(&m->d_thr, thr));
+  m->smem = qd::wms_smem_bytes(m->G.ne, m->G.nc, m->G.rw);
+  int optin = 0, dev = 0;
+  QD_CK(cudaGetDevice(&dev));
+  QD_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (m->smem > (size_t)optin) {
+    set_error("qd_wms_create: window too large for shared memory");
+    return QD_EUNSUPPORTED;
+  }
+  QD_CK(qd::wms_set_smem(m->smem));
+  int blocks = 0;
+  QD_CK(qd::wms_occupancy(m->smem, &blocks));
+  m->grid = dec->sm_count * std::max(1, blocks);
+  m->scratch_per_cta = qd::wms_scratch_per_cta(m->G.ne, T, ckpt);
+  QD_CK(cudaMalloc(&m->d_scratch, sizeof(float) * m->scratch_per_cta * m->grid));
+  QD_CK(cudaMalloc(&m->d_work, sizeof(int)));
+  *out = m.release();
+  return QD_OK;
+}
+
+qd_status qd_wms_destroy(qd_wms* m) {
+  if (!m) return QD_OK;
+  cudaFree(m->d_thr);
+  cudaFree(m->d_scratch);
+  cudaFree(m->d_work);
+  delete m;
+  return QD_OK;
+}
+
+qd_status qd_wms_info(const qd_wms* m, int out[6]) {
+  QD_REQ(m && out, "null argument");
+  out[0] = m->G.nr;
+  out[1] = m->G.nc;
+  out[2] = m->G.ne;
+  out[3] = m->G.T;
+  out[4] = m->G.ckpt;
+  out[5] = m->G.rw;
+  return QD_OK;
+}
+
+qd_status qd_wms_sample(qd_wms* m, uint64_t seed, uint64_t offset, int64_t n, uint32_t* synd, qd_stream_t stream) {
+  QD_REQ(m && synd && n >= 0, "qd_wms_sample: bad argument");
+  QD_CK(qd::launch_wms_sample((cudaStream_t)stream, m->G, m->d_thr, seed, offset, n, 1u + (unsigned)m->k, synd));
+  return QD_OK;
+}
+
+static qd_status wms_run(qd_wms* m, const float* w, const uint32_t* synd, int64_t n, int backward, float scale,
+                         float* grad_w, float* loss, float* post, qd_stream_t stream) {
+  QD_REQ(m && w && synd && n >= 0, "qd_wms: bad argument");
+  if (n == 0) return QD_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  QD_CK(cudaMemsetAsync(m->d_work, 0, sizeof(int), st));
+  const int grid = (int)std::min<long long>(n, m->grid);
+  QD_CK(qd::launch_wms(st, grid, m->smem, m->G, w, synd, n, backward, scale, grad_w, loss, post, m->d_scratch,
+                       m->scratch_per_cta, m->d_work));
+  return QD_OK;
+}
+
+qd_status qd_wms_loss(qd_wms* m, const float* w, const uint32_t* synd, int64_t n, float* loss, float* post,
+                      qd_stream_t stream) {
+  QD_REQ(loss, "qd_wms_loss: loss is required");
+  return wms_run(m, w, synd, n, 0, 0.0f, nullptr, loss, post, stream);
+}
+
+qd_status qd_wms_grad(qd_wms* m, const float* w, const uint32_t* synd, int64_t n, float grad_scale, float* grad_w,
+                      float* loss, qd_stream_t stream) {
+  QD_REQ(grad_w, "qd_wms_grad: grad_w is required");
+  return wms_run(m, w, synd, n, 1, grad_scale, grad_w, loss, nullptr, stream);
+}
+
+qd_status qd_adam_step(float* w, const float* g, float* m1, float* m2, int64_t n, float lr, float beta1, float beta2,
+                       float eps, int step, qd_stream_t stream) {
+  QD_REQ(w && g && m1 && m2 && n >= 0 && step >= 1, "qd_adam_step: bad argument");
+  QD_CK(qd::launch_adam((cudaStream_t)stream, w, g, m1, m2, n, lr, beta1, beta2, eps, step));
+  return QD_OK;
+}
+
+}  // extern "C"

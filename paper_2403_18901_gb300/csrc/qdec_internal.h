@@ -40,6 +40,7 @@ struct DemHost {
 struct KParams;
 struct WinDev;
 struct Layout;
+struct WmsGraph;
 
 // Build the merged DEM (backward sensitivity sweep over the circuit).
 bool build_dem_host(const qd_bb_code& code, const qd_noise& noise, DemHost& out);
@@ -63,5 +64,17 @@ cudaError_t launch_commit(cudaStream_t st, int n_commit, const int* cptr, const 
                           int b1);
 cudaError_t launch_evaluate(cudaStream_t st, const uint32_t* pred, const uint32_t* obs,
                             const uint32_t* resid, long long n, uint32_t* fail, long long* n_fail);
+
+size_t wms_smem_bytes(int ne, int nc, int rw);
+size_t wms_scratch_per_cta(int ne, int T, int ckpt);
+cudaError_t wms_set_smem(size_t bytes);
+cudaError_t wms_occupancy(size_t smem, int* blocks);
+cudaError_t launch_wms(cudaStream_t st, int grid, size_t smem, const WmsGraph& G, const float* w, const uint32_t* synd,
+                       long long n, int backward, float grad_scale, float* grad_w, float* loss, float* post,
+                       float* scratch, size_t scratch_per_cta, int* work);
+cudaError_t launch_wms_sample(cudaStream_t st, const WmsGraph& G, const uint32_t* thr, unsigned long long seed,
+                              unsigned long long off, long long n, unsigned domain, uint32_t* synd);
+cudaError_t launch_adam(cudaStream_t st, float* w, const float* g, float* m, float* v, long long n, float lr,
+                        float b1, float b2, float eps, int step);
 
 }  // namespace qd

@@ -74,6 +74,15 @@ _SIGS = {
     "qd_decode_shots_host": (_I, [_VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP]),
     "qd_decode_commit_static": (_I, [_VP, _I, _VP, _I64, _VP, _VP, _VP]),
     "qd_decoder_set_launch": (_I, [_VP, _I]),
+    "qd_decoder_set_weights": (_I, [_VP, _I, _VP, _I]),
+    "qd_wms_create": (_I, [_VP, _I, _I, _I, C.POINTER(_VP)]),
+    "qd_wms_destroy": (_I, [_VP]),
+    "qd_wms_info": (_I, [_VP, _VP]),
+    "qd_wms_sample": (_I, [_VP, _U64, _U64, _I64, _VP, _VP]),
+    "qd_wms_loss": (_I, [_VP, _VP, _VP, _I64, _VP, _VP, _VP]),
+    "qd_wms_grad": (_I, [_VP, _VP, _VP, _I64, C.c_float, _VP, _VP, _VP]),
+    "qd_adam_step": (_I, [_VP, _VP, _VP, _VP, _I64, C.c_float, C.c_float, C.c_float, C.c_float, _I,
+                          _VP]),
     "qd_decoder_counters": (_I, [_VP, _VP]),
     "qd_decoder_reset_counters": (_I, [_VP, _VP]),
 }
@@ -234,6 +243,18 @@ class Decoder:
         _check(lib().qd_decode_shots_host(self.h, _ptr(det), _ptr(obs), n, _ptr(pred), _ptr(fail),
                                           _ptr(nf), _stream(stream)))
         return pred, fail, int(nf[0])
+
+    def set_weights(self, k, w):
+        """w: CUDA float32 tensor [T][n_edges of window k] (kept referenced), or None."""
+        if w is None:
+            _check(lib().qd_decoder_set_weights(self.h, k, None, 0))
+            self._w = getattr(self, "_w", {})
+            self._w.pop(k, None)
+            return
+        assert w.is_cuda and w.dtype.is_floating_point and w.dim() == 2
+        self._w = getattr(self, "_w", {})
+        self._w[k] = w
+        _check(lib().qd_decoder_set_weights(self.h, k, _ptr(w), w.shape[0]))
 
     def set_launch(self, mode):
         """0 automatic, 1 shot mode (throughput), 2 path mode (latency)."""

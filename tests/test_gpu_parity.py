@@ -61,7 +61,7 @@ def test_sampler_bit_exact(key, R, n, off):
     assert (_u32(obs) == oo).all()
 
 
-def _pipeline(key, R, p, params, n, seed, trace_windows=(), mode=0):
+def _pipeline(key, R, p, params, n, seed, trace_windows=(), mode=0, weights=None):
     """Run both implementations window by window on the same oracle-sampled
     shots; compare everything.  mode: launch shape (0 automatic, 1 one warp per
     decision path, 2 one CTA per decision path).  Returns (oracle fail, gpu fail)."""
@@ -69,8 +69,11 @@ def _pipeline(key, R, p, params, n, seed, trace_windows=(), mode=0):
     d = qdec.Dem(CODES[key], p, R)
     dec = qdec.Decoder(d, params, max_shots=n)
     dec.set_launch(mode)
+    if weights is not None:
+        for k, w in weights.items():
+            dec.set_weights(k, torch.from_numpy(w).cuda())
     det0, obs0 = o.sample(seed, 0, n)
-    ofail, opred, ocorr = o.run_shots(params, det0, obs0, threads=8, want_corr=True)
+    ofail, opred, ocorr = o.run_shots(params, det0, obs0, threads=8, want_corr=True, weights=weights)
     det = _to_dev(det0)
     obs = _to_dev(obs0)
     corr = torch.zeros((n, dec.corr_words), dtype=torch.int32, device="cuda")
@@ -79,6 +82,7 @@ def _pipeline(key, R, p, params, n, seed, trace_windows=(), mode=0):
     resid = torch.zeros(n, dtype=torch.int32, device="cuda")
     fail = torch.zeros(n, dtype=torch.int32, device="cuda")
     host_det = det0.copy()
+    n_gdg = 0
     for k in range(dec.n_windows):
         win = dec.window_info(k)
         owin = o.window(params["W"], params["F"], k)
@@ -94,10 +98,9 @@ def _pipeline(key, R, p, params, n, seed, trace_windows=(), mode=0):
             trn = tr.cpu().numpy()
             st = status.cpu().numpy()
             s_all = _bits(host_det, o.n_det)
-            n_gdg = 0
             for sh in range(n):
                 synd = s_all[sh, win["r0"] * o.w: win["r0"] * o.w + win["n_rows"]]
-                oc, oinfo, otr = o.decode_window(params, k, synd, trace=True)
+                oc, oinfo, otr = o.decode_window(params, k, synd, trace=True, weights=weights)
                 gt = dec.parse_trace(trn[sh])
                 assert gt["head"][0] == int(oinfo["prebp_converged"])
                 assert gt["head"][3] == oinfo["prebp_iters"]
@@ -118,13 +121,14 @@ def _pipeline(key, R, p, params, n, seed, trace_windows=(), mode=0):
                         grec = gt["steps"][b][D]
                         assert (grec["g"], grec["value"], grec["n_agg"], grec["n_peel"]) == rec, (sh, b, D)
                     assert (gt["final_status"][b][:ns] == otr["final_status"][b]).all(), (sh, b)
-            assert n_gdg > 0, "no window ran GDG; pick another seed"
         assert (g[:, :cw_o] == ocorr[:, k, :]).all(), f"window {k}: corrections differ"
         dec.commit(k, corr, n, det, pred, resid)
         gbits = _bits(g, win["n_cols"])
         for sh in range(n):
             _apply_commit(host_det[sh], o, owin, gbits[sh])
     torch.cuda.synchronize()
+    if trace_windows:
+        assert n_gdg > 0, "no traced window ran GDG; pick another seed"
     assert (_u32(det) == host_det).all(), "committed syndromes differ"
     qdec._check(qdec.lib().qd_evaluate(qdec._ptr(pred), qdec._ptr(obs), qdec._ptr(resid), n,
                                        qdec._ptr(fail), None, qdec._stream(None)))
@@ -234,3 +238,19 @@ def test_repeatable():
     a = dec.decode_host(det0, obs0)
     b = dec.decode_host(det0, obs0)
     assert (a[0] == b[0]).all() and (a[1] == b[1]).all()
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_learned_weights_bit_exact(mode):
+    """Weighted min-sum (per-edge, per-iteration weights in place of alpha) in
+    the pre-BP and in every decision path, both launch shapes."""
+    o = oracle_dem("72", 0.003, 6)
+    params = preset("configured", k_guess=3)
+    rng = np.random.default_rng(123)
+    T = 7  # iterations past T reuse row T, exercised by the 100-iteration pre-BP
+    weights = {}
+    for k in range(o.n_windows(3, 1)):
+        ne = o.window(3, 1, k)["n_edges"]
+        weights[k] = rng.uniform(0.45, 0.9, size=(T, ne)).astype(np.float32)
+    _pipeline("72", 6, 0.003, params, n=64 if mode == 2 else 200, seed=4242,
+              trace_windows=(0, 1, 2, 3, 4), mode=mode, weights=weights)
