@@ -16,6 +16,7 @@ data path); rank 0 prints the JSON line with the max-over-ranks time.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -50,7 +51,23 @@ def parse():
     ap.add_argument("--latency-shots", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--seed", type=int, default=144_003)
+    ap.add_argument("--train-steps", type=int, default=60,
+                    help="Adam steps per window type for the learned weights (0: skip)")
+    ap.add_argument("--train-batch", type=int, default=4096)
     return ap.parse_args()
+
+
+def wilson(k, n, z=1.96):
+    if n == 0:
+        return (0.0, 1.0)
+    ph = k / n
+    c = (ph + z * z / (2 * n)) / (1 + z * z / n)
+    h = z * math.sqrt(ph * (1 - ph) / n + z * z / (4 * n * n)) / (1 + z * z / n)
+    return (max(0.0, c - h), min(1.0, c + h))
+
+
+def per_round(P, R=ROUNDS):
+    return 1.0 - (1.0 - P) ** (1.0 / R)
 
 
 def dist_env():
@@ -217,36 +234,38 @@ def main():
         work.copy_(pristine[b][0])
         dec.decode_all(work, pristine[b][1], B, pred, fail, nfail)
 
-    for b in range(args.warmup):
-        step(b)
-    torch.cuda.synchronize()
-    dec.reset_counters()
-    nfail.zero_()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    t_wall0 = time.perf_counter()
-    with ClockSampler(local) as clk:
-        for s in range(args.steps):
-            flush.fill_(s)  # L2 flushed between timed steps (outside the events)
-            ev[s][0].record(stream)
-            step(args.warmup + s)
-            ev[s][1].record(stream)
+    def timed(local_idx):
+        """Warm-up + exactly K timed steps; returns (seconds, failures, clocks)."""
+        for b in range(args.warmup):
+            step(b)
         torch.cuda.synchronize()
+        dec.reset_counters()
+        nfail.zero_()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local_idx) as clk:
+            for s_ in range(args.steps):
+                flush.fill_(s_)  # L2 flushed between timed steps (outside the events)
+                ev[s_][0].record(stream)
+                step(args.warmup + s_)
+                ev[s_][1].record(stream)
+            torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
+        if world > 1:
+            tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            t = float(tt.item())
+        return t, int(nfail.item()), clk.summary()
+
+    t_wall0 = time.perf_counter()
+    tot_s, failures, clocks = timed(local)
     t_wall = time.perf_counter() - t_wall0
-    if world > 1:
-        torch.distributed.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_s = sum(step_ms) / 1000.0
-    if world > 1:
-        t = torch.tensor([tot_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_s = float(t.item())
     counters = dec.counters()
-    failures = int(nfail.item())
-    clocks = clk.summary()
     windows = B * nwin * args.steps * world
     value = windows / tot_s
 
@@ -276,6 +295,35 @@ def main():
     alu_peak = n_sm * 128 * sm_mhz * 1e6 / 1e12  # T op/s, one FP32 op per lane per clock
     achieved = OPS_PER_EDGE_ITER * edge_iters / kern_s / 1e12
 
+    # ---- learned weighted min-sum: train on the GPU, then time the same shots ----
+    learned = None
+    if args.train_steps > 0:
+        from paper_2403_18901_gb300 import learn
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        logs = []
+        wts = learn.train(dem, dec, alpha=params["alpha"], T=25, ckpt=5, batch=args.train_batch,
+                          steps=args.train_steps, lr=1e-3, seed=2_403_189_01, log=logs.append)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        for k, w in wts.items():
+            dec.set_weights(k, w)
+        tot_l, fail_l, clocks_l = timed(local)
+        for k in wts:
+            dec.set_weights(k, None)
+        n_types = len({id(w) for w in wts.values()})
+        learned = {"train": {"steps_per_window_type": args.train_steps, "batch": args.train_batch,
+                             "window_types": n_types,
+                             "samples": args.train_steps * args.train_batch * n_types,
+                             "seconds": train_s, "T": 25, "checkpoint_every": 5, "adam_lr": 1e-3,
+                             "loss_log": logs},
+                   "value": windows / tot_l, "ms_per_step": 1000 * tot_l / args.steps,
+                   "clocks": clocks_l}
+    if world > 1:
+        fl = torch.tensor([failures], device="cuda")
+        torch.distributed.all_reduce(fl)
+        failures = int(fl[0].item())
+
     line = None
     if rank == 0:
         # ---- end to end: host buffers through qd_decode_shots_host ----
@@ -300,37 +348,59 @@ def main():
         # ---- latency mode: one shot per window step, CUDA-graph replay ----
         L = max(1, args.latency_shots)
         ldec = qdec.Decoder(dem, params, max_shots=1)
-        ldet = torch.empty((1, dw), dtype=torch.int32, device="cuda")
         lsrc = pristine[args.warmup][0][:L].clone()
-        lcorr = torch.empty((1, ldec.corr_words), dtype=torch.int32, device="cuda")
-        lpred = torch.zeros(1, dtype=torch.int32, device="cuda")
-        lres = torch.zeros(1, dtype=torch.int32, device="cuda")
-        gs = torch.cuda.Stream()
-        graphs = []
-        with torch.cuda.stream(gs):
-            for k in range(nwin):  # warm the launch path before capture
-                ldec.decode_window(k, ldet, 1, lcorr)
-                ldec.commit(k, lcorr, 1, ldet, lpred, lres)
-        torch.cuda.synchronize()
-        for k in range(nwin):
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g, stream=gs):
-                ldec.decode_window(k, ldet, 1, lcorr)
-                ldec.commit(k, lcorr, 1, ldet, lpred, lres)
-            graphs.append(g)
-        lat = []
-        for sidx in range(L):
-            ldet.copy_(lsrc[sidx:sidx + 1])
+
+        def latency(ld):
+            ldet = torch.empty((1, dw), dtype=torch.int32, device="cuda")
+            lcorr = torch.empty((1, ld.corr_words), dtype=torch.int32, device="cuda")
+            lpred = torch.zeros(1, dtype=torch.int32, device="cuda")
+            lres = torch.zeros(1, dtype=torch.int32, device="cuda")
+            gs = torch.cuda.Stream()
+            graphs = []
+            with torch.cuda.stream(gs):
+                for k in range(nwin):  # warm the launch path before capture
+                    ld.decode_window(k, ldet, 1, lcorr)
+                    ld.commit(k, lcorr, 1, ldet, lpred, lres)
+            torch.cuda.synchronize()
             for k in range(nwin):
-                a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record()
-                graphs[k].replay()
-                b2.record()
-                lat.append((a, b2))
-        torch.cuda.synchronize()
-        lat_ms = sorted(a.elapsed_time(b2) for a, b2 in lat)
-        p50 = lat_ms[len(lat_ms) // 2]
-        p99 = lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))]
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=gs):
+                    ld.decode_window(k, ldet, 1, lcorr)
+                    ld.commit(k, lcorr, 1, ldet, lpred, lres)
+                graphs.append(g)
+            lat = []
+            for sidx in range(L):
+                ldet.copy_(lsrc[sidx:sidx + 1])
+                for k in range(nwin):
+                    a = torch.cuda.Event(enable_timing=True)
+                    b2 = torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    graphs[k].replay()
+                    b2.record()
+                    lat.append((a, b2))
+            torch.cuda.synchronize()
+            lat_ms = sorted(a.elapsed_time(b2) for a, b2 in lat)
+            return (lat_ms[len(lat_ms) // 2], lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))],
+                    len(lat_ms))
+
+        p50, p99, n_lat = latency(ldec)
+        n_shots_total = B * args.steps * world
+        if learned is not None:
+            for k, w in wts.items():
+                ldec.set_weights(k, w)
+            lp50, lp99, _ = latency(ldec)
+            learned["latency_ms"] = {"p50": lp50, "p99": lp99}
+            fl_tot = fail_l if world == 1 else None
+            lo, hi = wilson(failures, n_shots_total)
+            llo, lhi = wilson(fail_l, B * args.steps)
+            learned["ler_per_round"] = {
+                "plain": {"failures": failures, "shots": n_shots_total,
+                          "p_L": per_round(failures / n_shots_total),
+                          "wilson95": [per_round(lo), per_round(hi)]},
+                "learned": {"failures": fail_l, "shots": B * args.steps,
+                            "p_L": per_round(fail_l / (B * args.steps)),
+                            "wilson95": [per_round(llo), per_round(lhi)]}}
+            del fl_tot
 
         cpu_rate, cores, cpu_shots, cpu_s = cpu_oracle_rate(params, args.cpu_seconds, args.seed)
         line = {
@@ -345,7 +415,7 @@ def main():
                        "cuda_graph": "latency mode replays one captured graph per window"},
             "shots_per_s": B * args.steps * world / tot_s,
             "logical_failures": failures, "shots_decoded": B * args.steps * world,
-            "latency_ms": {"p50": p50, "p99": p99, "windows": len(lat_ms),
+            "latency_ms": {"p50": p50, "p99": p99, "windows": n_lat,
                            "mode": "1 shot per window step, 16 paths in one CTA"},
             "paper_context": {"worst_case_ms_per_window": 3.0,
                               "hardware": "Intel i9-13900K, multi-threaded"},
@@ -359,6 +429,7 @@ def main():
                                  f"{nwin} launches",
                          "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz "
                                        f"({peak_kind} sm_max_mhz)"},
+            "launch": dec.launch_info(1),
             "edge_iterations_per_window": edge_iters / (B * nwin),
             "gdg_windows_frac": float(kc[3]) / (B * nwin),
             "clocks": clocks,
@@ -367,6 +438,7 @@ def main():
                              "sample": f"{cpu_shots} shots ({cpu_shots * nwin} windows) in "
                                        f"{cpu_s:.1f} s"},
             "wall_s_timed": t_wall,
+            "learned": learned,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

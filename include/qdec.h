@@ -306,6 +306,11 @@ qd_status qd_adam_step(float* w, const float* g, float* m1, float* m2, int64_t n
  * latency, at most 64 shots per call (larger batches fall back to shot mode). */
 qd_status qd_decoder_set_launch(qd_decoder* dec, int mode);
 
+/* Launch plan of window k: out[0] shared bytes per CTA in shot mode,
+ * out[1] its threads, out[2] its CTAs per SM, out[3] shared bytes per CTA in
+ * path mode, out[4] its threads, out[5] SM count. */
+qd_status qd_decoder_launch_info(const qd_decoder* dec, int k, int out[6]);
+
 /* Counters of the last qd_decode_windows call of window k, summed over shots:
  * out[0] pre-BP edge-iterations, out[1] GDG edge-iterations, out[2] windows
  * whose pre-BP converged, out[3] windows that ran GDG.  Synchronous. */

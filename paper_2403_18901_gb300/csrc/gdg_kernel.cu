@@ -142,6 +142,7 @@ __device__ int warp_scan_excl(int* a, int n, int lane) {
 struct WarpGrp {  // one warp
   int rank;
   static constexpr int size = 32;
+  static constexpr bool kWarp = true;
   __device__ void sync() const { __syncwarp(); }
   __device__ bool all(bool p) const { return __all_sync(FULL, p); }
   __device__ bool any(bool p) const { return __any_sync(FULL, p); }
@@ -162,6 +163,7 @@ struct WarpGrp {  // one warp
 
 struct CtaGrp {  // the whole CTA; every member must call every primitive
   int rank, size;
+  static constexpr bool kWarp = false;
   char* red;  // >= 32 * 16 bytes of shared memory
   __device__ void sync() const { __syncthreads(); }
   __device__ bool all(bool p) const { return __syncthreads_and(p) != 0; }
@@ -330,11 +332,14 @@ struct PathOut {
 };
 
 // One decision path of Alg. 2 on the shortened window, run by group g.
-template <class Grp>
+// LW: learned per-edge weights instead of alpha (compiled separately so the
+// plain decoder carries no weight lookups).
+template <bool LW, class Grp>
 __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int id, const Grp& g,
                          const PathOut& out, int dmx) {
   const int nr = G.nr, ns = G.ns, rw = G.rw, R = g.rank, S = g.size;
-  const int tpc = lanes_per_check(S, nr), sub = R & (tpc - 1);
+  // one lane per check for a warp; small lane groups per check for a CTA
+  const int tpc = Grp::kWarp ? 1 : lanes_per_check(S, nr), sub = R & (tpc - 1);
   const int nr_rounds = (nr + S / tpc - 1) / (S / tpc) * (S / tpc);
   const bool mainb = (id == 0);
   const int dmax = mainb ? P.dmax_main : P.dmax_other;
@@ -392,7 +397,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
             if (pv[u] != pv[u]) continue;  // stale message of a decimated VN
             const int e = (int)(ent[u] & 0xFFFFu);
             ++visits;
-            const float wprev = G.wts ? edge_weight(G.wts, G.wT, G.wE, P.alpha, iters, G.efull[e]) : P.alpha;
+            const float wprev = LW ? edge_weight(G.wts, G.wT, G.wE, P.alpha, iters, G.efull[e]) : P.alpha;
             const float v = first ? pv[u] : clipf(__fsub_rn(pv[u], c2v_msg(wprev, P.clip, oc, e, sg[u])), P.clip);
             const float a = fabsf(v);
             if (a < m1) {
@@ -424,7 +429,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
 #pragma unroll
           for (int u = 0; u < 8; ++u)
             if (e0 + u < ee) {
-              const float wt = G.wts ? edge_weight(G.wts, G.wT, G.wE, P.alpha, iters + 1, G.efull[e0 + u]) : P.alpha;
+              const float wt = LW ? edge_weight(G.wts, G.wT, G.wE, P.alpha, iters + 1, G.efull[e0 + u]) : P.alpha;
               c[u] = c2v_msg(wt, P.clip, B.cns[G.colrows[e0 + u]], e0 + u, B.sign[e0 + u]);
             }
 #pragma unroll
@@ -588,6 +593,7 @@ struct DecodeArgs {
 
 // a1 + a2 (+ a3 when not converged): the shared prefix of both launch shapes.
 // Returns true when the pre-BP converged (cbits then hold its decision).
+template <bool LW, bool WIDE>
 __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, long long shot, int* t_run_out) {
   const KParams& P = A.P;
   const Layout& L = A.L;
@@ -620,7 +626,7 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
   __syncthreads();
 
   // ---- a2: pre-BP on the full window ----
-  const int tpc_pre = lanes_per_check(NT, nr), sub_pre = tid & (tpc_pre - 1);
+  const int tpc_pre = WIDE ? lanes_per_check(NT, nr) : 1, sub_pre = tid & (tpc_pre - 1);
   const int nr_rounds = (nr + NT / tpc_pre - 1) / (NT / tpc_pre) * (NT / tpc_pre);
   bool conv = false;
   int t = 0;
@@ -670,7 +676,7 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
         for (int u = 0; u < 4; ++u) {
           if (q + u >= end) break;
           const int e = (int)(ent[u] & 0xFFFFu);
-          const float wprev = (t > 1 && W.wts) ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t - 1, e) : P.alpha;
+          const float wprev = (LW && t > 1) ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t - 1, e) : P.alpha;
           const float v = (t == 1) ? pv[u] : clipf(__fsub_rn(pv[u], c2v_msg(wprev, P.clip, oc, e, sg[u])), P.clip);
           const float a = fabsf(v);
           if (a < m1) {
@@ -700,7 +706,7 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
 #pragma unroll
         for (int u = 0; u < 8; ++u)
           if (e0 + u < ee) {
-            const float wt = W.wts ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t, e0 + u) : P.alpha;
+            const float wt = LW ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t, e0 + u) : P.alpha;
             c[u] = c2v_msg(wt, P.clip, cns[W.col_rows[e0 + u]], e0 + u, sign[e0 + u]);
           }
 #pragma unroll
@@ -869,6 +875,7 @@ __device__ void write_outputs(const DecodeArgs& A, char* sm, long long shot, boo
 }
 
 // ---- shot mode: persistent CTAs of 8 warps, one warp per decision path ----
+template <bool LW>
 __global__ void __launch_bounds__(256, 2) decode_shot_kernel(DecodeArgs A) {
   extern __shared__ __align__(16) char sm[];
   const Layout& L = A.L;
@@ -890,7 +897,7 @@ __global__ void __launch_bounds__(256, 2) decode_shot_kernel(DecodeArgs A) {
     if (shot >= A.n_shots) break;
     char* tr = A.trace ? A.trace + (size_t)shot * A.tr_bytes : nullptr;
     int t_run = 0;
-    const bool conv = window_prefix(A, A.W, sm, shot, &t_run);
+    const bool conv = window_prefix<LW, false>(A, A.W, sm, shot, &t_run);
     int winner = -1;
     const int n_short = conv ? 0 : A.W.n_short;
     if (!conv) {
@@ -906,7 +913,7 @@ __global__ void __launch_bounds__(256, 2) decode_shot_kernel(DecodeArgs A) {
         o.status = &res_status[id];
         o.pm = &res_pm[id];
         o.ebits = res_e + (size_t)id * L.sw;
-        run_path(A.P, G, B, id, g, o, A.dmx);
+        run_path<LW>(A.P, G, B, id, g, o, A.dmx);
       }
       __syncthreads();
       // ---- a8: least path metric, ties to the lowest id ----
@@ -932,6 +939,7 @@ __global__ void __launch_bounds__(256, 2) decode_shot_kernel(DecodeArgs A) {
 }
 
 // ---- path mode: one CTA per (shot, path); the last CTA of a shot decides ----
+template <bool LW>
 __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
   extern __shared__ __align__(16) char sm[];
   const Layout& L = A.L;
@@ -965,7 +973,7 @@ __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
     __syncthreads();
   }
   int t_run = 0;
-  const bool conv = window_prefix(A, W, sm, shot, &t_run);
+  const bool conv = window_prefix<LW, true>(A, W, sm, shot, &t_run);
   if (conv) {
     if (id == 0) write_outputs(A, sm, shot, true, -1, 0, t_run, tr);
     return;
@@ -980,7 +988,7 @@ __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
   o.status = (int*)mine;
   o.pm = (double*)(mine + 8);
   o.ebits = (uint32_t*)(mine + 16);
-  run_path(A.P, G, B, id, g, o, A.dmx);
+  run_path<LW>(A.P, G, B, id, g, o, A.dmx);
   // publish, then count arrivals; the last CTA of the shot reduces
   __threadfence();
   __syncthreads();
@@ -1130,15 +1138,21 @@ __global__ void evaluate_kernel(const uint32_t* __restrict__ pred, const uint32_
 size_t trace_bytes_per_shot(int nb, int dmx, int ns_max) { return dev::trace_bytes(nb, dmx, ns_max); }
 
 cudaError_t set_decode_smem(size_t bytes) {
-  cudaError_t e =
-      cudaFuncSetAttribute(dev::decode_shot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(dev::decode_path_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  const int b = (int)bytes;
+  cudaError_t e = cudaFuncSetAttribute(dev::decode_shot_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(dev::decode_shot_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(dev::decode_path_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(dev::decode_path_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  return e;
 }
 
 cudaError_t decode_occupancy(int mode, int threads, size_t smem, int* blocks) {
-  if (mode == 1) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::decode_path_kernel, threads, smem);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::decode_shot_kernel, threads, smem);
+  if (mode == 1)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::decode_path_kernel<false>, threads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::decode_shot_kernel<false>, threads, smem);
 }
 
 cudaError_t launch_decode(int mode, int grid, int threads, size_t smem, cudaStream_t st, const KParams& P,
@@ -1147,10 +1161,14 @@ cudaError_t launch_decode(int mode, int grid, int threads, size_t smem, cudaStre
                           int ns_max, int* work, long long* counters, char* path_res, int* arrive, int sw_max) {
   const dev::DecodeArgs A{P,     W,        L,     det,      det_words, n,     corr,     corr_words, status,
                           trace, tr_bytes, dmx,   ns_max,   work,      counters, path_res, arrive,     sw_max};
-  if (mode == 1)
-    dev::decode_path_kernel<<<grid, threads, smem, st>>>(A);
-  else
-    dev::decode_shot_kernel<<<grid, threads, smem, st>>>(A);
+  const bool lw = W.wts != nullptr;
+  if (mode == 1) {
+    if (lw) dev::decode_path_kernel<true><<<grid, threads, smem, st>>>(A);
+    else dev::decode_path_kernel<false><<<grid, threads, smem, st>>>(A);
+  } else {
+    if (lw) dev::decode_shot_kernel<true><<<grid, threads, smem, st>>>(A);
+    else dev::decode_shot_kernel<false><<<grid, threads, smem, st>>>(A);
+  }
   return cudaGetLastError();
 }
 

@@ -441,6 +441,19 @@ qd_status qd_decoder_set_weights(qd_decoder* dec, int k, const float* w, int T) 
   return QD_OK;
 }
 
+qd_status qd_decoder_launch_info(const qd_decoder* dec, int k, int out[6]) {
+  QD_REQ(dec && out, "null argument");
+  QD_REQ(k >= 0 && k < (int)dec->wins.size(), "qd_decoder_launch_info: window out of range");
+  const WinGpu& g = dec->wins[k];
+  out[0] = (int)g.L.total;
+  out[1] = 32 * kShotWarps;
+  out[2] = g.grid_per_sm;
+  out[3] = (int)g.Lp.total;
+  out[4] = kPathThreads;
+  out[5] = dec->sm_count;
+  return QD_OK;
+}
+
 qd_status qd_decoder_set_launch(qd_decoder* dec, int mode) {
   QD_REQ(dec, "null argument");
   QD_REQ(mode >= 0 && mode <= 2, "qd_decoder_set_launch: mode must be 0, 1 or 2");

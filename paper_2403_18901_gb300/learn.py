@@ -117,7 +117,7 @@ def train(dem, dec, alpha, T=25, ckpt=5, batch=4096, steps=245, lr=1e-3, seed=2_
             with torch.no_grad():
                 adam_step(w.data, w.grad, m, v, lr, step)
             if log is not None and (step == 1 or step % 50 == 0 or step == steps):
-                log(f"window type {group}: step {step} loss {float(loss):.5f}")
+                log(f"window type {group}: step {step} loss {float(loss.detach()):.5f}")
         wf = w.detach()
         for k in group:
             out[k] = wf

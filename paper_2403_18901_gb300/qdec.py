@@ -74,6 +74,7 @@ _SIGS = {
     "qd_decode_shots_host": (_I, [_VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP]),
     "qd_decode_commit_static": (_I, [_VP, _I, _VP, _I64, _VP, _VP, _VP]),
     "qd_decoder_set_launch": (_I, [_VP, _I]),
+    "qd_decoder_launch_info": (_I, [_VP, _I, _VP]),
     "qd_decoder_set_weights": (_I, [_VP, _I, _VP, _I]),
     "qd_wms_create": (_I, [_VP, _I, _I, _I, C.POINTER(_VP)]),
     "qd_wms_destroy": (_I, [_VP]),
@@ -255,6 +256,12 @@ class Decoder:
         self._w = getattr(self, "_w", {})
         self._w[k] = w
         _check(lib().qd_decoder_set_weights(self.h, k, _ptr(w), w.shape[0]))
+
+    def launch_info(self, k=0):
+        out = np.zeros(6, np.int32)
+        _check(lib().qd_decoder_launch_info(self.h, k, _ptr(out)))
+        return dict(shot_smem=int(out[0]), shot_threads=int(out[1]), shot_ctas_per_sm=int(out[2]),
+                    path_smem=int(out[3]), path_threads=int(out[4]), sms=int(out[5]))
 
     def set_launch(self, mode):
         """0 automatic, 1 shot mode (throughput), 2 path mode (latency)."""
