@@ -951,7 +951,7 @@ __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
   char* tr = A.trace ? A.trace + (size_t)shot * A.tr_bytes : nullptr;
   // stage the window graph in shared memory (one CTA per SM in this mode)
   WinDev W = A.W;
-  {
+  if (L.g_bytes) {
     const WinDev& G = A.W;
     uint16_t* cp = (uint16_t*)(sm + L.g_colptr);
     uint16_t* cr = (uint16_t*)(sm + L.g_colrows);

@@ -48,9 +48,9 @@ struct qd_dem {
 
 namespace {
 
-// Launch shapes of the decode kernel: shot mode (persistent CTAs of
-// kShotWarps warps, one warp per decision path) and path mode (one CTA of
-// kPathThreads threads per (shot, path)).
+// Launch shapes of the decode kernel: shot mode (persistent CTAs of up to
+// kShotWarps warps, one warp per decision path, as many as fit in shared
+// memory) and path mode (one CTA of kPathThreads threads per (shot, path)).
 constexpr int kShotWarps = 8;
 constexpr int kPathThreads = 512;
 constexpr long long kPathModeMaxShots = 64;
@@ -65,6 +65,7 @@ struct WinGpu {
   int* d_ccdet = nullptr;
   uint32_t* d_ccobs = nullptr;
   int grid_per_sm = 1;
+  int shot_warps = kShotWarps;
 };
 
 template <class T>
@@ -253,8 +254,16 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
     dec->corr_words = std::max(dec->corr_words, (h.n_cols + 31) / 32);
     dec->ns_max = std::max(dec->ns_max, h.n_short);
     dec->sw_max = std::max(dec->sw_max, (h.n_short + 31) / 32);
-    g.L = qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, k.nb, kShotWarps);
+    // as many decision-path slots (warps) as fit, then the path-mode layout,
+    // with the window graph staged in shared memory when it fits too
+    for (g.shot_warps = kShotWarps; g.shot_warps > 1; g.shot_warps >>= 1) {
+      g.L = qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, k.nb, g.shot_warps);
+      if (g.L.total <= (unsigned)optin) break;
+    }
+    g.L = qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, k.nb, g.shot_warps);
     g.Lp = qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, k.nb, 1, true);
+    if (g.Lp.total > (unsigned)optin)
+      g.Lp = qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, k.nb, 1, false);
     if (g.L.total > (unsigned)optin || g.Lp.total > (unsigned)optin) {
       set_error("qd_decoder_create: window " + std::to_string(w) + " needs " +
                 std::to_string(std::max(g.L.total, g.Lp.total)) + " B of shared memory (limit " +
@@ -294,7 +303,7 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
   QD_CK(qd::set_decode_smem(dec->smem_max));
   for (auto& g : dec->wins) {
     int blocks = 0;
-    QD_CK(qd::decode_occupancy(0, 32 * kShotWarps, g.L.total, &blocks));
+    QD_CK(qd::decode_occupancy(0, 32 * g.shot_warps, g.L.total, &blocks));
     g.grid_per_sm = std::max(1, blocks);
   }
   dec->trace_bytes = qd::trace_bytes_per_shot(k.nb, dec->dmx, dec->ns_max);
@@ -366,9 +375,9 @@ qd_status qd_decode_windows(qd_decoder* dec, int k, const uint32_t* det_bits, in
   }
   QD_CK(cudaMemsetAsync(dec->d_work + k, 0, sizeof(int), st));
   const long long grid = std::min<long long>(n_shots, (long long)dec->sm_count * g.grid_per_sm);
-  QD_CK(qd::launch_decode(0, (int)grid, 32 * kShotWarps, g.L.total, st, dec->kp, g.dv, g.L, det_bits, dw, n_shots,
-                          win_correction, dec->corr_words, status, (char*)trace, dec->trace_bytes, dec->dmx,
-                          dec->ns_max, dec->d_work + k, dec->d_counters, nullptr, nullptr, dec->sw_max));
+  QD_CK(qd::launch_decode(0, (int)grid, 32 * g.shot_warps, g.L.total, st, dec->kp, g.dv, g.L, det_bits, dw,
+                          n_shots, win_correction, dec->corr_words, status, (char*)trace, dec->trace_bytes,
+                          dec->dmx, dec->ns_max, dec->d_work + k, dec->d_counters, nullptr, nullptr, dec->sw_max));
   return QD_OK;
 }
 
@@ -446,7 +455,7 @@ qd_status qd_decoder_launch_info(const qd_decoder* dec, int k, int out[6]) {
   QD_REQ(k >= 0 && k < (int)dec->wins.size(), "qd_decoder_launch_info: window out of range");
   const WinGpu& g = dec->wins[k];
   out[0] = (int)g.L.total;
-  out[1] = 32 * kShotWarps;
+  out[1] = 32 * g.shot_warps;
   out[2] = g.grid_per_sm;
   out[3] = (int)g.Lp.total;
   out[4] = kPathThreads;
@@ -535,7 +544,7 @@ extern "C" qd_status qd_decode_commit_static(qd_decoder* dec, int k, uint32_t* d
   QD_CK(cudaMemsetAsync(base, 0, kStaticHeader, st));
   long long grid = std::min<long long>(n_shots, (long long)dec->sm_count * g.grid_per_sm);
   const int dw = (dec->dem->h.n_det + 31) / 32;
-  QD_CK(qd::launch_decode(0, (int)grid, 32 * kShotWarps, g.L.total, st, dec->kp, g.dv, g.L, det_bits, dw,
+  QD_CK(qd::launch_decode(0, (int)grid, 32 * g.shot_warps, g.L.total, st, dec->kp, g.dv, g.L, det_bits, dw,
                           n_shots, corr, dec->corr_words, nullptr, nullptr, 0, dec->dmx, dec->ns_max, work, stats,
                           nullptr, nullptr, dec->sw_max));
   const int w = dec->dem->h.w;

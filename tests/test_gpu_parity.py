@@ -254,3 +254,11 @@ def test_learned_weights_bit_exact(mode):
         weights[k] = rng.uniform(0.45, 0.9, size=(T, ne)).astype(np.float32)
     _pipeline("72", 6, 0.003, params, n=64 if mode == 2 else 200, seed=4242,
               trace_windows=(0, 1, 2, 3, 4), mode=mode, weights=weights)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_bb288_bit_exact(mode):
+    """[[288,12,18]]: the shortened window (864 columns) leaves room for fewer
+    decision-path slots per CTA; both launch shapes stay bit-exact."""
+    params = preset("configured", k_guess=4, p=0.002)
+    _pipeline("288", 3, 0.002, params, n=40, seed=288_002, trace_windows=(0, 1), mode=mode)
