@@ -53,6 +53,8 @@ typedef struct {
   const float* w;
   int wT, wE;
   const int* efull; /* edge -> full-window edge (NULL: identity) */
+  int* vblock;      /* block (round) of the column's first detector in the window */
+  const int* wcol;  /* column -> window column (NULL: identity) */
 } graph_t;
 
 /* The CN->VN multiplier of Eq. (1) at iteration t for edge e: alpha, or the
@@ -83,6 +85,8 @@ static void graph_init(graph_t* g, int nr, int nc, const int* col_ptr, const int
   g->wT = 0;
   g->wE = 0;
   g->efull = NULL;
+  g->wcol = NULL;
+  g->vblock = calloc(nc > 0 ? nc : 1, sizeof(int));
   for (int e = 0; e < g->ne; ++e) g->row_ptr[col_rows[e] + 1]++;
   for (int j = 0; j < nr; ++j) g->row_ptr[j + 1] += g->row_ptr[j];
   int* fill = malloc(sizeof(int) * (nr > 0 ? nr : 1));
@@ -98,6 +102,7 @@ static void graph_init(graph_t* g, int nr, int nc, const int* col_ptr, const int
 }
 
 static void graph_free(graph_t* g) {
+  free(g->vblock);
   free(g->col_ptr);
   free(g->col_rows);
   free(g->row_ptr);
@@ -286,6 +291,72 @@ static int agg_dec(const qdo_params* P, const float* h, float L, int D, int main
   return -1;
 }
 
+/*
+ * Learned decimation ranker (no counterpart in the paper; it stands in for
+ * the argmin of Alg. 1).  Parameters are rounded to fixed grids -- W1, W2 to
+ * multiples of 2^-6 in [-2, 2], b1 to multiples of 2^-7 in [-512, 512] (round half to even)
+ * -- and the features of a candidate VN are
+ *   x = (L/4, h0, h1, h2, h3     each rounded to the 1/2 grid within +-63.5,
+ *        #unsatisfied CN neighbours (at most 127), static degree,
+ *        block of the column's first detector within the window (at most 255)),
+ * so that every product and partial sum of the first layer is a multiple of
+ * 2^-7 below 2^13, i.e. exact in FP32 in any summation order.  Hidden unit
+ * u: relu(b1[u] + sum_k W1[u][k] x_k).  The second layer is summed in FP32 in
+ * a fixed order: for q = 0..3, s_q = sum over t = 0..7, c = 0..1 (in that
+ * order) of W2[u] h[u] with u = 8t + 2q + c, starting from 0; score =
+ * ((s_0 + s_1) + (s_2 + s_3)) + b2.
+ */
+typedef struct { float w1[64][8], b1[64], w2[64], b2; } ranker_t;
+
+static float qgrid(float x, float scale, float lim) {
+  float v = rintf(x * scale);
+  if (v > lim) v = lim;
+  if (v < -lim) v = -lim;
+  return v / scale;
+}
+
+static void ranker_quantize(const float* raw, ranker_t* r) {
+  for (int u = 0; u < 64; ++u)
+    for (int k = 0; k < 8; ++k) r->w1[u][k] = qgrid(raw[u * 8 + k], 64.0f, 128.0f);
+  for (int u = 0; u < 64; ++u) r->b1[u] = qgrid(raw[512 + u], 128.0f, 65536.0f);
+  for (int u = 0; u < 64; ++u) r->w2[u] = qgrid(raw[576 + u], 64.0f, 128.0f);
+  r->b2 = raw[640];
+}
+
+static float qfeat(float x) {
+  float v = rintf(2.0f * (x > 63.5f ? 63.5f : (x < -63.5f ? -63.5f : x)));
+  return v * 0.5f;
+}
+
+static float ranker_score(const ranker_t* r, const float* x) {
+  float h[64];
+  for (int u = 0; u < 64; ++u) {
+    double a = r->b1[u];
+    for (int k = 0; k < 8; ++k) a += (double)r->w1[u][k] * (double)x[k]; /* exact */
+    float hf = (float)a;
+    h[u] = hf > 0.0f ? hf : 0.0f;
+  }
+  float sq[4];
+  for (int q = 0; q < 4; ++q) {
+    float acc = 0.0f;
+    for (int t = 0; t < 8; ++t)
+      for (int c = 0; c < 2; ++c) {
+        int u = 8 * t + 2 * q + c;
+        float prod = r->w2[u] * h[u];
+        acc = acc + prod;
+      }
+    sq[q] = acc;
+  }
+  return ((sq[0] + sq[1]) + (sq[2] + sq[3])) + r->b2;
+}
+
+/* Scores of n feature rows x [n][8] under raw parameters (test access). */
+void qdo_ranker_score(const float* raw, const float* x, int n, float* out) {
+  ranker_t r;
+  ranker_quantize(raw, &r);
+  for (int i = 0; i < n; ++i) out[i] = ranker_score(&r, x + 8 * i);
+}
+
 /* Alg. 1, SELECT-VN, with Alg. 3 applied to each candidate outside the low
  * error mode.  Candidates: active VNs of degree >= 3, in index order; strict
  * '<' keeps the lowest index on ties.  f = 1 iff L_min <= 0 (the sign of
@@ -295,7 +366,7 @@ static int agg_dec(const qdo_params* P, const float* h, float L, int D, int main
 static int select_vn(const graph_t* g, state_t* s, const qdo_params* P, int D, int main_branch,
                      int* f_out, int* n_agg) {
   int* nus = calloc(g->nc > 0 ? g->nc : 1, sizeof(int));
-  if (!P->low_error_mode) {
+  if (!P->low_error_mode || P->ranker || P->dump) {
     for (int j = 0; j < g->nr; ++j) {
       int par = s->sp[j];
       for (int q = g->row_ptr[j]; q < g->row_ptr[j + 1]; ++q) {
@@ -308,6 +379,12 @@ static int select_vn(const graph_t* g, state_t* s, const qdo_params* P, int D, i
   }
   float Lmin = INFINITY, Lt = INFINITY;
   int gmin = -1, gt = -1;
+  ranker_t rk;
+  float best = -INFINITY, Lbest = 0.0f;
+  int gbest = -1;
+  if (P->ranker) ranker_quantize(P->ranker, &rk);
+  const int dumping = P->dump && main_branch;
+  const int d0 = dumping ? *P->dump_n : 0;
   *n_agg = 0;
   for (int i = 0; i < g->nc; ++i) {
     if (s->status[i] != -1) continue;
@@ -322,6 +399,31 @@ static int select_vn(const graph_t* g, state_t* s, const qdo_params* P, int D, i
         continue;
       }
     }
+    float x[8] = {qfeat(L * 0.25f), qfeat(h[0]), qfeat(h[1]), qfeat(h[2]), qfeat(h[3]),
+                  (float)(nus[i] > 127 ? 127 : nus[i]), (float)g->vdeg[i],
+                  (float)(g->vblock[i] > 255 ? 255 : g->vblock[i])};
+    if (dumping) {
+      int pos = (*P->dump_n)++;
+      if (pos < P->dump_cap) {
+        qdo_rank_rec* r = &P->dump[pos];
+        memcpy(r->x, x, sizeof(x));
+        r->shot = 0;
+        r->wcol = g->wcol ? g->wcol[i] : i;
+        r->depth = (int16_t)D;
+        r->path = 0;
+        r->flags = L <= 0.0f ? 1 : 0;
+      }
+    }
+    if (P->ranker) {
+      /* READING: the ranker replaces the argmin; ties keep the lowest index */
+      float sc = ranker_score(&rk, x);
+      if (sc > best) {
+        best = sc;
+        gbest = i;
+        Lbest = L;
+      }
+      continue;
+    }
     if (L < Lmin) {
       Lmin = L;
       gmin = i;
@@ -332,12 +434,24 @@ static int select_vn(const graph_t* g, state_t* s, const qdo_params* P, int D, i
     }
   }
   free(nus);
-  if (gt != -1) {
+  int gsel;
+  if (P->ranker) {
+    /* f keeps Alg. 1's rule: 1 iff the selected VN's history sum is <= 0 */
+    *f_out = (gbest != -1 && Lbest <= 0.0f) ? 1 : 0;
+    gsel = gbest;
+  } else if (gt != -1) {
     *f_out = 1;
-    return gt;
+    gsel = gt;
+  } else {
+    *f_out = (gmin != -1 && Lmin <= 0.0f) ? 1 : 0;
+    gsel = gmin;
   }
-  *f_out = (gmin != -1 && Lmin <= 0.0f) ? 1 : 0;
-  return gmin;
+  if (dumping && gsel >= 0) {
+    int w = g->wcol ? g->wcol[gsel] : gsel;
+    for (int q = d0; q < *P->dump_n && q < P->dump_cap; ++q)
+      if (P->dump[q].wcol == w) P->dump[q].flags |= 2;
+  }
+  return gsel;
 }
 
 /* Eq. (5) accumulated in double from the FP32 priors. */
@@ -581,10 +695,12 @@ static int decode_window_impl(const window_t* wd, const qdo_params* P, const uin
   }
   graph_t gs;
   graph_init(&gs, wd->nr, ns, cp, cr, ll);
+  for (int k = 0; k < ns; ++k) gs.vblock[k] = wd->col_rows[wd->col_ptr[sel[k]]] / (wd->nr / wd->nb);
   gs.w = W;
   gs.wT = P->wT;
   gs.wE = wd->ne;
   gs.efull = ef;
+  gs.wcol = sel;
   uint8_t* es = malloc(ns + 1);
   int best = gdg_all(&gs, synd, P, es, br, steps, fstat);
   memset(corr, 0, wd->nc);

@@ -19,6 +19,20 @@ class QdoCode(C.Structure):
                 ("bx", C.c_int * 3), ("by", C.c_int * 3)]
 
 
+def ranker_score(params, x):
+    """Oracle ranker scores of feature rows x [n, 8] (FP32)."""
+    p = np.ascontiguousarray(params, np.float32)
+    x = np.ascontiguousarray(x, np.float32).reshape(-1, 8)
+    out = np.zeros(x.shape[0], np.float32)
+    lib().qdo_ranker_score(_ptr(p), _ptr(x), x.shape[0], _ptr(out))
+    return out
+
+
+# one ranker candidate record (qdo_rank_rec)
+RANK_REC = np.dtype([("x", "<f4", (8,)), ("shot", "<i4"), ("wcol", "<i4"), ("depth", "<i2"),
+                     ("path", "<i2"), ("flags", "<i4")])
+
+
 class QdoParams(C.Structure):
     _fields_ = [("W", C.c_int), ("F", C.c_int), ("alpha", C.c_float), ("n_pre", C.c_int),
                 ("iters_per_step", C.c_int), ("d_max_main", C.c_int), ("d_max_other", C.c_int),
@@ -27,7 +41,8 @@ class QdoParams(C.Structure):
                 ("pa_other", C.c_float), ("pb_main", C.c_float), ("pb_other", C.c_float),
                 ("pb_d1", C.c_float), ("pc", C.c_float), ("pd", C.c_float),
                 ("pc_max_depth", C.c_int), ("n_unsat_min", C.c_int),
-                ("wts", C.POINTER(C.c_void_p)), ("wT", C.c_int)]
+                ("wts", C.POINTER(C.c_void_p)), ("wT", C.c_int), ("ranker", C.c_void_p),
+                ("dump", C.c_void_p), ("dump_n", C.c_void_p), ("dump_cap", C.c_int)]
 
 
 class QdoBranch(C.Structure):
@@ -44,6 +59,7 @@ def lib():
         path = _build.build()
         L = C.CDLL(path)
         P = C.POINTER
+        L.qdo_ranker_score.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
         L.qdo_dem_build.restype = C.c_void_p
         L.qdo_dem_build.argtypes = [P(QdoCode), C.c_double, C.c_int]
         L.qdo_dem_free.argtypes = [C.c_void_p]
@@ -92,13 +108,20 @@ def make_code(code):
     return c
 
 
-def make_params(p, weights=None):
-    """weights: None or {window index: float32 array [T][n_edges of the window]}."""
+def make_params(p, weights=None, ranker=None):
+    """weights: None or {window index: float32 array [T][n_edges of the window]};
+    ranker: None or 641 float32 parameters of the decimation ranker."""
     q = QdoParams()
     for name, _ in QdoParams._fields_:
-        if name in ("wts", "wT"):
+        if name in ("wts", "wT", "ranker", "dump", "dump_n", "dump_cap"):
             continue
         setattr(q, name, p[name])
+    q.ranker = None
+    if ranker is not None:
+        r = np.ascontiguousarray(ranker, np.float32)
+        assert r.size == 641
+        q.ranker = r.ctypes.data
+        q._keep_r = r
     q.wT = 0
     q.wts = None
     if weights:
@@ -258,13 +281,21 @@ class OracleDEM:
         return det, obs
 
     # ---- decoding ----
-    def decode_window(self, params, k, synd, trace=False, weights=None):
+    def decode_window(self, params, k, synd, trace=False, weights=None, ranker=None, dump=None):
+        """dump: None or a RANK_REC array that receives path 0's candidate
+        records (the returned info carries 'n_dump', the number produced)."""
         W, F = params["W"], params["F"]
         win = self.window(W, F, k)
         synd = np.ascontiguousarray(synd, np.uint8)
         corr = np.zeros(win["n_cols"], np.uint8)
         info = np.zeros(4, np.int32)
-        P = make_params(params, weights)
+        P = make_params(params, weights, ranker)
+        dn = np.zeros(1, np.int32)
+        if dump is not None:
+            assert dump.dtype == RANK_REC and dump.flags.c_contiguous
+            P.dump = dump.ctypes.data
+            P.dump_n = dn.ctypes.data
+            P.dump_cap = dump.shape[0]
         nb = 1 << params["k_guess"]
         dmx = max(params["d_max_main"], params["d_max_other"])
         if trace:
@@ -284,10 +315,10 @@ class OracleDEM:
             lib().qdo_decode_window(self.h, C.byref(P), k, _ptr(synd), _ptr(corr), _ptr(info),
                                     None, None, None, None)
             tr = None
-        return corr, dict(prebp_converged=bool(info[0]), winner=int(info[1]),
+        return corr, dict(n_dump=int(dn[0]), prebp_converged=bool(info[0]), winner=int(info[1]),
                           n_short=int(info[2]), prebp_iters=int(info[3])), tr
 
-    def run_shots(self, params, det, obs, threads=1, want_corr=False, weights=None):
+    def run_shots(self, params, det, obs, threads=1, want_corr=False, weights=None, ranker=None):
         """Sliding-window decode of every shot.  Returns (fail, obs_pred, corr_words)."""
         det = np.ascontiguousarray(det, np.uint32)
         obs = np.ascontiguousarray(obs, np.uint32)
@@ -298,7 +329,7 @@ class OracleDEM:
         maxc = max(self.window(params["W"], params["F"], k)["n_cols"] for k in range(nwin))
         cw = (maxc + 31) // 32
         corr = np.zeros((n, nwin, cw), np.uint32) if want_corr else None
-        P = make_params(params, weights)
+        P = make_params(params, weights, ranker)
 
         def work(a, b):
             lib().qdo_run_shots(self.h, C.byref(P), _ptr(det[a:b]), _ptr(obs[a:b]), b - a,

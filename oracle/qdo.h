@@ -50,7 +50,27 @@ typedef struct {
    * counts from the last message (re)initialisation; t > wT uses row wT. */
   const float* const* wts;
   int wT;
+  /* Learned decimation ranker (no counterpart in the paper): NULL for
+   * Alg. 1, else 641 raw FP32 parameters W1[64][8], b1[64], W2[64], b2 of
+   * score = W2 . relu(W1 x + b1) + b2 over 8 candidate features. */
+  const float* ranker;
+  /* Candidate dump of path 0 (training data for the ranker; NULL: off): at
+   * every selection step, one record per candidate left after Alg. 3, in
+   * column order, while *dump_n < dump_cap (*dump_n counts every record). */
+  struct qdo_rank_rec* dump;
+  int* dump_n;
+  int dump_cap;
 } qdo_params;
+
+/* One ranker candidate: features x (as the ranker sees them), the window
+ * column, the selection depth D and path id; flags bit 0 = [L <= 0] (the
+ * value Alg. 1 would give it), bit 1 = the candidate selected at this step. */
+typedef struct qdo_rank_rec {
+  float x[8];
+  int32_t shot, wcol;
+  int16_t depth, path;
+  int32_t flags;
+} qdo_rank_rec;
 
 /* Per-branch summary of one GDG decision path. */
 typedef struct {
@@ -129,6 +149,10 @@ int qdo_run_shots(const qdo_dem* d, const qdo_params* P, const uint32_t* det_bit
                   const uint32_t* obs_bits, int64_t n_shots, uint8_t* fail,
                   uint32_t* obs_pred, uint32_t* win_corr_words /* may be NULL */,
                   int corr_words_per_window);
+
+/* Ranker scores of n feature rows x [n][8] under raw parameters (641 floats,
+ * rounded to the ranker's grids first). */
+void qdo_ranker_score(const float* raw, const float* x, int n, float* out);
 
 #ifdef __cplusplus
 }
