@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--train-steps", type=int, default=60,
                     help="Adam steps per window type for the learned weights (0: skip)")
     ap.add_argument("--train-batch", type=int, default=4096)
+    ap.add_argument("--ranker-steps", type=int, default=300,
+                    help="Adam steps of the decimation ranker (0: skip)")
+    ap.add_argument("--ranker-shots", type=int, default=4096,
+                    help="window samples per collection round for the ranker (4 rounds)")
     return ap.parse_args()
 
 
@@ -309,6 +313,7 @@ def main():
         for k, w in wts.items():
             dec.set_weights(k, w)
         tot_l, fail_l, clocks_l = timed(local)
+        cl = dec.counters()
         for k in wts:
             dec.set_weights(k, None)
         n_types = len({id(w) for w in wts.values()})
@@ -318,7 +323,34 @@ def main():
                              "seconds": train_s, "T": 25, "checkpoint_every": 5, "adam_lr": 1e-3,
                              "loss_log": logs},
                    "value": windows / tot_l, "ms_per_step": 1000 * tot_l / args.steps,
+                   "edge_iterations_per_window": float(cl[0] + cl[1]) / (B * nwin * args.steps),
+                   "gdg_windows_frac": float(cl[3]) / (B * nwin * args.steps),
                    "clocks": clocks_l}
+    # ---- learned decimation ranker: train on the decoder's own records ----
+    ranked = None
+    if args.ranker_steps > 0:
+        from paper_2403_18901_gb300 import ranker as rk
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rdec = qdec.Decoder(dem, params, max_shots=max(B, args.ranker_shots))
+        rparams, rinfo = rk.train(rdec, 1, steps=args.ranker_steps, shots_per_round=args.ranker_shots, rounds=4,
+                                  cap=1 << 24, batch=65536, lr=1e-2, seed=2_403_189_01)
+        torch.cuda.synchronize()
+        rtrain_s = time.perf_counter() - t0
+        del rdec
+        rhost = rparams.cpu().numpy()
+        dec.set_ranker(rhost)
+        tot_r, fail_r, clocks_r = timed(local)
+        cr = dec.counters()
+        rlaunch = dec.launch_info(1)
+        dec.set_ranker(None)
+        ranked = {"train": dict(rinfo, steps=args.ranker_steps, window=1, rounds=4,
+                                shots_per_round=args.ranker_shots, batch=65536, adam_lr=1e-2,
+                                seconds=rtrain_s),
+                  "value": windows / tot_r, "ms_per_step": 1000 * tot_r / args.steps, "clocks": clocks_r,
+                  "edge_iterations_per_window": float(cr[0] + cr[1]) / (B * nwin * args.steps),
+                  "gdg_windows_frac": float(cr[3]) / (B * nwin * args.steps),
+                  "launch": rlaunch, "failures": fail_r}
     if world > 1:
         fl = torch.tensor([failures], device="cuda")
         torch.distributed.all_reduce(fl)
@@ -402,6 +434,21 @@ def main():
                             "wilson95": [per_round(llo), per_round(lhi)]}}
             del fl_tot
 
+        if ranked is not None:
+            ldec.set_ranker(rhost)
+            rp50, rp99, _ = latency(ldec)
+            ldec.set_ranker(None)
+            ranked["latency_ms"] = {"p50": rp50, "p99": rp99}
+            lo, hi = wilson(failures, n_shots_total)
+            rlo, rhi = wilson(ranked["failures"], B * args.steps)
+            ranked["ler_per_round"] = {
+                "plain": {"failures": failures, "shots": n_shots_total,
+                          "p_L": per_round(failures / n_shots_total),
+                          "wilson95": [per_round(lo), per_round(hi)]},
+                "ranker": {"failures": ranked["failures"], "shots": B * args.steps,
+                           "p_L": per_round(ranked["failures"] / (B * args.steps)),
+                           "wilson95": [per_round(rlo), per_round(rhi)]}}
+
         cpu_rate, cores, cpu_shots, cpu_s = cpu_oracle_rate(params, args.cpu_seconds, args.seed)
         line = {
             "metric": METRIC, "value": value, "unit": "windows/s", "n_gpus": world,
@@ -439,6 +486,7 @@ def main():
                                        f"{cpu_s:.1f} s"},
             "wall_s_timed": t_wall,
             "learned": learned,
+            "ranker": ranked,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

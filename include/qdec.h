@@ -263,6 +263,79 @@ qd_status qd_decode_commit_static(qd_decoder* dec, int k, uint32_t* det_bits, in
 qd_status qd_decoder_set_weights(qd_decoder* dec, int k, const float* w, int T);
 
 /*
+ * Learned decimation ranker (no counterpart in the paper: it replaces the
+ * argmin over the history sums L_i of Alg. 1, SELECT-VN, in every window and
+ * decision path; aggressive decimation (Alg. 3), the guess rule of Alg. 2 and
+ * f = [L_g <= 0] for the selected VN g stay as they are).
+ *   params  HOST pointer to 641 FP32 values, copied: W1[64][8], b1[64],
+ *           W2[64], b2 of score = W2 . relu(W1 x + b1) + b2; NULL removes it.
+ * The library rounds W1 and W2 to multiples of 2^-6 clamped to [-2, 2] and b1
+ * to multiples of 2^-7 within [-512, 512] (round half to even), keeps b2 as given, and selects
+ * the candidate with the highest score (ties to the lowest short column).
+ * Features of candidate i, in this order: L_i / 4, h_0..h_3 (the last four
+ * posteriors, oldest first), each rounded to the 1/2 grid and clamped to
+ * +-63.5; the number of unsatisfied neighbour checks (at most 127); the
+ * static column degree; the window block of the column's first detector
+ * (at most 255).  Installing or removing the ranker re-plans the shared-memory
+ * layouts; not to be called while this decoder's launches are in flight.
+ * Returns QD_EINVAL on a non-finite parameter, QD_EUNSUPPORTED when a window
+ * no longer fits in shared memory.
+ */
+qd_status qd_decoder_set_ranker(qd_decoder* dec, const float* params);
+
+/*
+ * One ranker candidate record (training data; no counterpart in the paper).
+ * x: the eight ranker features above, exactly as the ranker sees them;
+ * shot: index within the decode call; wcol: window column; depth: the
+ * selection depth D of Alg. 2; path: the decision path (0); flags bit 0 =
+ * [L <= 0] (the value f Alg. 1 gives the candidate), bit 1 = the candidate the
+ * active rule (Alg. 1 or the ranker) selected at this step.
+ */
+typedef struct {
+  float x[8];
+  int32_t shot, wcol;
+  int16_t depth, path;
+  int32_t flags;
+} qd_rank_rec_t;
+
+/*
+ * Candidate dump: while set, every decode of this decoder appends, for
+ * decision path 0 at each selection step, one record per candidate left after
+ * Alg. 3.  records: device [capacity] qd_rank_rec_t; count: device int32 that
+ * the caller zeroes, incremented once per candidate (records beyond capacity
+ * are counted, not written); record order is unspecified.  records = NULL
+ * turns the dump off.  Like the ranker it re-plans the shared-memory layouts.
+ */
+qd_status qd_decoder_set_dump(qd_decoder* dec, void* records, int* count, int capacity);
+
+/*
+ * Window-local samples for window k (training data): every column of the
+ * window fires independently with its prior p_i (Philox4x32-10, counter
+ * (column / 4, shot, 1 + k)), the same draws as qd_wms_sample.
+ *   det_bits   device [n][det_words]: the window syndrome H_win e placed at
+ *              the window's detector rows, zeros elsewhere (input of
+ *              qd_decode_windows for window k)
+ *   fault_bits device [n][corr_words] or NULL: e, by window column
+ */
+qd_status qd_window_sample(qd_decoder* dec, int k, uint64_t seed, uint64_t offset, int64_t n, uint32_t* det_bits,
+                           uint32_t* fault_bits, qd_stream_t stream);
+
+/*
+ * Ranker forward / backward on n candidate records (device pointers):
+ *   params     [641] FP32 W1[64][8], b1[64], W2[64], b2
+ *   labels     [n] uint8 0/1 (required for grad and loss)
+ *   quantize   1: the forward uses the grid-rounded parameters the decoder
+ *              uses and the gradient passes straight through the rounding
+ *   score      [n] or NULL: the logit z
+ *   loss       [n] or NULL: w_y (softplus(z) - y z), w_1 = pos_weight, w_0 = 1
+ *   grad       [641] or NULL: ACCUMULATES grad_scale * d(sum of losses)/d params
+ *              (FP32 atomics: the last bits depend on the order of arrival)
+ */
+qd_status qd_ranker_eval(const float* params, const void* records, const uint8_t* labels, int64_t n, int quantize,
+                         float pos_weight, float grad_scale, float* grad, float* loss, float* score,
+                         qd_stream_t stream);
+
+/*
  * Training the learned weighted min-sum of window k (no counterpart in the
  * paper).  A training sample is a window syndrome s = H_win e with every
  * window column firing independently with its prior (the syndrome a window

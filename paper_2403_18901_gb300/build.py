@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libqdec.so")
-SOURCES = ["gdg_kernel.cu", "learn_kernel.cu", "qdec_api.cu", "dem_host.cpp"]
+SOURCES = ["gdg_kernel.cu", "learn_kernel.cu", "ranker_kernel.cu", "qdec_api.cu", "dem_host.cpp"]
 HEADERS = ["gdg_kernel.cuh", "qdec_internal.h", os.path.join("..", "..", "include", "qdec.h")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

@@ -240,6 +240,8 @@ struct ShortG {
   const uint16_t* efull;  // short edge -> full-window edge (learned weights)
   const float* wts;
   int wT, wE;
+  int rpb;  // window rows per block (block of a column = its first row / rpb)
+  const uint16_t* sel;  // short column -> window column
 };
 
 struct Slot {
@@ -249,13 +251,14 @@ struct Slot {
   CNState* cns;
   int* deg;
   uint32_t *sp, *par, *unsat;
+  int8_t* hq;  // ranker only: the last four posteriors as round(2 clamp(x, 63.5)), oldest first
 };
 
 __device__ __forceinline__ Slot make_slot(char* base, const Layout& L) {
   return Slot{(float*)(base + L.b_post),   (float*)(base + L.b_acc),     (uint8_t*)(base + L.b_hfl),
               (uint8_t*)(base + L.b_sign), (int8_t*)(base + L.b_status), (CNState*)(base + L.b_cns),
               (int*)(base + L.b_deg),      (uint32_t*)(base + L.b_sp),   (uint32_t*)(base + L.b_par),
-              (uint32_t*)(base + L.b_unsat)};
+              (uint32_t*)(base + L.b_unsat), (int8_t*)(base + L.b_hq)};
 }
 
 // Posterior of a decimated VN: a NaN, so the check-node pass recognises a
@@ -321,6 +324,145 @@ __device__ int peel(const ShortG& G, const Slot& B, const Grp& g) {
   return -2;
 }
 
+// ---- learned decimation ranker (replaces the argmin of Alg. 1) ----
+// score = W2 . relu(W1 x + b1) + b2 over the candidate features
+//   x = (L/4, h0, h1, h2, h3 on the 1/2 grid clamped to +-63.5, #unsatisfied
+//        neighbour checks (<= 127), static degree, block of the first
+//        detector (<= 255)).
+// With W1 on the 2^-6 grid in [-2, 2] and b1 on the 2^-7 grid in [-512, 512] every layer-1
+// partial sum is a multiple of 2^-7 below 2^13: the BF16 tensor-core product
+// with FP32 accumulation is exact, in any order.  Layer 2 runs in FP32 in one
+// fixed order per candidate: s_q = sum over t = 0..7, c = 0..1 of
+// W2[u] h[u], u = 8t + 2q + c (lane q of the quad that holds those units in
+// the MMA accumulator layout), score = ((s_0 + s_1) + (s_2 + s_3)) + b2.
+
+__device__ __forceinline__ float qfeat(float x) {
+  return (float)__float2int_rn(2.0f * fminf(fmaxf(x, -63.5f), 63.5f)) * 0.5f;
+}
+__device__ __forceinline__ int8_t qhist(float x) { return (int8_t)__float2int_rn(2.0f * fminf(fmaxf(x, -63.5f), 63.5f)); }
+
+// two BF16-exact floats as a packed pair (low half = first)
+__device__ __forceinline__ uint32_t bf16x2_exact(float lo, float hi) {
+  return (__float_as_uint(lo) >> 16) | (__float_as_uint(hi) & 0xFFFF0000u);
+}
+
+// D = A B + C, m16n8k8, BF16 inputs, FP32 accumulate
+__device__ __forceinline__ void mma_m16n8k8_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0, float c0,
+                                                 float c1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%7,%8,%9,%10};\n"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a0), "r"(a1), "r"(b0), "f"(c0), "f"(c1), "f"(c0), "f"(c1));
+}
+
+__device__ __forceinline__ bool ranker_candidate(const ShortG& G, const Slot& B, int k) {
+  return k < G.ns && B.status[k] == -1 && G.vdeg[k] > 2;
+}
+
+// Features 2 tig and 2 tig + 1 of short column k (zero for a non-candidate).
+__device__ __forceinline__ uint32_t ranker_pair(const ShortG& G, const Slot& B, int k, bool cand, int tig) {
+  if (!cand) return 0u;
+  float lo, hi;
+  const uint32_t h4 = *(const uint32_t*)(B.hq + 4 * k);
+  const float hv0 = (float)(int8_t)(h4 & 0xFF) * 0.5f, hv1 = (float)(int8_t)((h4 >> 8) & 0xFF) * 0.5f;
+  const float hv2 = (float)(int8_t)((h4 >> 16) & 0xFF) * 0.5f, hv3 = (float)(int8_t)(h4 >> 24) * 0.5f;
+  if (tig == 0) {
+    lo = qfeat(__fmul_rn(B.acc[k], 0.25f));
+    hi = hv0;
+  } else if (tig == 1) {
+    lo = hv1;
+    hi = hv2;
+  } else if (tig == 2) {
+    int nus = 0;
+    for (int e = G.colptr[k]; e < G.colptr[k + 1]; ++e) nus += bit_of(B.unsat, G.colrows[e]);
+    lo = hv3;
+    hi = (float)min(nus, 127);
+  } else {
+    lo = (float)G.vdeg[k];
+    hi = (float)min(G.colrows[G.colptr[k]] / G.rpb, 255);
+  }
+  return bf16x2_exact(lo, hi);
+}
+
+// Highest score over the candidates (ties to the lowest column), as
+// (-score, column) for the group's lexicographic argmin.  Each warp of the
+// group scores tiles of 16 consecutive columns; every lane of the group calls.
+template <class Grp>
+__device__ void ranker_select(const KParams& P, const ShortG& G, const Slot& B, const Grp& g, float& nv, int& nk) {
+  const int lane = g.rank & 31, wid = g.rank >> 5, nw = g.size >> 5;
+  const int gi = lane >> 2, tig = lane & 3, qb = lane & ~3;
+  const float* b1 = P.rkq + 512;
+  const float* w2 = P.rkq + 576;
+  const float b2 = P.rkq[640];
+  nv = CUDART_INF_F;
+  nk = kNone;
+  for (int t0 = 16 * wid; t0 < G.ns; t0 += 16 * nw) {
+    const int r0 = t0 + gi, r1 = r0 + 8;
+    const bool c0 = ranker_candidate(G, B, r0), c1 = ranker_candidate(G, B, r1);
+    const uint32_t a0 = ranker_pair(G, B, r0, c0, tig), a1 = ranker_pair(G, B, r1, c1, tig);
+    float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int u = 8 * t + 2 * tig;
+      float d[4];
+      mma_m16n8k8_bf16(d, a0, a1, P.rkb[32 * t + lane], b1[u], b1[u + 1]);
+      const float wa = w2[u], wb = w2[u + 1];
+      s0 = __fadd_rn(s0, __fmul_rn(wa, d[0] > 0.0f ? d[0] : 0.0f));
+      s0 = __fadd_rn(s0, __fmul_rn(wb, d[1] > 0.0f ? d[1] : 0.0f));
+      s1 = __fadd_rn(s1, __fmul_rn(wa, d[2] > 0.0f ? d[2] : 0.0f));
+      s1 = __fadd_rn(s1, __fmul_rn(wb, d[3] > 0.0f ? d[3] : 0.0f));
+    }
+    float q[4], p[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      q[i] = __shfl_sync(FULL, s0, qb + i);
+      p[i] = __shfl_sync(FULL, s1, qb + i);
+    }
+    const float sc0 = __fadd_rn(__fadd_rn(__fadd_rn(q[0], q[1]), __fadd_rn(q[2], q[3])), b2);
+    const float sc1 = __fadd_rn(__fadd_rn(__fadd_rn(p[0], p[1]), __fadd_rn(p[2], p[3])), b2);
+    // rows grow with the tile, so a strict '<' keeps the lowest column
+    if (c0 && -sc0 < nv) {
+      nv = -sc0;
+      nk = r0;
+    }
+    if (c1 && -sc1 < nv) {
+      nv = -sc1;
+      nk = r1;
+    }
+  }
+  g.argmin(nv, nk);
+}
+
+// Records of every candidate of this step (path 0 only), in any order.
+template <class Grp>
+__device__ void dump_candidates(const KParams& P, const ShortG& G, const Slot& B, const Grp& g, long long shot, int D,
+                                int gsel) {
+  for (int k = g.rank; k < G.ns; k += g.size) {
+    if (!ranker_candidate(G, B, k)) continue;
+    const uint32_t h4 = *(const uint32_t*)(B.hq + 4 * k);
+    int nus = 0;
+    for (int e = G.colptr[k]; e < G.colptr[k + 1]; ++e) nus += bit_of(B.unsat, G.colrows[e]);
+    const float L = B.acc[k];
+    const int pos = atomicAdd(P.dump_n, 1);
+    if (pos >= P.dump_cap) continue;
+    RankRec r;
+    r.x[0] = qfeat(__fmul_rn(L, 0.25f));
+    r.x[1] = (float)(int8_t)(h4 & 0xFF) * 0.5f;
+    r.x[2] = (float)(int8_t)((h4 >> 8) & 0xFF) * 0.5f;
+    r.x[3] = (float)(int8_t)((h4 >> 16) & 0xFF) * 0.5f;
+    r.x[4] = (float)(int8_t)(h4 >> 24) * 0.5f;
+    r.x[5] = (float)min(nus, 127);
+    r.x[6] = (float)G.vdeg[k];
+    r.x[7] = (float)min(G.colrows[G.colptr[k]] / G.rpb, 255);
+    r.shot = (int32_t)shot;
+    r.wcol = G.sel[k];
+    r.depth = (int16_t)D;
+    r.path = 0;
+    r.flags = (L <= 0.0f ? 1 : 0) | (k == gsel ? 2 : 0);
+    P.dump[pos] = r;
+  }
+}
+
 struct PathOut {
   int* status;
   double* pm;
@@ -329,6 +471,7 @@ struct PathOut {
   StepTrace* st;
   int8_t* fstat;
   long long* visits;  // accumulates active edge visits
+  long long shot;
 };
 
 // One decision path of Alg. 2 on the shortened window, run by group g.
@@ -438,6 +581,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
         }
         B.post[k] = p;
         if (hist) {
+          if (P.rkq || P.dump) B.hq[4 * k + (it - (P.ips - 3))] = qhist(p);
           const uint8_t f = (uint8_t)((p <= 0.0f) | ((p < PA) << 1) | ((p > P.pc) << 2) | ((p > P.pd) << 3));
           if (hist0) {
             B.acc[k] = p;
@@ -473,7 +617,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
     {
       // ---- SELECT-VN (Alg. 1) with AGG-DEC (Alg. 3) ----
       const uint32_t* lastpar = B.par + ((iters - 1) & 1) * rw;
-      if (!P.low_err)
+      if (!P.low_err || P.rkq || P.dump)
         for (int x = R; x < rw; x += S) B.unsat[x] = lastpar[x] ^ B.sp[x];
       g.sync();
       const float PBd = (D == 1) ? P.pb_d1 : PB;
@@ -495,6 +639,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
             continue;
           }
         }
+        if (P.rkq) continue;
         if (L < bL) {
           bL = L;
           bk = k;
@@ -504,8 +649,14 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
           tk = k;
         }
       }
-      g.argmin(bL, bk);
-      g.argmin(tL, tk);
+      if (P.rkq) {
+        g.sync();  // the aggressive decisions are visible
+        ranker_select(P, G, B, g, bL, bk);
+        if (bk != kNone) bL = B.acc[bk];  // f keeps the rule of Alg. 1: [L <= 0]
+      } else {
+        g.argmin(bL, bk);
+        g.argmin(tL, tk);
+      }
       nagg = g.sum_i(nagg);
       g.sync();
       int gsel, f;
@@ -519,6 +670,10 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
         if (out.st && R == 0) out.st[D - 1] = StepTrace{-1, -1, 0, (int16_t)nagg, 0};
         status = BR_NOCAND;
         goto done;
+      }
+      if (P.dump && id == 0) {
+        dump_candidates(P, G, B, g, out.shot, D, gsel);
+        g.sync();
       }
       int v = f;
       if (D <= P.k) v = ((id >> (P.k - D)) & 1) ? 1 - f : f;  // b + (-1)^b f
@@ -836,10 +991,10 @@ __device__ __forceinline__ ShortG short_graph(char* sm, const Layout& L, const W
                 (const uint16_t*)(sm + L.s_rowptr), (const uint32_t*)(sm + L.s_rowent),
                 (const float*)(sm + L.s_llr),       (const uint8_t*)(sm + L.s_vdeg),
                 (const uint32_t*)(sm + L.sbits),    (const uint16_t*)(sm + L.s_efull),
-                W.wts, W.wT, W.n_edges};
+                W.wts, W.wT, W.n_edges, W.rows_per_block, (const uint16_t*)(sm + L.sel)};
 }
 
-__device__ __forceinline__ PathOut trace_out(const DecodeArgs& A, char* tr, int id) {
+__device__ __forceinline__ PathOut trace_out(const DecodeArgs& A, char* tr, int id, long long shot) {
   PathOut o{};
   if (tr) {
     o.btr = (BranchTrace*)(tr + trace_off_br()) + id;
@@ -847,6 +1002,7 @@ __device__ __forceinline__ PathOut trace_out(const DecodeArgs& A, char* tr, int 
     o.fstat = (int8_t*)(tr + trace_off_fs(A.P.nb, A.dmx)) + (size_t)id * A.ns_max;
   }
   o.visits = &A.counters[1];
+  o.shot = shot;
   return o;
 }
 
@@ -909,7 +1065,7 @@ __global__ void __launch_bounds__(256, 2) decode_shot_kernel(DecodeArgs A) {
         if (lane == 0) id = atomicAdd(&misc[2], 1);
         id = __shfl_sync(FULL, id, 0);
         if (id >= A.P.nb) break;
-        PathOut o = trace_out(A, tr, id);
+        PathOut o = trace_out(A, tr, id, shot);
         o.status = &res_status[id];
         o.pm = &res_pm[id];
         o.ebits = res_e + (size_t)id * L.sw;
@@ -984,7 +1140,7 @@ __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
   const CtaGrp g{tid, (int)blockDim.x, sm + L.red};
   const size_t rb = path_result_bytes(A.sw_max);
   char* mine = A.path_res + ((size_t)shot * nb + id) * rb;
-  PathOut o = trace_out(A, tr, id);
+  PathOut o = trace_out(A, tr, id, shot);
   o.status = (int*)mine;
   o.pm = (double*)(mine + 8);
   o.ebits = (uint32_t*)(mine + 16);

@@ -19,11 +19,30 @@ struct KParams {
   float alpha, clip, pa_main, pa_other, pb_main, pb_other, pb_d1, pc, pd;
   int n_pre, ips, dmax_main, dmax_other, k, low_err, peel_init, pc_max_depth, n_unsat_min;
   int nb;  // 2^k
+  // learned decimation ranker (NULL: the argmin of Alg. 1): rkq = the
+  // grid-rounded W1[64][8], b1[64], W2[64], b2; rkb[t][lane] = the BF16 pair
+  // (W1[8t + lane/4][2 (lane%4)], W1[8t + lane/4][2 (lane%4) + 1]), the B
+  // fragment of an m16n8k8 MMA for hidden units 8t..8t+7
+  const float* rkq;
+  const uint32_t* rkb;
+  // candidate dump of path 0 (ranker training data; NULL: off)
+  struct RankRec* dump;
+  int* dump_n;
+  int dump_cap;
+};
+
+// One ranker candidate (layout of qd_rank_rec_t): features, shot, window
+// column, selection depth, path; flags bit 0 = [L <= 0], bit 1 = selected.
+struct RankRec {
+  float x[8];
+  int32_t shot, wcol;
+  int16_t depth, path;
+  int32_t flags;
 };
 
 // One window's Tanner graph in global memory (read-only for all shots).
 struct WinDev {
-  int n_rows, n_cols, n_edges, row0, n_short, es_max;
+  int n_rows, n_cols, n_edges, row0, n_short, es_max, rows_per_block;
   const uint16_t *col_ptr, *col_rows, *row_ptr;
   const uint32_t* row_ent;  // CSR entry: CSC edge id | (column << 16)
   const float* llr;
@@ -74,7 +93,7 @@ struct Layout {
   // pre-BP (relative to U)
   unsigned p_post, p_key, p_cns, p_sign, p_par, p_sort, p_end;
   // one path slot (relative to the slot base)
-  unsigned b_post, b_acc, b_hfl, b_status, b_sign, b_cns, b_deg, b_sp, b_par, b_unsat, b_size;
+  unsigned b_post, b_acc, b_hfl, b_status, b_sign, b_cns, b_deg, b_sp, b_par, b_unsat, b_hq, b_size;
   unsigned total;
   int rw, cw, sw, sortn, nslots;
 };
@@ -82,7 +101,7 @@ struct Layout {
 __host__ __device__ inline unsigned al16(unsigned x) { return (x + 15u) & ~15u; }
 
 __host__ __device__ inline Layout make_layout(int nr, int nc, int ne, int ns, int es, int nb,
-                                              int nslots, bool stage_graph = false) {
+                                              int nslots, bool stage_graph = false, bool ranker = false) {
   Layout L{};
   L.rw = (nr + 31) / 32;
   L.cw = (nc + 31) / 32;
@@ -137,6 +156,7 @@ __host__ __device__ inline Layout make_layout(int nr, int nc, int ne, int ns, in
   L.b_sp = b; b = al16(b + 4u * L.rw);
   L.b_par = b; b = al16(b + 8u * L.rw);
   L.b_unsat = b; b = al16(b + 4u * L.rw);
+  L.b_hq = b; b = al16(b + (ranker ? 4u * ns : 0u));
   L.b_size = b;
   unsigned ub = L.p_end > b * (unsigned)nslots ? L.p_end : b * (unsigned)nslots;
   L.total = L.U + ub;

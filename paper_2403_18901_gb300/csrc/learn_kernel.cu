@@ -279,9 +279,14 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
   return c;
 }
 
+// Window-local samples: every window column fires with its prior (Philox
+// word 3 = domain).  Outputs (each optional): the window syndrome [n][rw];
+// the same bits placed at rows row0.. of a whole-shot detector vector
+// [n][det_words] (zeros elsewhere); the fired columns [n][cw].
 __global__ void wms_sample_kernel(WmsGraph G, const uint32_t* __restrict__ thr, unsigned long long seed,
                                   unsigned long long off, long long n, uint32_t domain,
-                                  uint32_t* __restrict__ synd) {
+                                  uint32_t* __restrict__ synd, uint32_t* __restrict__ det, int det_words,
+                                  int row0, uint32_t* __restrict__ fault, int cw) {
   extern __shared__ uint32_t srow[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long s = (long long)blockIdx.x * (blockDim.x >> 5) + wib;
@@ -297,17 +302,34 @@ __global__ void wms_sample_kernel(WmsGraph G, const uint32_t* __restrict__ thr, 
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const int c = 4 * g + r;
-        if (c < G.nc && uu[r] < thr[c])
+        if (c < G.nc && uu[r] < thr[c]) {
           for (int e = G.col_ptr[c]; e < G.col_ptr[c + 1]; ++e) {
             const int j = G.col_rows[e];
             atomicXor(&row[j >> 5], 1u << (j & 31));
           }
+          if (fault) atomicOr(&fault[(size_t)s * cw + (c >> 5)], 1u << (c & 31));
+        }
       }
     }
   }
   __syncwarp();
-  if (s < n)
-    for (int x = lane; x < G.rw; x += 32) synd[(size_t)s * G.rw + x] = row[x];
+  if (s < n) {
+    if (synd)
+      for (int x = lane; x < G.rw; x += 32) synd[(size_t)s * G.rw + x] = row[x];
+    if (det)
+      for (int x = lane; x < det_words; x += 32) {
+        // detector bits 32x .. 32x + 31 = window rows 32x - row0 ..
+        const int b = 32 * x - row0;
+        uint32_t v = 0;
+        if (b > -32 && b < G.nr) {
+          const int wq = b >= 0 ? (b >> 5) : -1, sh = b & 31;
+          const uint32_t lo = (wq >= 0 && wq < G.rw) ? row[wq] : 0u;
+          const uint32_t hi = (wq + 1 >= 0 && wq + 1 < G.rw) ? row[wq + 1] : 0u;
+          v = sh ? ((lo >> sh) | (hi << (32 - sh))) : lo;
+        }
+        det[(size_t)s * det_words + x] = v;
+      }
+  }
 }
 
 __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
@@ -349,11 +371,16 @@ cudaError_t launch_wms(cudaStream_t st, int grid, size_t smem, const WmsGraph& G
 }
 
 cudaError_t launch_wms_sample(cudaStream_t st, const WmsGraph& G, const uint32_t* thr, unsigned long long seed,
-                              unsigned long long off, long long n, unsigned domain, uint32_t* synd) {
+                              unsigned long long off, long long n, unsigned domain, uint32_t* synd, uint32_t* det,
+                              int det_words, int row0, uint32_t* fault, int cw) {
   if (n <= 0) return cudaSuccess;
+  if (fault) {
+    const cudaError_t e = cudaMemsetAsync(fault, 0, sizeof(uint32_t) * (size_t)n * cw, st);
+    if (e != cudaSuccess) return e;
+  }
   const int wpb = 8;
   lrn::wms_sample_kernel<<<(unsigned)((n + wpb - 1) / wpb), 32 * wpb, sizeof(uint32_t) * wpb * G.rw, st>>>(
-      G, thr, seed, off, n, domain, synd);
+      G, thr, seed, off, n, domain, synd, det, det_words, row0, fault, cw);
   return cudaGetLastError();
 }
 

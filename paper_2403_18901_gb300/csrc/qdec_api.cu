@@ -66,6 +66,7 @@ struct WinGpu {
   uint32_t* d_ccobs = nullptr;
   int grid_per_sm = 1;
   int shot_warps = kShotWarps;
+  uint32_t* d_wthr = nullptr;  // window-local sampling thresholds (on first use)
 };
 
 template <class T>
@@ -99,12 +100,83 @@ struct qd_decoder {
   char* d_path_res = nullptr;
   int* d_arrive = nullptr;
   size_t trace_bytes = 0, smem_max = 0;
+  int smem_optin = 0;
+  bool hist_on = false;  // layouts hold the quantised history (ranker or dump)
+  void* d_ranker = nullptr;  // grid-rounded parameters (644 floats), then the 256 B fragments
   int* d_work = nullptr;
   long long* d_counters = nullptr;
   uint32_t* d_corr = nullptr;
   uint32_t *d_det = nullptr, *d_obs = nullptr, *d_pred = nullptr, *d_fail = nullptr, *d_resid = nullptr;
   long long* d_nfail = nullptr;
 };
+
+namespace {
+// Shared-memory layouts of every window: as many decision-path slots (warps)
+// as fit in shot mode, then the path-mode layout with the window graph staged
+// in shared memory when it fits too.  The ranker and the candidate dump add
+// the quantised history (4 bytes per short column) to every slot.
+qd_status configure_layouts(qd_decoder* dec, bool hist, const char* who) {
+  struct Conf {
+    qd::Layout L, Lp;
+    int shot_warps, grid_per_sm;
+  };
+  const int optin = dec->smem_optin;
+  const int nb = dec->kp.nb;
+  size_t smem_max = 0;
+  std::vector<Conf> cf(dec->wins.size());
+  for (size_t w = 0; w < cf.size(); ++w) {
+    Conf& c = cf[w];
+    const auto& h = dec->wins[w].h;
+    auto lay = [&](int slots, bool stage) {
+      return qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, nb, slots, stage, hist);
+    };
+    // the most resident decision-path warps per SM (slots per CTA x CTAs per
+    // SM); ties to more slots per CTA
+    int best = 0;
+    c.shot_warps = 1;
+    for (int sw = kShotWarps; sw >= 1; --sw) {
+      const qd::Layout Ls = lay(sw, false);
+      if (Ls.total > (unsigned)optin) continue;
+      int blocks = 0;
+      QD_CK(qd::decode_occupancy(0, 32 * sw, Ls.total, &blocks));
+      if (sw * blocks > best) {
+        best = sw * blocks;
+        c.shot_warps = sw;
+      }
+    }
+    c.L = lay(c.shot_warps, false);
+    c.Lp = lay(1, true);
+    if (c.Lp.total > (unsigned)optin) c.Lp = lay(1, false);
+    if (c.L.total > (unsigned)optin || c.Lp.total > (unsigned)optin) {
+      set_error(std::string(who) + ": window " + std::to_string(w) + " needs " +
+                std::to_string(std::max(c.L.total, c.Lp.total)) + " B of shared memory (limit " +
+                std::to_string(optin) + ")");
+      return QD_EUNSUPPORTED;
+    }
+    smem_max = std::max<size_t>(smem_max, std::max(c.L.total, c.Lp.total));
+    int blocks = 0;
+    QD_CK(qd::decode_occupancy(0, 32 * c.shot_warps, c.L.total, &blocks));
+    c.grid_per_sm = std::max(1, blocks);
+  }
+  for (size_t w = 0; w < cf.size(); ++w) {
+    WinGpu& g = dec->wins[w];
+    g.L = cf[w].L;
+    g.Lp = cf[w].Lp;
+    g.shot_warps = cf[w].shot_warps;
+    g.grid_per_sm = cf[w].grid_per_sm;
+  }
+  dec->smem_max = smem_max;
+  dec->hist_on = hist;
+  return QD_OK;
+}
+
+// Lay the windows out again when the need for the quantised history changes.
+qd_status update_hist(qd_decoder* dec, const char* who) {
+  const bool want = dec->kp.rkq != nullptr || dec->kp.dump != nullptr;
+  if (want == dec->hist_on) return QD_OK;
+  return configure_layouts(dec, want, who);
+}
+}  // namespace
 
 extern "C" {
 
@@ -180,8 +252,10 @@ qd_status qd_decoder_destroy(qd_decoder* dec) {
     cudaFree(w.d_ccptr);
     cudaFree(w.d_ccdet);
     cudaFree(w.d_ccobs);
+    cudaFree(w.d_wthr);
   }
   cudaFree(dec->d_work);
+  cudaFree(dec->d_ranker);
   cudaFree(dec->d_path_res);
   cudaFree(dec->d_arrive);
   cudaFree(dec->d_counters);
@@ -254,23 +328,6 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
     dec->corr_words = std::max(dec->corr_words, (h.n_cols + 31) / 32);
     dec->ns_max = std::max(dec->ns_max, h.n_short);
     dec->sw_max = std::max(dec->sw_max, (h.n_short + 31) / 32);
-    // as many decision-path slots (warps) as fit, then the path-mode layout,
-    // with the window graph staged in shared memory when it fits too
-    for (g.shot_warps = kShotWarps; g.shot_warps > 1; g.shot_warps >>= 1) {
-      g.L = qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, k.nb, g.shot_warps);
-      if (g.L.total <= (unsigned)optin) break;
-    }
-    g.L = qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, k.nb, g.shot_warps);
-    g.Lp = qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, k.nb, 1, true);
-    if (g.Lp.total > (unsigned)optin)
-      g.Lp = qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, k.nb, 1, false);
-    if (g.L.total > (unsigned)optin || g.Lp.total > (unsigned)optin) {
-      set_error("qd_decoder_create: window " + std::to_string(w) + " needs " +
-                std::to_string(std::max(g.L.total, g.Lp.total)) + " B of shared memory (limit " +
-                std::to_string(optin) + ")");
-      return QD_EUNSUPPORTED;
-    }
-    dec->smem_max = std::max<size_t>(dec->smem_max, std::max(g.L.total, g.Lp.total));
     // graph arrays in one allocation
     size_t o_cp = 0, o_cr = o_cp + 2 * h.col_ptr.size(), o_rp = o_cr + 2 * h.col_rows.size(),
            o_re = (o_rp + 2 * h.row_ptr.size() + 15) & ~(size_t)15, o_ll = o_re + 4 * h.row_ent.size(),
@@ -284,7 +341,7 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
     QD_CK(cudaMalloc(&g.d_graph, tot));
     QD_CK(cudaMemcpy(g.d_graph, blob.data(), tot, cudaMemcpyHostToDevice));
     char* b = (char*)g.d_graph;
-    g.dv = qd::WinDev{h.n_rows, h.n_cols, h.n_edges, h.row0, h.n_short, h.short_edges_max,
+    g.dv = qd::WinDev{h.n_rows, h.n_cols, h.n_edges, h.row0, h.n_short, h.short_edges_max, h.n_rows / h.n_blocks,
                       (const uint16_t*)(b + o_cp), (const uint16_t*)(b + o_cr), (const uint16_t*)(b + o_rp),
                       (const uint32_t*)(b + o_re), (const float*)(b + o_ll), nullptr, 0};
     // committed columns: their full detector sets and observables
@@ -300,12 +357,11 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
     QD_CK(upload(&g.d_ccdet, cc_det));
     QD_CK(upload(&g.d_ccobs, cc_obs));
   }
-  QD_CK(qd::set_decode_smem(dec->smem_max));
-  for (auto& g : dec->wins) {
-    int blocks = 0;
-    QD_CK(qd::decode_occupancy(0, 32 * g.shot_warps, g.L.total, &blocks));
-    g.grid_per_sm = std::max(1, blocks);
-  }
+  dec->smem_optin = optin;
+  // the kernels' dynamic shared-memory allowance is the device limit, so
+  // decoders of different sizes coexist (the launch asks for what it needs)
+  QD_CK(qd::set_decode_smem((size_t)optin));
+  if (qd_status st = configure_layouts(dec.get(), false, "qd_decoder_create")) return st;
   dec->trace_bytes = qd::trace_bytes_per_shot(k.nb, dec->dmx, dec->ns_max);
   QD_CK(cudaMalloc(&dec->d_work, sizeof(int) * (nwin + 1)));
   const long long pm_shots = std::min<long long>(max_shots, kPathModeMaxShots);
@@ -447,6 +503,65 @@ qd_status qd_decoder_set_weights(qd_decoder* dec, int k, const float* w, int T) 
   QD_REQ(w == nullptr || T >= 1, "qd_decoder_set_weights: T must be >= 1");
   dec->wins[k].dv.wts = w;
   dec->wins[k].dv.wT = w ? T : 0;
+  return QD_OK;
+}
+
+qd_status qd_decoder_set_ranker(qd_decoder* dec, const float* params) {
+  QD_REQ(dec, "null argument");
+  if (!params) {
+    dec->kp.rkq = nullptr;
+    dec->kp.rkb = nullptr;
+    return update_hist(dec, "qd_decoder_set_ranker");
+  }
+  // the grids of the exact first layer (the same rule as the reference model)
+  auto grid = [](float x, float scale, float lim) {
+    float v = std::rint(x * scale);
+    v = v > lim ? lim : (v < -lim ? -lim : v);
+    return v / scale;
+  };
+  std::vector<float> q(644, 0.0f);
+  for (int i = 0; i < 641; ++i)
+    QD_REQ(std::isfinite(params[i]), "qd_decoder_set_ranker: non-finite parameter");
+  for (int i = 0; i < 512; ++i) q[i] = grid(params[i], 64.0f, 128.0f);
+  for (int u = 0; u < 64; ++u) q[512 + u] = grid(params[512 + u], 128.0f, 65536.0f);
+  for (int u = 0; u < 64; ++u) q[576 + u] = grid(params[576 + u], 64.0f, 128.0f);
+  q[640] = params[640];
+  std::vector<uint32_t> frag(256);
+  for (int t = 0; t < 8; ++t)
+    for (int lane = 0; lane < 32; ++lane) {
+      const int u = 8 * t + lane / 4, kk = 2 * (lane % 4);
+      uint32_t lo, hi;
+      memcpy(&lo, &q[u * 8 + kk], 4);
+      memcpy(&hi, &q[u * 8 + kk + 1], 4);
+      frag[32 * t + lane] = (lo >> 16) | (hi & 0xFFFF0000u);  // exact: 7 significant bits
+    }
+  if (!dec->d_ranker) QD_CK(cudaMalloc(&dec->d_ranker, 644 * 4 + 256 * 4));
+  QD_CK(cudaMemcpy(dec->d_ranker, q.data(), 644 * 4, cudaMemcpyHostToDevice));
+  QD_CK(cudaMemcpy((char*)dec->d_ranker + 644 * 4, frag.data(), 256 * 4, cudaMemcpyHostToDevice));
+  const float* old_q = dec->kp.rkq;
+  const uint32_t* old_b = dec->kp.rkb;
+  dec->kp.rkq = (const float*)dec->d_ranker;
+  dec->kp.rkb = (const uint32_t*)((char*)dec->d_ranker + 644 * 4);
+  if (qd_status st = update_hist(dec, "qd_decoder_set_ranker")) {
+    dec->kp.rkq = old_q;
+    dec->kp.rkb = old_b;
+    return st;
+  }
+  return QD_OK;
+}
+
+qd_status qd_decoder_set_dump(qd_decoder* dec, void* records, int* count, int capacity) {
+  QD_REQ(dec, "null argument");
+  QD_REQ(!records || (count && capacity >= 0), "qd_decoder_set_dump: need count and capacity >= 0");
+  dec->kp.dump = (qd::RankRec*)records;
+  dec->kp.dump_n = records ? count : nullptr;
+  dec->kp.dump_cap = records ? capacity : 0;
+  if (qd_status st = update_hist(dec, "qd_decoder_set_dump")) {
+    dec->kp.dump = nullptr;
+    dec->kp.dump_n = nullptr;
+    dec->kp.dump_cap = 0;
+    return st;
+  }
   return QD_OK;
 }
 
@@ -622,7 +737,8 @@ qd_status qd_wms_info(const qd_wms* m, int out[6]) {
 
 qd_status qd_wms_sample(qd_wms* m, uint64_t seed, uint64_t offset, int64_t n, uint32_t* synd, qd_stream_t stream) {
   QD_REQ(m && synd && n >= 0, "qd_wms_sample: bad argument");
-  QD_CK(qd::launch_wms_sample((cudaStream_t)stream, m->G, m->d_thr, seed, offset, n, 1u + (unsigned)m->k, synd));
+  QD_CK(qd::launch_wms_sample((cudaStream_t)stream, m->G, m->d_thr, seed, offset, n, 1u + (unsigned)m->k, synd,
+                              nullptr, 0, 0, nullptr, 0));
   return QD_OK;
 }
 
@@ -648,6 +764,33 @@ qd_status qd_wms_grad(qd_wms* m, const float* w, const uint32_t* synd, int64_t n
                       float* loss, qd_stream_t stream) {
   QD_REQ(grad_w, "qd_wms_grad: grad_w is required");
   return wms_run(m, w, synd, n, 1, grad_scale, grad_w, loss, nullptr, stream);
+}
+
+qd_status qd_window_sample(qd_decoder* dec, int k, uint64_t seed, uint64_t offset, int64_t n, uint32_t* det_bits,
+                           uint32_t* fault_bits, qd_stream_t stream) {
+  QD_REQ(dec && det_bits && n >= 0, "qd_window_sample: bad argument");
+  QD_REQ(k >= 0 && k < (int)dec->wins.size(), "qd_window_sample: window out of range");
+  WinGpu& g = dec->wins[k];
+  if (!g.d_wthr) {
+    std::vector<uint32_t> thr(g.h.n_cols);
+    for (int c = 0; c < g.h.n_cols; ++c) thr[c] = dec->dem->h.col_thr[g.h.gcols[c]];
+    QD_CK(upload(&g.d_wthr, thr));
+  }
+  const qd::WmsGraph G{g.h.n_rows, g.h.n_cols, g.h.n_edges, (g.h.n_rows + 31) / 32, 1, 1,
+                       g.dv.col_ptr, g.dv.col_rows, g.dv.row_ptr, g.dv.row_ent, g.dv.llr, dec->P.clip};
+  QD_CK(qd::launch_wms_sample((cudaStream_t)stream, G, g.d_wthr, seed, offset, n, 1u + (unsigned)k, nullptr,
+                              det_bits, (dec->dem->h.n_det + 31) / 32, g.h.row0, fault_bits, dec->corr_words));
+  return QD_OK;
+}
+
+qd_status qd_ranker_eval(const float* params, const void* records, const uint8_t* labels, int64_t n, int quantize,
+                         float pos_weight, float grad_scale, float* grad, float* loss, float* score,
+                         qd_stream_t stream) {
+  QD_REQ(params && records && n >= 0, "qd_ranker_eval: bad argument");
+  QD_REQ(!(grad || loss) || labels, "qd_ranker_eval: labels are required for grad and loss");
+  QD_CK(qd::launch_ranker((cudaStream_t)stream, params, (const qd::RankRec*)records, labels, n, quantize,
+                          pos_weight, grad_scale, grad, loss, score));
+  return QD_OK;
 }
 
 qd_status qd_adam_step(float* w, const float* g, float* m1, float* m2, int64_t n, float lr, float beta1, float beta2,

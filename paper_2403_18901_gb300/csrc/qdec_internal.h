@@ -41,6 +41,7 @@ struct KParams;
 struct WinDev;
 struct Layout;
 struct WmsGraph;
+struct RankRec;
 
 // Build the merged DEM (backward sensitivity sweep over the circuit).
 bool build_dem_host(const qd_bb_code& code, const qd_noise& noise, DemHost& out);
@@ -73,7 +74,11 @@ cudaError_t launch_wms(cudaStream_t st, int grid, size_t smem, const WmsGraph& G
                        long long n, int backward, float grad_scale, float* grad_w, float* loss, float* post,
                        float* scratch, size_t scratch_per_cta, int* work);
 cudaError_t launch_wms_sample(cudaStream_t st, const WmsGraph& G, const uint32_t* thr, unsigned long long seed,
-                              unsigned long long off, long long n, unsigned domain, uint32_t* synd);
+                              unsigned long long off, long long n, unsigned domain, uint32_t* synd, uint32_t* det,
+                              int det_words, int row0, uint32_t* fault, int cw);
+cudaError_t launch_ranker(cudaStream_t st, const float* params, const RankRec* recs, const uint8_t* labels,
+                          long long n, int quantize, float pos_weight, float scale, float* grad, float* loss,
+                          float* score);
 cudaError_t launch_adam(cudaStream_t st, float* w, const float* g, float* m, float* v, long long n, float lr,
                         float b1, float b2, float eps, int step);
 

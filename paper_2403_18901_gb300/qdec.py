@@ -76,6 +76,10 @@ _SIGS = {
     "qd_decoder_set_launch": (_I, [_VP, _I]),
     "qd_decoder_launch_info": (_I, [_VP, _I, _VP]),
     "qd_decoder_set_weights": (_I, [_VP, _I, _VP, _I]),
+    "qd_decoder_set_ranker": (_I, [_VP, _VP]),
+    "qd_decoder_set_dump": (_I, [_VP, _VP, _VP, _I]),
+    "qd_window_sample": (_I, [_VP, _I, _U64, _U64, _I64, _VP, _VP, _VP]),
+    "qd_ranker_eval": (_I, [_VP, _VP, _VP, _I64, _I, C.c_float, C.c_float, _VP, _VP, _VP, _VP]),
     "qd_wms_create": (_I, [_VP, _I, _I, _I, C.POINTER(_VP)]),
     "qd_wms_destroy": (_I, [_VP]),
     "qd_wms_info": (_I, [_VP, _VP]),
@@ -256,6 +260,33 @@ class Decoder:
         self._w = getattr(self, "_w", {})
         self._w[k] = w
         _check(lib().qd_decoder_set_weights(self.h, k, _ptr(w), w.shape[0]))
+
+    def set_ranker(self, params):
+        """params: 641 float32 values W1[64][8], b1[64], W2[64], b2 (host
+        array, copied), or None for the argmin of Alg. 1."""
+        if params is None:
+            _check(lib().qd_decoder_set_ranker(self.h, None))
+            return
+        r = np.ascontiguousarray(params, np.float32).reshape(-1)
+        assert r.size == 641
+        _check(lib().qd_decoder_set_ranker(self.h, _ptr(r)))
+
+    def set_dump(self, records, count):
+        """records: CUDA uint8 tensor [capacity, 48] (qd_rank_rec_t rows),
+        count: CUDA int32 tensor [1] (caller zeroes it); None turns the dump off."""
+        if records is None:
+            _check(lib().qd_decoder_set_dump(self.h, None, None, 0))
+            self._dump = None
+            return
+        assert records.is_cuda and records.dim() == 2 and records.shape[1] == 48
+        self._dump = (records, count)
+        _check(lib().qd_decoder_set_dump(self.h, _ptr(records), _ptr(count), records.shape[0]))
+
+    def window_sample(self, k, seed, offset, n, det, fault=None, stream=None):
+        """Window-local samples of window k into det [n][det_words] (and the
+        fired window columns into fault [n][corr_words])."""
+        _check(lib().qd_window_sample(self.h, k, seed, offset, n, _ptr(det), _ptr(fault) if fault is not None
+                                      else None, _stream(stream)))
 
     def launch_info(self, k=0):
         out = np.zeros(6, np.int32)

@@ -61,7 +61,7 @@ def test_sampler_bit_exact(key, R, n, off):
     assert (_u32(obs) == oo).all()
 
 
-def _pipeline(key, R, p, params, n, seed, trace_windows=(), mode=0, weights=None):
+def _pipeline(key, R, p, params, n, seed, trace_windows=(), mode=0, weights=None, ranker=None):
     """Run both implementations window by window on the same oracle-sampled
     shots; compare everything.  mode: launch shape (0 automatic, 1 one warp per
     decision path, 2 one CTA per decision path).  Returns (oracle fail, gpu fail)."""
@@ -72,8 +72,11 @@ def _pipeline(key, R, p, params, n, seed, trace_windows=(), mode=0, weights=None
     if weights is not None:
         for k, w in weights.items():
             dec.set_weights(k, torch.from_numpy(w).cuda())
+    if ranker is not None:
+        dec.set_ranker(ranker)
     det0, obs0 = o.sample(seed, 0, n)
-    ofail, opred, ocorr = o.run_shots(params, det0, obs0, threads=8, want_corr=True, weights=weights)
+    ofail, opred, ocorr = o.run_shots(params, det0, obs0, threads=8, want_corr=True, weights=weights,
+                                       ranker=ranker)
     det = _to_dev(det0)
     obs = _to_dev(obs0)
     corr = torch.zeros((n, dec.corr_words), dtype=torch.int32, device="cuda")
@@ -100,7 +103,7 @@ def _pipeline(key, R, p, params, n, seed, trace_windows=(), mode=0, weights=None
             s_all = _bits(host_det, o.n_det)
             for sh in range(n):
                 synd = s_all[sh, win["r0"] * o.w: win["r0"] * o.w + win["n_rows"]]
-                oc, oinfo, otr = o.decode_window(params, k, synd, trace=True, weights=weights)
+                oc, oinfo, otr = o.decode_window(params, k, synd, trace=True, weights=weights, ranker=ranker)
                 gt = dec.parse_trace(trn[sh])
                 assert gt["head"][0] == int(oinfo["prebp_converged"])
                 assert gt["head"][3] == oinfo["prebp_iters"]
