@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--train-batch", type=int, default=4096)
     ap.add_argument("--ranker-steps", type=int, default=300,
                     help="Adam steps of the decimation ranker (0: skip)")
+    ap.add_argument("--batch-shots", type=int, default=30000,
+                    help="shots per code of the batched uneven workload (0: skip)")
     ap.add_argument("--ranker-shots", type=int, default=4096,
                     help="window samples per collection round for the ranker (4 rounds)")
     return ap.parse_args()
@@ -188,6 +190,104 @@ class ClockSampler:
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def batched_uneven(args, torch, qdec, CODES, preset):
+    """[[90,8,10]], [[108,8,10]] and [[144,12,12]] (p = 0.003, d rounds) with
+    W = 2 + (shot mod 3): one decoder per (code, W) holding a third of the
+    code's shots, all advanced together by qd_batch_step (one decode and one
+    commit launch per window step), shapes from qd_batch_autotune, the whole
+    window loop replayed as one CUDA graph.  Compared with the same decoders
+    run one after another (qd_decode_all each)."""
+    p = 0.003
+    codes = [("90", 10), ("108", 10), ("144", 12)]
+    per = args.batch_shots // 3
+    mem = []
+    for ci, (key, R) in enumerate(codes):
+        dem = qdec.Dem(CODES[key], p, R)
+        for W in (2, 3, 4):
+            params = preset(args.preset, k_guess=K_GUESS, p=p, W=W)
+            dec = qdec.Decoder(dem, params, max_shots=per)
+            det, obs = dem.sample(args.seed + 7 * ci, W * per, per)  # disjoint shot ranges per (code, W)
+            mem.append(dict(key=key, R=R, W=W, dem=dem, dec=dec, det=det, obs=obs))
+    n = [per] * len(mem)
+    b = qdec.Batch([m["dec"] for m in mem])
+    # autotune the interior step on a slice of the shots; use that shape everywhere it fits
+    tune_n = [min(per, 1024)] * len(mem)
+    default = b.info(1)
+    tune_ms = b.autotune(1, [m["det"] for m in mem], tune_n, reps=1)
+    shape = b.info(1)
+    for j in range(b.n_steps):
+        try:
+            b.set_shape(j, shape["warps"], shape["ctas_per_sm"])
+        except qdec.QdError:
+            pass
+    det = [m["det"].clone() for m in mem]
+    pred = [torch.zeros(per, dtype=torch.int32, device="cuda") for _ in mem]
+    resid = [torch.zeros(per, dtype=torch.int32, device="cuda") for _ in mem]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for j in range(b.n_steps):
+            b.step(j, det, n, pred, resid, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        for j in range(b.n_steps):
+            b.step(j, det, n, pred, resid, stream=s)
+
+    def reset():
+        for i, m in enumerate(mem):
+            det[i].copy_(m["det"])
+            pred[i].zero_()
+            resid[i].zero_()
+
+    reset()
+    g.replay()  # warm-up
+    torch.cuda.synchronize()
+    reset()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1000.0
+    windows = sum(per * m["dec"].n_windows for m in mem)
+    out_members = []
+    for i, m in enumerate(mem):
+        pr = pred[i].cpu().numpy().view(np.uint32)
+        rs = resid[i].cpu().numpy().view(np.uint32)
+        ob = m["obs"].cpu().numpy().view(np.uint32)
+        f = int(((rs & 1) | (pr != ob)).astype(bool).sum())
+        lo, hi = wilson(f, per)
+        out_members.append({"code": CODES[m["key"]]["name"], "rounds": m["R"], "W": m["W"], "shots": per,
+                            "windows": per * m["dec"].n_windows, "failures": f,
+                            "p_L": per_round(f / per, m["R"]),
+                            "wilson95": [per_round(lo, m["R"]), per_round(hi, m["R"])]})
+    # the same decoders one after another
+    wk = [m["det"].clone() for m in mem]
+    pr2 = torch.zeros(per, dtype=torch.int32, device="cuda")
+    fl2 = torch.zeros(per, dtype=torch.int32, device="cuda")
+    nf2 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for i, m in enumerate(mem):  # warm-up
+        m["dec"].decode_all(wk[i], m["obs"], per, pr2, fl2, nf2)
+    for i, m in enumerate(mem):
+        wk[i].copy_(m["det"])
+    torch.cuda.synchronize()
+    e0.record()
+    for i, m in enumerate(mem):
+        m["dec"].decode_all(wk[i], m["obs"], per, pr2, fl2, nf2)
+    e1.record()
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) / 1000.0
+    return {"workload": "[[90,8,10]] x10 rounds, [[108,8,10]] x10, [[144,12,12]] x12; p=0.003; "
+                        "W = 2 + (shot mod 3); GDG 2^4 paths",
+            "shots_per_code": 3 * per, "members": len(mem), "window_steps": b.n_steps,
+            "launches_per_pass": 3 * b.n_steps,
+            "value": windows / t_batch, "unit": "windows/s", "seconds": t_batch,
+            "sequential_value": windows / t_seq, "sequential_seconds": t_seq,
+            "autotune": {"step": 1, "default": default, "chosen": shape, "ms": tune_ms,
+                         "shots_per_member": tune_n[0]},
+            "cuda_graph": "one graph of all window steps", "per_member": out_members}
 
 
 def measured_peaks():
@@ -351,6 +451,9 @@ def main():
                   "edge_iterations_per_window": float(cr[0] + cr[1]) / (B * nwin * args.steps),
                   "gdg_windows_frac": float(cr[3]) / (B * nwin * args.steps),
                   "launch": rlaunch, "failures": fail_r}
+    batched = None
+    if args.batch_shots > 0 and rank == 0:
+        batched = batched_uneven(args, torch, qdec, CODES, preset)
     if world > 1:
         fl = torch.tensor([failures], device="cuda")
         torch.distributed.all_reduce(fl)
@@ -487,6 +590,7 @@ def main():
             "wall_s_timed": t_wall,
             "learned": learned,
             "ranker": ranked,
+            "batched_uneven": batched,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

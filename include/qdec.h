@@ -252,6 +252,55 @@ qd_status qd_decode_commit_static(qd_decoder* dec, int k, uint32_t* det_bits, in
                                   uint32_t* obs_pred, uint32_t* residue_fail, qd_stream_t stream);
 
 /*
+ * Batched window steps (no counterpart in the paper, which decodes one code
+ * and window size at a time): several decoders -- different codes, noise
+ * levels or window sizes W -- advance together.  Window step j decodes window
+ * j of every member that has one, in ONE persistent launch (shots of all
+ * members share the CTAs through one work counter, heavier windows first),
+ * then commits all of them in one launch (Eq. (10)-(11)).  Results are
+ * identical to qd_decode_windows + qd_commit_and_slide per member.  The batch
+ * borrows the members (which must outlive it) and their correction buffers:
+ * members of a batch must not run other decodes concurrently.
+ */
+typedef struct qd_batch qd_batch;
+qd_status qd_batch_create(qd_decoder* const* members, int n_members, qd_batch** out); /* 1..16 members */
+qd_status qd_batch_destroy(qd_batch* b);
+/* number of window steps: the largest member window count */
+qd_status qd_batch_n_steps(const qd_batch* b, int* n_steps);
+/*
+ * One window step.  Host arrays of per-member DEVICE pointers / counts:
+ *   det_bits[i]     [n_shots[i]][det_words_i], updated in place by the commit
+ *   obs_pred[i]     [n_shots[i]], ^= L e_commit
+ *   residue_fail[i] [n_shots[i]], |= the Eq. (11) residue flag
+ * Members without window `step`, or with n_shots[i] = 0, are skipped.
+ * Asynchronous on `stream`; capturable in a CUDA graph (it launches a memset
+ * and two kernels).
+ */
+qd_status qd_batch_step(qd_batch* b, int step, uint32_t* const* det_bits, const int64_t* n_shots,
+                        uint32_t* const* obs_pred, uint32_t* const* residue_fail, qd_stream_t stream);
+/*
+ * CTA shape of step `step`: `warps` warps per CTA (1..8) and a shared-memory
+ * budget that leaves room for `ctas_per_sm` (1 or 2) CTAs per SM.  Every
+ * member's layout takes as many decision-path slots (one per warp, at most
+ * `warps`) as fit in the budget, so small windows run a path on every warp and
+ * large ones on fewer.  Default: 8 warps, two CTAs per SM where every member
+ * fits.  QD_EUNSUPPORTED when a member's window does not fit one slot.
+ */
+qd_status qd_batch_set_shape(qd_batch* b, int step, int warps, int ctas_per_sm);
+/* out = {warps, dynamic shared bytes, CTAs per SM, members with this step} */
+qd_status qd_batch_info(const qd_batch* b, int step, int out[4]);
+/*
+ * Autotuner: times the decode launch of step `step` on the given inputs for
+ * every shape (4..8 warps x 1 or 2 CTAs per SM) that fits (one warm-up +
+ * `reps` timed launches each, CUDA events
+ * on `stream`, synchronous), keeps the fastest and returns its mean time in
+ * *best_ms (may be NULL).  Writes only the members' correction buffers; the
+ * inputs are not modified.  Not capturable.
+ */
+qd_status qd_batch_autotune(qd_batch* b, int step, uint32_t* const* det_bits, const int64_t* n_shots, int reps,
+                            qd_stream_t stream, float* best_ms);
+
+/*
  * Learned weighted min-sum for window k (no counterpart in the paper: the
  * fixed normalisation alpha of Eq. (1) becomes a per-edge, per-iteration
  * weight).  w: device [T][n_edges of window k], FP32, indexed by the window's

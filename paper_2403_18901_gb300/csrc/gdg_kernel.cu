@@ -30,6 +30,7 @@
 #include <cstdint>
 
 #include "gdg_kernel.cuh"
+#include "qdec_internal.h"
 
 namespace qd {
 namespace dev {
@@ -746,6 +747,34 @@ struct DecodeArgs {
   int sw_max;
 };
 
+// One window step of several decoders in one launch (kernel parameter).
+struct BatchArgs {
+  int n_seg;
+  unsigned q_off;  // shared-memory offset of the launch's own work slot
+  int* work;
+  long long seg_end[kMaxBatch];  // cumulative shot counts
+  DecodeArgs seg[kMaxBatch];
+};
+
+// Commit (Eq. (10)) + residue test (Eq. (11)) of one decoder's window.
+struct CommitArgs {
+  int n_commit;
+  const int *cptr, *cdet;
+  const uint32_t* cobs;
+  int corr_words;
+  const uint32_t* corr;
+  long long n;
+  uint32_t* det;
+  int det_words;
+  uint32_t *obs_pred, *resid;
+  int b0, b1;
+};
+struct CommitBatch {
+  int n_seg;
+  long long seg_end[kMaxBatch];
+  CommitArgs seg[kMaxBatch];
+};
+
 // a1 + a2 (+ a3 when not converged): the shared prefix of both launch shapes.
 // Returns true when the pre-BP converged (cbits then hold its decision).
 template <bool LW, bool WIDE>
@@ -1030,10 +1059,11 @@ __device__ void write_outputs(const DecodeArgs& A, char* sm, long long shot, boo
   }
 }
 
-// ---- shot mode: persistent CTAs of 8 warps, one warp per decision path ----
+// ---- shot mode: persistent CTAs of up to 8 warps, one warp per decision path ----
+// One shot of one window by the whole CTA (every thread calls).  misc[2], the
+// decision-path queue, must be 0 on entry.
 template <bool LW>
-__global__ void __launch_bounds__(256, 2) decode_shot_kernel(DecodeArgs A) {
-  extern __shared__ __align__(16) char sm[];
+__device__ void shot_body(const DecodeArgs& A, long long shot, char* sm) {
   const Layout& L = A.L;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int* misc = (int*)(sm + L.misc);
@@ -1042,21 +1072,14 @@ __global__ void __launch_bounds__(256, 2) decode_shot_kernel(DecodeArgs A) {
   uint32_t* res_e = (uint32_t*)(sm + L.res_ebits);
   uint32_t* cbits = (uint32_t*)(sm + L.cbits);
   const uint16_t* sel = (const uint16_t*)(sm + L.sel);
-  while (true) {
-    __syncthreads();
-    if (tid == 0) {
-      misc[0] = atomicAdd(A.work, 1);
-      misc[2] = 0;  // decision-path queue, path 0 first
-    }
-    __syncthreads();
-    const long long shot = misc[0];
-    if (shot >= A.n_shots) break;
-    char* tr = A.trace ? A.trace + (size_t)shot * A.tr_bytes : nullptr;
-    int t_run = 0;
-    const bool conv = window_prefix<LW, false>(A, A.W, sm, shot, &t_run);
-    int winner = -1;
-    const int n_short = conv ? 0 : A.W.n_short;
-    if (!conv) {
+  char* tr = A.trace ? A.trace + (size_t)shot * A.tr_bytes : nullptr;
+  int t_run = 0;
+  const bool conv = window_prefix<LW, false>(A, A.W, sm, shot, &t_run);
+  int winner = -1;
+  const int n_short = conv ? 0 : A.W.n_short;
+  if (!conv) {
+    // warps beyond the layout's path slots (batched launches) sit out the paths
+    if (warp < L.nslots) {
       const ShortG G = short_graph(sm, L, A.W, n_short);
       const Slot B = make_slot(sm + L.U + (size_t)warp * L.b_size, L);
       const WarpGrp g{lane};
@@ -1071,26 +1094,69 @@ __global__ void __launch_bounds__(256, 2) decode_shot_kernel(DecodeArgs A) {
         o.ebits = res_e + (size_t)id * L.sw;
         run_path<LW>(A.P, G, B, id, g, o, A.dmx);
       }
-      __syncthreads();
-      // ---- a8: least path metric, ties to the lowest id ----
-      if (tid == 0) {
-        int best = -1;
-        double bp = CUDART_INF;
-        for (int id = 0; id < A.P.nb; ++id)
-          if (res_status[id] == BR_CONVERGED && res_pm[id] < bp) {
-            bp = res_pm[id];
-            best = id;
-          }
-        misc[1] = best;
-      }
-      __syncthreads();
-      winner = misc[1];
-      const uint32_t* eb = res_e + (size_t)(winner >= 0 ? winner : 0) * L.sw;
-      for (int k = tid; k < n_short; k += blockDim.x)
-        if ((eb[k >> 5] >> (k & 31)) & 1u) atomicOr(&cbits[sel[k] >> 5], 1u << (sel[k] & 31));
-      __syncthreads();
     }
-    write_outputs(A, sm, shot, conv, winner, n_short, t_run, tr);
+    __syncthreads();
+    // ---- a8: least path metric, ties to the lowest id ----
+    if (tid == 0) {
+      int best = -1;
+      double bp = CUDART_INF;
+      for (int id = 0; id < A.P.nb; ++id)
+        if (res_status[id] == BR_CONVERGED && res_pm[id] < bp) {
+          bp = res_pm[id];
+          best = id;
+        }
+      misc[1] = best;
+    }
+    __syncthreads();
+    winner = misc[1];
+    const uint32_t* eb = res_e + (size_t)(winner >= 0 ? winner : 0) * L.sw;
+    for (int k = tid; k < n_short; k += blockDim.x)
+      if ((eb[k >> 5] >> (k & 31)) & 1u) atomicOr(&cbits[sel[k] >> 5], 1u << (sel[k] & 31));
+    __syncthreads();
+  }
+  write_outputs(A, sm, shot, conv, winner, n_short, t_run, tr);
+}
+
+template <bool LW>
+__global__ void __launch_bounds__(256, 2) decode_shot_kernel(DecodeArgs A) {
+  extern __shared__ __align__(16) char sm[];
+  int* misc = (int*)(sm + A.L.misc);
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      misc[0] = atomicAdd(A.work, 1);
+      misc[2] = 0;  // decision-path queue, path 0 first
+    }
+    __syncthreads();
+    const long long shot = misc[0];
+    if (shot >= A.n_shots) break;
+    shot_body<LW>(A, shot, sm);
+  }
+}
+
+// ---- batched shot mode: one persistent launch over the same window step of
+// several decoders (codes and window sizes of different shapes).  Shots are
+// numbered across the members in table order; a CTA takes the next one and
+// runs it with that member's graph, layout and buffers.  A member's layout
+// has as many path slots as fit in the launch's shared memory (at most one
+// per warp): small windows use every warp, large ones fewer. ----
+template <bool LW>
+__global__ void __launch_bounds__(256, 2) decode_batch_kernel(const __grid_constant__ BatchArgs B) {
+  extern __shared__ __align__(16) char sm[];
+  int* q = (int*)(sm + B.q_off);
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) q[0] = atomicAdd(B.work, 1);
+    __syncthreads();
+    const long long g = q[0];
+    if (g >= B.seg_end[B.n_seg - 1]) break;
+    int m = 0;
+    while (g >= B.seg_end[m]) ++m;
+    const DecodeArgs& A = B.seg[m];
+    const long long shot = g - (m ? B.seg_end[m - 1] : 0);
+    if (threadIdx.x == 0) ((int*)(sm + A.L.misc))[2] = 0;
+    __syncthreads();
+    shot_body<LW>(A, shot, sm);
   }
 }
 
@@ -1232,45 +1298,54 @@ __global__ void sample_kernel(int n_cols, const uint32_t* __restrict__ thr, cons
   }
 }
 
-// Commit (Eq. (10)) + residue test (Eq. (11)); one thread per shot.
-__global__ void commit_kernel(int n_commit, const int* __restrict__ cptr, const int* __restrict__ cdet,
-                              const uint32_t* __restrict__ cobs, int corr_words,
-                              const uint32_t* __restrict__ corr, long long n, uint32_t* __restrict__ det,
-                              int det_words, uint32_t* __restrict__ obs_pred, uint32_t* __restrict__ resid,
-                              int res_b0, int res_b1) {
-  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const uint32_t* c = corr + (size_t)s * corr_words;
-  uint32_t* d = det + (size_t)s * det_words;
+// Commit (Eq. (10)) + residue test (Eq. (11)) of shot s.
+__device__ void commit_one(const CommitArgs& C, long long s) {
+  const uint32_t* c = C.corr + (size_t)s * C.corr_words;
+  uint32_t* d = C.det + (size_t)s * C.det_words;
   uint32_t ob = 0;
-  const int nw = (n_commit + 31) >> 5;
+  const int nw = (C.n_commit + 31) >> 5;
   for (int x = 0; x < nw; ++x) {
     uint32_t m = c[x];
-    const int rem = n_commit - 32 * x;
+    const int rem = C.n_commit - 32 * x;
     if (rem < 32) m &= (1u << rem) - 1u;
     while (m) {
       const int b = __ffs(m) - 1;
       m &= m - 1;
       const int col = 32 * x + b;
-      for (int e = cptr[col]; e < cptr[col + 1]; ++e) {
-        const int q = cdet[e];
+      for (int e = C.cptr[col]; e < C.cptr[col + 1]; ++e) {
+        const int q = C.cdet[e];
         d[q >> 5] ^= 1u << (q & 31);
       }
-      ob ^= cobs[col];
+      ob ^= C.cobs[col];
     }
   }
-  obs_pred[s] ^= ob;
+  C.obs_pred[s] ^= ob;
   uint32_t bad = 0;
-  for (int q = res_b0; q < res_b1;) {
+  for (int q = C.b0; q < C.b1;) {
     const int wq = q >> 5, lo = q & 31;
-    const int hiq = min(res_b1, (wq + 1) * 32);
+    const int hiq = min(C.b1, (wq + 1) * 32);
     uint32_t m = d[wq] >> lo;
     const int nb = hiq - q;
     if (nb < 32) m &= (1u << nb) - 1u;
     bad |= m;
     q = hiq;
   }
-  if (bad) resid[s] |= 1u;
+  if (bad) C.resid[s] |= 1u;
+}
+
+// one thread per shot
+__global__ void commit_kernel(const CommitArgs C) {
+  const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < C.n) commit_one(C, s);
+}
+
+// one thread per shot over several decoders' shots
+__global__ void commit_batch_kernel(const __grid_constant__ CommitBatch B) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= B.seg_end[B.n_seg - 1]) return;
+  int m = 0;
+  while (g >= B.seg_end[m]) ++m;
+  commit_one(B.seg[m], g - (m ? B.seg_end[m - 1] : 0));
 }
 
 __global__ void evaluate_kernel(const uint32_t* __restrict__ pred, const uint32_t* __restrict__ obs,
@@ -1302,7 +1377,56 @@ cudaError_t set_decode_smem(size_t bytes) {
     e = cudaFuncSetAttribute(dev::decode_path_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(dev::decode_path_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(dev::decode_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(dev::decode_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   return e;
+}
+
+cudaError_t batch_occupancy(int threads, size_t smem, int* blocks) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::decode_batch_kernel<false>, threads, smem);
+}
+
+cudaError_t launch_decode_batch(cudaStream_t st, int grid, int threads, size_t smem, unsigned q_off, int* work,
+                                const BatchMember* m, int n) {
+  if (n <= 0 || n > kMaxBatch) return n <= 0 ? cudaSuccess : cudaErrorInvalidValue;
+  dev::BatchArgs B{};
+  B.n_seg = n;
+  B.q_off = q_off;
+  B.work = work;
+  bool lw = false;
+  long long end = 0;
+  for (int i = 0; i < n; ++i) {
+    const BatchMember& x = m[i];
+    end += x.n;
+    B.seg_end[i] = end;
+    B.seg[i] = dev::DecodeArgs{*x.P,   *x.W,   *x.L,     x.det,      x.det_words, x.n,      x.corr,
+                               x.corr_words, nullptr, nullptr, 0,     x.dmx,    x.ns_max, nullptr,
+                               x.counters, nullptr, nullptr, x.sw_max};
+    lw = lw || x.W->wts != nullptr;
+  }
+  if (lw) dev::decode_batch_kernel<true><<<grid, threads, smem, st>>>(B);
+  else dev::decode_batch_kernel<false><<<grid, threads, smem, st>>>(B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_commit_batch(cudaStream_t st, const BatchMember* m, int n) {
+  if (n <= 0 || n > kMaxBatch) return n <= 0 ? cudaSuccess : cudaErrorInvalidValue;
+  dev::CommitBatch B{};
+  B.n_seg = n;
+  long long end = 0;
+  for (int i = 0; i < n; ++i) {
+    const BatchMember& x = m[i];
+    end += x.n;
+    B.seg_end[i] = end;
+    B.seg[i] = dev::CommitArgs{x.n_commit, x.cptr, x.cdet, x.cobs, x.corr_words, x.corr, x.n,
+                               (uint32_t*)x.det, x.det_words, x.obs_pred, x.resid, x.b0, x.b1};
+  }
+  if (end == 0) return cudaSuccess;
+  const int tpb = 128;
+  dev::commit_batch_kernel<<<(unsigned)((end + tpb - 1) / tpb), tpb, 0, st>>>(B);
+  return cudaGetLastError();
 }
 
 cudaError_t decode_occupancy(int mode, int threads, size_t smem, int* blocks) {
@@ -1344,9 +1468,8 @@ cudaError_t launch_commit(cudaStream_t st, int n_commit, const int* cptr, const 
                           uint32_t* obs_pred, uint32_t* resid, int b0, int b1) {
   if (n <= 0) return cudaSuccess;
   const int tpb = 128;
-  dev::commit_kernel<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, st>>>(n_commit, cptr, cdet, cobs, corr_words,
-                                                                      corr, n, det, det_words, obs_pred, resid,
-                                                                      b0, b1);
+  const dev::CommitArgs C{n_commit, cptr, cdet, cobs, corr_words, corr, n, det, det_words, obs_pred, resid, b0, b1};
+  dev::commit_kernel<<<(unsigned)((n + tpb - 1) / tpb), tpb, 0, st>>>(C);
   return cudaGetLastError();
 }
 

@@ -15,6 +15,8 @@
 
 namespace qd {
 
+constexpr int kMaxBatch = 16;  // decoders in one batched launch
+
 struct KParams {
   float alpha, clip, pa_main, pa_other, pb_main, pb_other, pb_d1, pc, pd;
   int n_pre, ips, dmax_main, dmax_other, k, low_err, peel_init, pc_max_depth, n_unsat_min;

@@ -28,6 +28,12 @@ using qd::set_error;
     }                                                                                 \
   } while (0)
 
+#define QD_CK_ST(call)             \
+  do {                             \
+    const qd_status s_ = (call);   \
+    if (s_ != QD_OK) return s_;    \
+  } while (0)
+
 #define QD_REQ(cond, msg)    \
   do {                       \
     if (!(cond)) {           \
@@ -667,6 +673,258 @@ extern "C" qd_status qd_decode_commit_static(qd_decoder* dec, int k, uint32_t* d
                           det_bits, dw, obs_pred, residue_fail, g.h.r0 * w, g.h.commit_b1 * w));
   return QD_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batched window steps over several decoders (codes / window sizes).
+struct qd_batch {
+  std::vector<qd_decoder*> mem;
+  int n_steps = 0, sm_count = 0, optin = 0;
+  size_t budget2 = 0;  // dynamic shared bytes that leave room for two CTAs per SM
+  struct Step {
+    int warps = 1, blocks = 1;
+    size_t budget = 0, smem = 0;
+    unsigned q_off = 0;
+    std::vector<qd::Layout> L;  // per member (unused where the member has no such window)
+  };
+  std::vector<Step> steps;
+  int* d_work = nullptr;  // one counter per step
+};
+
+namespace {
+// CTAs of `warps` warps with at most `budget` bytes of dynamic shared memory:
+// each member's layout takes as many path slots (<= warps) as fit.
+qd_status batch_plan(qd_batch* b, int j, int warps, size_t budget) {
+  qd_batch::Step S;
+  S.L.assign(b->mem.size(), qd::Layout{});
+  unsigned mx = 0;
+  for (size_t i = 0; i < b->mem.size(); ++i) {
+    const qd_decoder* d = b->mem[i];
+    if (j >= (int)d->wins.size()) continue;
+    const auto& h = d->wins[j].h;
+    int s = warps;
+    for (; s >= 1; --s) {
+      S.L[i] = qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, d->kp.nb, s, false,
+                               d->hist_on);
+      if (qd::al16(S.L[i].total) + 16 <= budget) break;
+    }
+    if (s < 1) {
+      set_error("qd_batch: member " + std::to_string(i) + " window " + std::to_string(j) + " needs " +
+                std::to_string(S.L[i].total + 16) + " B of shared memory with one path slot (budget " +
+                std::to_string(budget) + ")");
+      return QD_EUNSUPPORTED;
+    }
+    mx = std::max(mx, S.L[i].total);
+  }
+  S.q_off = qd::al16(mx);
+  S.smem = S.q_off + 16;
+  S.warps = warps;
+  S.budget = budget;
+  int blocks = 0;
+  QD_CK(qd::batch_occupancy(32 * warps, S.smem, &blocks));
+  S.blocks = std::max(1, blocks);
+  b->steps[j] = S;
+  return QD_OK;
+}
+
+// The member table of step j; returns the number of members with work.
+int batch_members(qd_batch* b, int j, uint32_t* const* det, const int64_t* n, uint32_t* const* obs_pred,
+                  uint32_t* const* resid, std::vector<qd::BatchMember>& out) {
+  out.clear();
+  // heavier windows first, so the tail of the persistent launch is short
+  std::vector<int> order;
+  for (size_t i = 0; i < b->mem.size(); ++i)
+    if (j < (int)b->mem[i]->wins.size() && n[i] > 0) order.push_back((int)i);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return b->mem[x]->wins[j].h.n_edges > b->mem[y]->wins[j].h.n_edges;
+  });
+  for (int i : order) {
+    qd_decoder* d = b->mem[i];
+    const WinGpu& g = d->wins[j];
+    qd::BatchMember m{};
+    m.P = &d->kp;
+    m.W = &g.dv;
+    m.L = &b->steps[j].L[i];
+    m.det = det[i];
+    m.det_words = (d->dem->h.n_det + 31) / 32;
+    m.n = n[i];
+    m.corr = d->d_corr;
+    m.corr_words = d->corr_words;
+    m.dmx = d->dmx;
+    m.ns_max = d->ns_max;
+    m.sw_max = d->sw_max;
+    m.counters = d->d_counters;
+    m.n_commit = g.h.n_commit;
+    m.cptr = g.d_ccptr;
+    m.cdet = g.d_ccdet;
+    m.cobs = g.d_ccobs;
+    m.obs_pred = obs_pred ? obs_pred[i] : nullptr;
+    m.resid = resid ? resid[i] : nullptr;
+    const int w = d->dem->h.w;
+    m.b0 = g.h.r0 * w;
+    m.b1 = g.h.commit_b1 * w;
+    out.push_back(m);
+  }
+  return (int)out.size();
+}
+
+qd_status batch_decode(qd_batch* b, int j, const std::vector<qd::BatchMember>& m, cudaStream_t st) {
+  const qd_batch::Step& S = b->steps[j];
+  long long tot = 0;
+  for (const auto& x : m) tot += x.n;
+  QD_CK(cudaMemsetAsync(b->d_work + j, 0, sizeof(int), st));
+  const long long grid = std::min<long long>(tot, (long long)b->sm_count * S.blocks);
+  QD_CK(qd::launch_decode_batch(st, (int)grid, 32 * S.warps, S.smem, S.q_off, b->d_work + j, m.data(),
+                                (int)m.size()));
+  return QD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+qd_status qd_batch_create(qd_decoder* const* members, int n_members, qd_batch** out) {
+  QD_REQ(members && out, "qd_batch_create: null argument");
+  QD_REQ(n_members >= 1 && n_members <= qd::kMaxBatch,
+         "qd_batch_create: need 1 <= n_members <= " + std::to_string(qd::kMaxBatch));
+  std::unique_ptr<qd_batch> b(new (std::nothrow) qd_batch());
+  if (!b) return QD_ENOMEM;
+  for (int i = 0; i < n_members; ++i) {
+    QD_REQ(members[i], "qd_batch_create: null member");
+    b->mem.push_back(members[i]);
+    b->n_steps = std::max(b->n_steps, (int)members[i]->wins.size());
+  }
+  int dev = 0;
+  QD_CK(cudaGetDevice(&dev));
+  QD_CK(cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev));
+  QD_CK(cudaDeviceGetAttribute(&b->optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  QD_CK(qd::set_decode_smem((size_t)b->optin));
+  int per_sm = 0, reserved = 0;
+  QD_CK(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  QD_CK(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+  b->budget2 = (size_t)std::max(0, per_sm / 2 - reserved);
+  b->steps.resize(b->n_steps);
+  // default shape: 8 warps, two CTAs per SM when every member fits a slot
+  for (int j = 0; j < b->n_steps; ++j)
+    if (batch_plan(b.get(), j, kShotWarps, b->budget2) != QD_OK)
+      QD_CK_ST(batch_plan(b.get(), j, kShotWarps, (size_t)b->optin));
+  QD_CK(cudaMalloc(&b->d_work, sizeof(int) * std::max(1, b->n_steps)));
+  *out = b.release();
+  return QD_OK;
+}
+
+qd_status qd_batch_destroy(qd_batch* b) {
+  if (!b) return QD_OK;
+  cudaFree(b->d_work);
+  delete b;
+  return QD_OK;
+}
+
+qd_status qd_batch_n_steps(const qd_batch* b, int* n) {
+  QD_REQ(b && n, "null argument");
+  *n = b->n_steps;
+  return QD_OK;
+}
+
+qd_status qd_batch_set_shape(qd_batch* b, int step, int warps, int ctas_per_sm) {
+  QD_REQ(b, "null argument");
+  QD_REQ(step >= 0 && step < b->n_steps, "qd_batch_set_shape: step out of range");
+  QD_REQ(warps >= 1 && warps <= kShotWarps, "qd_batch_set_shape: warps must be in [1, 8]");
+  QD_REQ(ctas_per_sm == 1 || ctas_per_sm == 2, "qd_batch_set_shape: ctas_per_sm must be 1 or 2");
+  const qd_batch::Step keep = b->steps[step];
+  if (qd_status st = batch_plan(b, step, warps, ctas_per_sm == 2 ? b->budget2 : (size_t)b->optin)) {
+    b->steps[step] = keep;
+    return st;
+  }
+  return QD_OK;
+}
+
+qd_status qd_batch_info(const qd_batch* b, int step, int out[4]) {
+  QD_REQ(b && out, "null argument");
+  QD_REQ(step >= 0 && step < b->n_steps, "qd_batch_info: step out of range");
+  const auto& S = b->steps[step];
+  out[0] = S.warps;
+  out[1] = (int)S.smem;
+  out[2] = S.blocks;
+  int active = 0;
+  for (auto* d : b->mem) active += step < (int)d->wins.size();
+  out[3] = active;
+  return QD_OK;
+}
+
+qd_status qd_batch_step(qd_batch* b, int step, uint32_t* const* det_bits, const int64_t* n_shots,
+                        uint32_t* const* obs_pred, uint32_t* const* residue_fail, qd_stream_t stream) {
+  QD_REQ(b && det_bits && n_shots && obs_pred && residue_fail, "qd_batch_step: null argument");
+  QD_REQ(step >= 0 && step < b->n_steps, "qd_batch_step: step out of range");
+  for (size_t i = 0; i < b->mem.size(); ++i) {
+    QD_REQ(n_shots[i] >= 0 && n_shots[i] <= b->mem[i]->max_shots,
+           "qd_batch_step: n_shots of member " + std::to_string(i) + " outside [0, max_shots]");
+    QD_REQ(n_shots[i] == 0 || (det_bits[i] && obs_pred[i] && residue_fail[i]),
+           "qd_batch_step: null buffer of member " + std::to_string(i));
+  }
+  std::vector<qd::BatchMember> m;
+  if (!batch_members(b, step, det_bits, n_shots, obs_pred, residue_fail, m)) return QD_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (qd_status s = batch_decode(b, step, m, st)) return s;
+  QD_CK(qd::launch_commit_batch(st, m.data(), (int)m.size()));
+  return QD_OK;
+}
+
+qd_status qd_batch_autotune(qd_batch* b, int step, uint32_t* const* det_bits, const int64_t* n_shots, int reps,
+                            qd_stream_t stream, float* best_ms) {
+  QD_REQ(b && det_bits && n_shots, "qd_batch_autotune: null argument");
+  QD_REQ(step >= 0 && step < b->n_steps, "qd_batch_autotune: step out of range");
+  QD_REQ(reps >= 1, "qd_batch_autotune: reps < 1");
+  for (size_t i = 0; i < b->mem.size(); ++i)
+    QD_REQ(n_shots[i] >= 0 && n_shots[i] <= b->mem[i]->max_shots, "qd_batch_autotune: n_shots outside range");
+  std::vector<qd::BatchMember> m;
+  if (!batch_members(b, step, det_bits, n_shots, nullptr, nullptr, m)) return QD_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  QD_CK(cudaEventCreate(&e0));
+  QD_CK(cudaEventCreate(&e1));
+  const qd_batch::Step keep = b->steps[step];
+  float best = 0.0f;
+  int pick_w = 0;
+  size_t pick_b = 0;
+  qd_status st_out = QD_OK;
+  const size_t budgets[2] = {b->budget2, (size_t)b->optin};
+  for (int w = kShotWarps; w >= 4 && st_out == QD_OK; --w)
+    for (size_t bud : budgets) {
+      if (batch_plan(b, step, w, bud) != QD_OK) continue;
+      // the member table points at this step's layouts, which batch_plan rebuilt
+      batch_members(b, step, det_bits, n_shots, nullptr, nullptr, m);
+      if ((st_out = batch_decode(b, step, m, st)) != QD_OK) break;  // warm-up
+      cudaError_t e = cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r)
+        if ((st_out = batch_decode(b, step, m, st)) != QD_OK) break;
+      if (st_out != QD_OK) break;
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        set_error(std::string("qd_batch_autotune: ") + cudaGetErrorString(e));
+        st_out = QD_ECUDA;
+        break;
+      }
+      ms /= reps;
+      if (!pick_w || ms < best) {
+        best = ms;
+        pick_w = w;
+        pick_b = bud;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st_out != QD_OK || !pick_w) {
+    b->steps[step] = keep;
+    return st_out;
+  }
+  QD_CK_ST(batch_plan(b, step, pick_w, pick_b));
+  if (best_ms) *best_ms = best;
+  return QD_OK;
+}
+
+}  // extern "C"
 
 // ---------------------------------------------------------------------------
 // Learned weighted min-sum: training on window samples.

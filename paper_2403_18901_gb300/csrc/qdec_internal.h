@@ -55,6 +55,27 @@ cudaError_t launch_decode(int mode, int grid, int threads, size_t smem, cudaStre
                           const WinDev& W, const Layout& L, const uint32_t* det, int det_words, long long n,
                           uint32_t* corr, int corr_words, int32_t* status, char* trace, size_t tr_bytes, int dmx,
                           int ns_max, int* work, long long* counters, char* path_res, int* arrive, int sw_max);
+// One decoder's share of a batched window step (decode + commit).
+struct BatchMember {
+  const KParams* P;
+  const WinDev* W;
+  const Layout* L;
+  const uint32_t* det;  // also updated by the commit
+  int det_words;
+  long long n;
+  uint32_t* corr;
+  int corr_words, dmx, ns_max, sw_max;
+  long long* counters;
+  int n_commit;
+  const int *cptr, *cdet;
+  const uint32_t* cobs;
+  uint32_t *obs_pred, *resid;
+  int b0, b1;
+};
+cudaError_t batch_occupancy(int threads, size_t smem, int* blocks);
+cudaError_t launch_decode_batch(cudaStream_t st, int grid, int threads, size_t smem, unsigned q_off, int* work,
+                                const BatchMember* m, int n);
+cudaError_t launch_commit_batch(cudaStream_t st, const BatchMember* m, int n);
 cudaError_t launch_sample(cudaStream_t st, int n_cols, const uint32_t* thr, const int* cptr,
                           const int* cdet, const uint32_t* cobs, int det_words,
                           unsigned long long seed, unsigned long long off, long long n, uint32_t* det,

@@ -78,6 +78,13 @@ _SIGS = {
     "qd_decoder_set_weights": (_I, [_VP, _I, _VP, _I]),
     "qd_decoder_set_ranker": (_I, [_VP, _VP]),
     "qd_decoder_set_dump": (_I, [_VP, _VP, _VP, _I]),
+    "qd_batch_create": (_I, [_VP, _I, C.POINTER(_VP)]),
+    "qd_batch_destroy": (_I, [_VP]),
+    "qd_batch_n_steps": (_I, [_VP, C.POINTER(_I)]),
+    "qd_batch_step": (_I, [_VP, _I, _VP, _VP, _VP, _VP, _VP]),
+    "qd_batch_set_shape": (_I, [_VP, _I, _I, _I]),
+    "qd_batch_info": (_I, [_VP, _I, _VP]),
+    "qd_batch_autotune": (_I, [_VP, _I, _VP, _VP, _I, _VP, _VP]),
     "qd_window_sample": (_I, [_VP, _I, _U64, _U64, _I64, _VP, _VP, _VP]),
     "qd_ranker_eval": (_I, [_VP, _VP, _VP, _I64, _I, C.c_float, C.c_float, _VP, _VP, _VP, _VP]),
     "qd_wms_create": (_I, [_VP, _I, _I, _I, C.POINTER(_VP)]),
@@ -329,3 +336,51 @@ class Decoder:
 
     def _ns_max(self):
         return max(self.window_info(k)["n_short"] for k in range(self.n_windows))
+
+
+class Batch:
+    """Several decoders advanced one window step at a time, each step one
+    decode launch and one commit launch over all members (qd_batch_*)."""
+
+    def __init__(self, decoders):
+        arr = (C.c_void_p * len(decoders))(*[d.h for d in decoders])
+        h = C.c_void_p()
+        _check(lib().qd_batch_create(arr, len(decoders), C.byref(h)))
+        self.h, self.members = h, list(decoders)
+        n = C.c_int()
+        _check(lib().qd_batch_n_steps(self.h, C.byref(n)))
+        self.n_steps = n.value
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.qd_batch_destroy(self.h)
+            self.h = None
+
+    @staticmethod
+    def _ptrs(ts):
+        return (C.c_void_p * len(ts))(*[t.data_ptr() if t is not None else None for t in ts])
+
+    def _args(self, det, n, pred=None, resid=None):
+        self._keep = (self._ptrs(det), (C.c_int64 * len(n))(*n),
+                      self._ptrs(pred) if pred is not None else None,
+                      self._ptrs(resid) if resid is not None else None)
+        return self._keep
+
+    def step(self, j, det, n, pred, resid, stream=None):
+        """det, pred, resid: per-member CUDA tensors; n: per-member shot counts."""
+        a = self._args(det, n, pred, resid)
+        _check(lib().qd_batch_step(self.h, j, a[0], a[1], a[2], a[3], _stream(stream)))
+
+    def set_shape(self, j, warps, ctas_per_sm=2):
+        _check(lib().qd_batch_set_shape(self.h, j, int(warps), int(ctas_per_sm)))
+
+    def info(self, j):
+        out = np.zeros(4, np.int32)
+        _check(lib().qd_batch_info(self.h, j, _ptr(out)))
+        return dict(warps=int(out[0]), smem=int(out[1]), ctas_per_sm=int(out[2]), members=int(out[3]))
+
+    def autotune(self, j, det, n, reps=3, stream=None):
+        a = self._args(det, n)
+        ms = C.c_float()
+        _check(lib().qd_batch_autotune(self.h, j, a[0], a[1], int(reps), _stream(stream), C.byref(ms)))
+        return ms.value
