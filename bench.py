@@ -574,7 +574,7 @@ def main():
             "gpu_launches": args.steps * (2 * nwin + 1),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
                          "frac": achieved / alu_peak, "traffic": None,
-                         "kernel": "decode_window_kernel",
+                         "kernel": "decode_shot_kernel",
                          "work": f"{OPS_PER_EDGE_ITER} ops x {edge_iters} edge-iterations in "
                                  f"{nwin} launches",
                          "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz "
