@@ -242,7 +242,8 @@ struct ShortG {
   const float* wts;
   int wT, wE;
   int rpb;  // window rows per block (block of a column = its first row / rpb)
-  const uint16_t* sel;  // short column -> window column
+  const uint16_t* sel;    // short column -> window column
+  const uint16_t* cperm;  // checks by descending degree in the shortened matrix (ties by index)
 };
 
 struct Slot {
@@ -515,46 +516,43 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
       uint32_t* par = B.par + (iters & 1) * rw;
       for (int x = R; x < rw; x += S) par[x] = 0;
       // ---- check-node update, Eq. (1), over active VNs; tpc lanes per check ----
+      // checks in descending static degree, so the lanes of a round loop alike
       for (int j0 = R / tpc; j0 < nr_rounds; j0 += S / tpc) {
-        const int j = j0 < nr ? j0 : nr - 1;
+        const int j = G.cperm[j0 < nr ? j0 : nr - 1];
         const int d = j0 < nr ? B.deg[j] : 0;
         if (tpc == 1 && d == 0) continue;  // no shuffle partner waits for this lane
         const CNState oc = B.cns[j];
         float m1 = CUDART_INF_F, m2 = CUDART_INF_F;
         int am = 0xFFFF;
         uint32_t neg = 0;
+        // one row entry; the (min1, min2) pair and so every message do not
+        // depend on the order in which a check sees its inputs
+        auto take = [&](uint32_t ent, float pv, uint32_t sg) {
+          if (pv != pv) return;  // stale message of a decimated VN
+          const int e = (int)(ent & 0xFFFFu);
+          ++visits;
+          const float wprev = LW ? edge_weight(G.wts, G.wT, G.wE, P.alpha, iters, G.efull[e]) : P.alpha;
+          const float v = first ? pv : clipf(__fsub_rn(pv, c2v_msg(wprev, P.clip, oc, e, sg)), P.clip);
+          const float a = fabsf(v);
+          if (a < m1) {
+            m2 = m1;
+            m1 = a;
+            am = e;
+          } else if (a < m2) {
+            m2 = a;
+          }
+          const uint32_t sgn = v < 0.0f;
+          neg ^= sgn;
+          B.sign[e] = (uint8_t)sgn;
+        };
         const int qe = d ? G.rowptr[j + 1] : 0;
-        for (int q = (d ? G.rowptr[j] : 0) + 4 * sub; q < qe; q += 4 * tpc) {
-          uint32_t ent[4];
-          float pv[4];
-          uint32_t sg[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) ent[u] = (q + u < qe) ? G.rowent[q + u] : 0u;
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            pv[u] = B.post[ent[u] >> 16];
-            sg[u] = B.sign[ent[u] & 0xFFFFu];
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (q + u >= qe) break;
-            if (pv[u] != pv[u]) continue;  // stale message of a decimated VN
-            const int e = (int)(ent[u] & 0xFFFFu);
-            ++visits;
-            const float wprev = LW ? edge_weight(G.wts, G.wT, G.wE, P.alpha, iters, G.efull[e]) : P.alpha;
-            const float v = first ? pv[u] : clipf(__fsub_rn(pv[u], c2v_msg(wprev, P.clip, oc, e, sg[u])), P.clip);
-            const float a = fabsf(v);
-            if (a < m1) {
-              m2 = m1;
-              m1 = a;
-              am = e;
-            } else if (a < m2) {
-              m2 = a;
-            }
-            const uint32_t sgn = v < 0.0f;
-            neg ^= sgn;
-            B.sign[e] = (uint8_t)sgn;
-          }
+        for (int q = (d ? G.rowptr[j] : 0) + 2 * sub; q < qe; q += 2 * tpc) {
+          const bool two = q + 1 < qe;
+          const uint32_t e0 = G.rowent[q], e1 = two ? G.rowent[q + 1] : e0;
+          const float p0 = B.post[e0 >> 16], p1 = B.post[e1 >> 16];
+          const uint32_t s0 = B.sign[e0 & 0xFFFFu], s1 = B.sign[e1 & 0xFFFFu];
+          take(e0, p0, s0);
+          if (two) take(e1, p1, s1);
         }
         if (tpc > 1) group_min2(m1, m2, am, neg, tpc);
         if (sub == 0 && d > 0)
@@ -568,18 +566,18 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
         if (B.status[k] != -1) continue;
         float p = G.llr[k];
         const int eb = G.colptr[k], ee = G.colptr[k + 1];
-        for (int e0 = eb; e0 < ee; e0 += 8) {
-          float c[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u)
-            if (e0 + u < ee) {
-              const float wt = LW ? edge_weight(G.wts, G.wT, G.wE, P.alpha, iters + 1, G.efull[e0 + u]) : P.alpha;
-              c[u] = c2v_msg(wt, P.clip, B.cns[G.colrows[e0 + u]], e0 + u, B.sign[e0 + u]);
-            }
-#pragma unroll
-          for (int u = 0; u < 8; ++u)
-            if (e0 + u < ee) p = __fadd_rn(p, c[u]);  // ascending check order (Eq. (2))
+        auto msg = [&](int e) {
+          const float wt = LW ? edge_weight(G.wts, G.wT, G.wE, P.alpha, iters + 1, G.efull[e]) : P.alpha;
+          return c2v_msg(wt, P.clip, B.cns[G.colrows[e]], e, B.sign[e]);
+        };
+        // ascending check order (Eq. (2)); most short columns have degree 1 or 2
+        int e = eb;
+        for (; e + 1 < ee; e += 2) {
+          const float c0 = msg(e), c1 = msg(e + 1);
+          p = __fadd_rn(p, c0);
+          p = __fadd_rn(p, c1);
         }
+        if (e < ee) p = __fadd_rn(p, msg(e));
         B.post[k] = p;
         if (hist) {
           if (P.rkq || P.dump) B.hq[4 * k + (it - (P.ips - 3))] = qhist(p);
@@ -885,18 +883,17 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
     for (int i = tid; i < nc; i += NT) {
       float p = W.llr[i];
       const int eb = W.col_ptr[i], ee = W.col_ptr[i + 1];
-      for (int e0 = eb; e0 < ee; e0 += 8) {
-        float c[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (e0 + u < ee) {
-            const float wt = LW ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t, e0 + u) : P.alpha;
-            c[u] = c2v_msg(wt, P.clip, cns[W.col_rows[e0 + u]], e0 + u, sign[e0 + u]);
-          }
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (e0 + u < ee) p = __fadd_rn(p, c[u]);  // ascending check order (Eq. (2))
+      auto msg = [&](int e) {
+        const float wt = LW ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t, e) : P.alpha;
+        return c2v_msg(wt, P.clip, cns[W.col_rows[e]], e, sign[e]);
+      };
+      int e = eb;  // ascending check order (Eq. (2))
+      for (; e + 1 < ee; e += 2) {
+        const float c0 = msg(e), c1 = msg(e + 1);
+        p = __fadd_rn(p, c0);
+        p = __fadd_rn(p, c1);
       }
+      if (e < ee) p = __fadd_rn(p, msg(e));
       post[i] = p;
       if (kacc) {
         float kv;
@@ -1010,6 +1007,18 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
       const int pos = atomicAdd(&rc[scr[e]], 1);
       sre[pos] = (uint32_t)e | ((uint32_t)k << 16);
     }
+  // processing order of the checks: descending degree, ties by index (rank
+  // by counting, no sort needed at these sizes)
+  uint16_t* cperm = (uint16_t*)(sm + L.s_cperm);
+  for (int j = tid; j < nr; j += NT) {
+    const int dj = srp[j + 1] - srp[j];
+    int r = 0;
+    for (int i = 0; i < nr; ++i) {
+      const int di = srp[i + 1] - srp[i];
+      r += (di > dj) || (di == dj && i < j);
+    }
+    cperm[r] = (uint16_t)j;
+  }
   __syncthreads();
   return false;
 }
@@ -1020,7 +1029,8 @@ __device__ __forceinline__ ShortG short_graph(char* sm, const Layout& L, const W
                 (const uint16_t*)(sm + L.s_rowptr), (const uint32_t*)(sm + L.s_rowent),
                 (const float*)(sm + L.s_llr),       (const uint8_t*)(sm + L.s_vdeg),
                 (const uint32_t*)(sm + L.sbits),    (const uint16_t*)(sm + L.s_efull),
-                W.wts, W.wT, W.n_edges, W.rows_per_block, (const uint16_t*)(sm + L.sel)};
+                W.wts, W.wT, W.n_edges, W.rows_per_block, (const uint16_t*)(sm + L.sel),
+                (const uint16_t*)(sm + L.s_cperm)};
 }
 
 __device__ __forceinline__ PathOut trace_out(const DecodeArgs& A, char* tr, int id, long long shot) {

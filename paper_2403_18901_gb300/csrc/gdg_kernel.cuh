@@ -87,7 +87,7 @@ __host__ __device__ inline size_t path_result_bytes(int sw) { return (16 + 4 * (
 // Shared-memory layout of one CTA (byte offsets), identical on host and device.
 struct Layout {
   // persistent
-  unsigned sbits, cbits, sel, s_colptr, s_colrows, s_rowptr, s_rowent, s_llr, s_vdeg, s_efull, rowcnt,
+  unsigned sbits, cbits, sel, s_colptr, s_colrows, s_rowptr, s_rowent, s_llr, s_vdeg, s_efull, s_cperm, rowcnt,
       res_status, res_pm, res_ebits, red, misc;
   // window graph staged in shared memory (path mode only; 0 bytes otherwise)
   unsigned g_colptr, g_colrows, g_rowptr, g_rowent, g_llr, g_bytes;
@@ -123,6 +123,7 @@ __host__ __device__ inline Layout make_layout(int nr, int nc, int ne, int ns, in
   L.s_llr = o; o = al16(o + 4u * ns);
   L.s_vdeg = o; o = al16(o + 1u * ns);
   L.s_efull = o; o = al16(o + 2u * es);
+  L.s_cperm = o; o = al16(o + 2u * nr);
   L.rowcnt = o; o = al16(o + 4u * (nr + 1));
   L.res_status = o; o = al16(o + 4u * nb);
   L.res_pm = o; o = al16(o + 8u * nb);
