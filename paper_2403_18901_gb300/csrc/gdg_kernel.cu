@@ -49,6 +49,26 @@ __device__ __forceinline__ float c2v_msg(float alpha, float clip, const CNState&
   return ((((c.ac >> 16) & 1u) ^ sg) != 0) ? -mag : mag;
 }
 
+// Check state as stored.  With learned weights the magnitudes stay unscaled
+// (each edge applies its own weight); for the plain decoder they are stored
+// already multiplied by alpha (alpha * clip for a single active input), the
+// same FP32 products c2v_msg forms, so a message is one select and a sign.
+template <bool LW>
+__device__ __forceinline__ CNState cn_store(float alpha, float clip, float m1, float m2, int am, uint32_t par,
+                                            bool single) {
+  if (LW) return CNState{m1, m2, (uint32_t)am | (par << 16) | ((uint32_t)single << 17), 0u};
+  const float s1 = __fmul_rn(alpha, single ? clip : m1);
+  const float s2 = single ? s1 : __fmul_rn(alpha, m2);
+  return CNState{s1, s2, (uint32_t)am | (par << 16), 0u};
+}
+
+template <bool LW>
+__device__ __forceinline__ float c2v(float w, float clip, const CNState& c, int e, uint32_t sg) {
+  if (LW) return c2v_msg(w, clip, c, e, sg);
+  const float m = ((c.ac & 0xFFFFu) == (uint32_t)e) ? c.m2 : c.m1;
+  return ((((c.ac >> 16) & 1u) ^ sg) != 0) ? -m : m;
+}
+
 __device__ __forceinline__ uint32_t bit_of(const uint32_t* w, int j) { return (w[j >> 5] >> (j & 31)) & 1u; }
 
 // Multiplier of Eq. (1) at iteration t >= 1 for full-window edge ef: alpha, or
@@ -244,6 +264,7 @@ struct ShortG {
   int rpb;  // window rows per block (block of a column = its first row / rpb)
   const uint16_t* sel;    // short column -> window column
   const uint16_t* cperm;  // checks by descending degree in the shortened matrix (ties by index)
+  const uint16_t* vperm;  // short columns by descending degree (ties by index)
 };
 
 struct Slot {
@@ -532,7 +553,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
           const int e = (int)(ent & 0xFFFFu);
           ++visits;
           const float wprev = LW ? edge_weight(G.wts, G.wT, G.wE, P.alpha, iters, G.efull[e]) : P.alpha;
-          const float v = first ? pv : clipf(__fsub_rn(pv, c2v_msg(wprev, P.clip, oc, e, sg)), P.clip);
+          const float v = first ? pv : clipf(__fsub_rn(pv, c2v<LW>(wprev, P.clip, oc, e, sg)), P.clip);
           const float a = fabsf(v);
           if (a < m1) {
             m2 = m1;
@@ -556,19 +577,21 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
         }
         if (tpc > 1) group_min2(m1, m2, am, neg, tpc);
         if (sub == 0 && d > 0)
-          B.cns[j] = CNState{m1, m2, (uint32_t)am | ((neg ^ bit_of(B.sp, j)) << 16) | ((uint32_t)(d == 1) << 17), 0u};
+          B.cns[j] = cn_store<LW>(P.alpha, P.clip, m1, m2, am, neg ^ bit_of(B.sp, j), d == 1);
       }
       g.sync();
       // ---- variable-node update, Eq. (2)-(3); history of Sec. IV-A ----
       const bool hist = it > P.ips - 4;
       const bool hist0 = it == P.ips - 3;
-      for (int k = R; k < ns; k += S) {
+      // variables in descending degree, so the lanes of a round loop alike
+      for (int k0 = R; k0 < ns; k0 += S) {
+        const int k = G.vperm[k0];
         if (B.status[k] != -1) continue;
         float p = G.llr[k];
         const int eb = G.colptr[k], ee = G.colptr[k + 1];
         auto msg = [&](int e) {
           const float wt = LW ? edge_weight(G.wts, G.wT, G.wE, P.alpha, iters + 1, G.efull[e]) : P.alpha;
-          return c2v_msg(wt, P.clip, B.cns[G.colrows[e]], e, B.sign[e]);
+          return c2v<LW>(wt, P.clip, B.cns[G.colrows[e]], e, B.sign[e]);
         };
         // ascending check order (Eq. (2)); most short columns have degree 1 or 2
         int e = eb;
@@ -859,7 +882,7 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
           if (q + u >= end) break;
           const int e = (int)(ent[u] & 0xFFFFu);
           const float wprev = (LW && t > 1) ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t - 1, e) : P.alpha;
-          const float v = (t == 1) ? pv[u] : clipf(__fsub_rn(pv[u], c2v_msg(wprev, P.clip, oc, e, sg[u])), P.clip);
+          const float v = (t == 1) ? pv[u] : clipf(__fsub_rn(pv[u], c2v<LW>(wprev, P.clip, oc, e, sg[u])), P.clip);
           const float a = fabsf(v);
           if (a < m1) {
             m2 = m1;
@@ -875,17 +898,17 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
       }
       if (tpc_pre > 1) group_min2(m1, m2, am, neg, tpc_pre);
       if (sub_pre == 0 && j0 < nr)
-        cns[j] = CNState{m1, m2,
-                         (uint32_t)am | ((neg ^ bit_of(sbits, j)) << 16) | ((uint32_t)(end - beg == 1) << 17), 0u};
+        cns[j] = cn_store<LW>(P.alpha, P.clip, m1, m2, am, neg ^ bit_of(sbits, j), end - beg == 1);
     }
     __syncthreads();
     const bool kacc = t >= tk0;
-    for (int i = tid; i < nc; i += NT) {
+    for (int i0 = tid; i0 < nc; i0 += NT) {
+      const int i = W.vperm[i0];  // descending degree: the lanes of a round loop alike
       float p = W.llr[i];
       const int eb = W.col_ptr[i], ee = W.col_ptr[i + 1];
       auto msg = [&](int e) {
         const float wt = LW ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t, e) : P.alpha;
-        return c2v_msg(wt, P.clip, cns[W.col_rows[e]], e, sign[e]);
+        return c2v<LW>(wt, P.clip, cns[W.col_rows[e]], e, sign[e]);
       };
       int e = eb;  // ascending check order (Eq. (2))
       for (; e + 1 < ee; e += 2) {
@@ -1019,6 +1042,16 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
     }
     cperm[r] = (uint16_t)j;
   }
+  uint16_t* vperm = (uint16_t*)(sm + L.s_vperm);
+  for (int k = tid; k < n_short; k += NT) {
+    const int dk = svd[k];
+    int r = 0;
+    for (int i = 0; i < n_short; ++i) {
+      const int di = svd[i];
+      r += (di > dk) || (di == dk && i < k);
+    }
+    vperm[r] = (uint16_t)k;
+  }
   __syncthreads();
   return false;
 }
@@ -1030,7 +1063,7 @@ __device__ __forceinline__ ShortG short_graph(char* sm, const Layout& L, const W
                 (const float*)(sm + L.s_llr),       (const uint8_t*)(sm + L.s_vdeg),
                 (const uint32_t*)(sm + L.sbits),    (const uint16_t*)(sm + L.s_efull),
                 W.wts, W.wT, W.n_edges, W.rows_per_block, (const uint16_t*)(sm + L.sel),
-                (const uint16_t*)(sm + L.s_cperm)};
+                (const uint16_t*)(sm + L.s_cperm), (const uint16_t*)(sm + L.s_vperm)};
 }
 
 __device__ __forceinline__ PathOut trace_out(const DecodeArgs& A, char* tr, int id, long long shot) {

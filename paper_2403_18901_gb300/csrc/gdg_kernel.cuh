@@ -52,6 +52,7 @@ struct WinDev {
   // alpha at iteration t (counted from message initialisation); NULL = alpha
   const float* wts;
   int wT;
+  const uint16_t* vperm;  // pre-BP processing order of the columns (descending degree)
 };
 
 // A window's Tanner graph for the learned weighted min-sum (training kernels).
@@ -63,9 +64,11 @@ struct WmsGraph {
   float clip;
 };
 
-// Compressed state of one check node: two smallest |input|, the edge holding
-// the smallest (low 16 bits of ac) and flags (bit 16: sign parity xor s_j,
-// bit 17: exactly one active input).
+// Compressed state of one check node: two smallest |input| (multiplied by
+// alpha for the plain decoder; alpha * clip twice when exactly one input is
+// active), the edge holding the smallest (low 16 bits of ac) and flags
+// (bit 16: sign parity xor s_j; with learned weights bit 17: exactly one
+// active input, the magnitudes then unscaled).
 struct __align__(16) CNState {
   float m1, m2;
   uint32_t ac, pad;
@@ -87,7 +90,7 @@ __host__ __device__ inline size_t path_result_bytes(int sw) { return (16 + 4 * (
 // Shared-memory layout of one CTA (byte offsets), identical on host and device.
 struct Layout {
   // persistent
-  unsigned sbits, cbits, sel, s_colptr, s_colrows, s_rowptr, s_rowent, s_llr, s_vdeg, s_efull, s_cperm, rowcnt,
+  unsigned sbits, cbits, sel, s_colptr, s_colrows, s_rowptr, s_rowent, s_llr, s_vdeg, s_efull, s_cperm, s_vperm, rowcnt,
       res_status, res_pm, res_ebits, red, misc;
   // window graph staged in shared memory (path mode only; 0 bytes otherwise)
   unsigned g_colptr, g_colrows, g_rowptr, g_rowent, g_llr, g_bytes;
@@ -124,6 +127,7 @@ __host__ __device__ inline Layout make_layout(int nr, int nc, int ne, int ns, in
   L.s_vdeg = o; o = al16(o + 1u * ns);
   L.s_efull = o; o = al16(o + 2u * es);
   L.s_cperm = o; o = al16(o + 2u * nr);
+  L.s_vperm = o; o = al16(o + 2u * ns);
   L.rowcnt = o; o = al16(o + 4u * (nr + 1));
   L.res_status = o; o = al16(o + 4u * nb);
   L.res_pm = o; o = al16(o + 8u * nb);

@@ -337,8 +337,15 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
     // graph arrays in one allocation
     size_t o_cp = 0, o_cr = o_cp + 2 * h.col_ptr.size(), o_rp = o_cr + 2 * h.col_rows.size(),
            o_re = (o_rp + 2 * h.row_ptr.size() + 15) & ~(size_t)15, o_ll = o_re + 4 * h.row_ent.size(),
-           tot = o_ll + 4 * h.llr.size();
+           o_vp = o_ll + 4 * h.llr.size(), tot = o_vp + 2 * (size_t)h.n_cols;
+    // pre-BP processing order of the variables: descending degree, ties by index
+    std::vector<uint16_t> vperm(h.n_cols);
+    for (int c = 0; c < h.n_cols; ++c) vperm[c] = (uint16_t)c;
+    std::stable_sort(vperm.begin(), vperm.end(), [&](uint16_t a, uint16_t b) {
+      return h.col_ptr[a + 1] - h.col_ptr[a] > h.col_ptr[b + 1] - h.col_ptr[b];
+    });
     std::vector<char> blob(tot);
+    memcpy(blob.data() + o_vp, vperm.data(), 2 * vperm.size());
     memcpy(blob.data() + o_cp, h.col_ptr.data(), 2 * h.col_ptr.size());
     memcpy(blob.data() + o_cr, h.col_rows.data(), 2 * h.col_rows.size());
     memcpy(blob.data() + o_rp, h.row_ptr.data(), 2 * h.row_ptr.size());
@@ -349,7 +356,8 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
     char* b = (char*)g.d_graph;
     g.dv = qd::WinDev{h.n_rows, h.n_cols, h.n_edges, h.row0, h.n_short, h.short_edges_max, h.n_rows / h.n_blocks,
                       (const uint16_t*)(b + o_cp), (const uint16_t*)(b + o_cr), (const uint16_t*)(b + o_rp),
-                      (const uint32_t*)(b + o_re), (const float*)(b + o_ll), nullptr, 0};
+                      (const uint32_t*)(b + o_re), (const float*)(b + o_ll), nullptr, 0,
+                      (const uint16_t*)(b + o_vp)};
     // committed columns: their full detector sets and observables
     std::vector<int> cc_ptr(1, 0), cc_det;
     std::vector<uint32_t> cc_obs;
