@@ -364,7 +364,7 @@ void qdo_ranker_score(const float* raw, const float* x, int n, float* out) {
  * the state before the loop (an aggressive decision always equals the VN's
  * current hard decision, so it never changes any CN's satisfaction). */
 static int select_vn(const graph_t* g, state_t* s, const qdo_params* P, int D, int main_branch,
-                     int* f_out, int* n_agg) {
+                     int path0, int* f_out, int* n_agg) {
   int* nus = calloc(g->nc > 0 ? g->nc : 1, sizeof(int));
   if (!P->low_error_mode || P->ranker || P->dump) {
     for (int j = 0; j < g->nr; ++j) {
@@ -383,7 +383,7 @@ static int select_vn(const graph_t* g, state_t* s, const qdo_params* P, int D, i
   float best = -INFINITY, Lbest = 0.0f;
   int gbest = -1;
   if (P->ranker) ranker_quantize(P->ranker, &rk);
-  const int dumping = P->dump && main_branch;
+  const int dumping = P->dump && path0;
   const int d0 = dumping ? *P->dump_n : 0;
   *n_agg = 0;
   for (int i = 0; i < g->nc; ++i) {
@@ -462,11 +462,46 @@ static double path_metric(const graph_t* g, const state_t* s) {
   return pm;
 }
 
+/*
+ * The decision paths of Fig. 2 / Alg. 2.  Ids 0 .. 2^k - 1 form the guessing
+ * tree (id 0 = the main branch; at depth D <= k path id takes bit k - D of
+ * its id, most significant first, as b of b + (-1)^b f).  With side branches
+ * (side_max >= k), ids 2^k .. add the side branches that split off the main
+ * branch at D_split = k+1 .. side_max, and id 1 -- contrary only at D = k --
+ * is the side branch with D_split = k.  A side branch takes f everywhere
+ * except 1 - f at D_split and runs D_split + (d_max_other - k) steps; tree
+ * branches run d_max_other = k + (steps after the last guess).
+ * READING: a side branch is the main branch up to and including its split
+ * step (main-branch thresholds of Alg. 3 there), as the paper's side threads
+ * start from the main thread's status at the split; afterwards it uses the
+ * other-branch thresholds.  Messages stay continuous along every path.
+ */
+int qdo_n_paths(const qdo_params* P) {
+  int nt = 1 << P->k_guess;
+  return nt + (P->side_max > P->k_guess ? P->side_max - P->k_guess : 0);
+}
+
+int qdo_path_dmax_all(const qdo_params* P) {
+  int dmx = P->d_max_main > P->d_max_other ? P->d_max_main : P->d_max_other;
+  int side = P->side_max + (P->d_max_other - P->k_guess);
+  if (P->side_max > 0 && side > dmx) dmx = side;
+  return dmx;
+}
+
+/* 0 = tree (or main) path, else the split depth of a side branch */
+static int side_split(const qdo_params* P, int id) {
+  int nt = 1 << P->k_guess;
+  if (P->side_max <= 0) return 0;
+  if (id >= nt) return P->k_guess + 1 + (id - nt);
+  if (id == 1 && P->k_guess >= 1) return P->k_guess;
+  return 0;
+}
+
 /* One decision path of Alg. 2 on graph g (the shortened window). */
 static void run_branch(const graph_t* g, const uint8_t* synd, const qdo_params* P, int id,
                        state_t* s, qdo_branch_summary* out, qdo_step_record* steps) {
-  int dmax = id == 0 ? P->d_max_main : P->d_max_other;
-  int main_branch = (id == 0);
+  const int split = side_split(P, id);
+  int dmax = id == 0 ? P->d_max_main : (split ? split + (P->d_max_other - P->k_guess) : P->d_max_other);
   state_reset(s, g, synd);
   out->status = BR_MAXDEPTH;
   out->depth = 0;
@@ -489,7 +524,8 @@ static void run_branch(const graph_t* g, const uint8_t* synd, const qdo_params* 
     }
     if (D == dmax) break; /* READING: no decimation after the last BP step */
     int f, nagg;
-    int gsel = select_vn(g, s, P, D, main_branch, &f, &nagg);
+    int main_rules = id == 0 || (split && D <= split);
+    int gsel = select_vn(g, s, P, D, main_rules, id == 0, &f, &nagg);
     qdo_step_record* rec = steps ? &steps[D - 1] : NULL;
     if (gsel < 0) {
       if (rec) { rec->g = -1; rec->value = -1; rec->n_agg = nagg; rec->n_peel = 0; }
@@ -497,7 +533,9 @@ static void run_branch(const graph_t* g, const uint8_t* synd, const qdo_params* 
       return;
     }
     int v = f;
-    if (D <= P->k_guess) {
+    if (split) {
+      if (D == split) v = 1 - f; /* the one contrary decision of a side branch */
+    } else if (D <= P->k_guess) {
       int b = (id >> (P->k_guess - D)) & 1;
       v = b ? 1 - f : f; /* b + (-1)^b f */
     }
@@ -538,11 +576,11 @@ int qdo_bp_run(int n_rows, int n_cols, const int* col_ptr, const int* col_rows, 
   return conv ? it : -it;
 }
 
-/* GDG over all 2^k paths of graph g; returns the winning id or -1. */
+/* GDG over all decision paths of graph g; returns the winning id or -1. */
 static int gdg_all(const graph_t* g, const uint8_t* synd, const qdo_params* P, uint8_t* e_out,
                    qdo_branch_summary* br_out, qdo_step_record* steps_out, int8_t* status_out) {
-  int nb = 1 << P->k_guess;
-  int dmx = P->d_max_main > P->d_max_other ? P->d_max_main : P->d_max_other;
+  int nb = qdo_n_paths(P);
+  int dmx = qdo_path_dmax_all(P);
   state_t s;
   state_alloc(&s, g);
   int best = -1;

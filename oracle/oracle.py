@@ -40,7 +40,7 @@ class QdoParams(C.Structure):
                 ("shorten", C.c_int), ("clip", C.c_float), ("pa_main", C.c_float),
                 ("pa_other", C.c_float), ("pb_main", C.c_float), ("pb_other", C.c_float),
                 ("pb_d1", C.c_float), ("pc", C.c_float), ("pd", C.c_float),
-                ("pc_max_depth", C.c_int), ("n_unsat_min", C.c_int),
+                ("pc_max_depth", C.c_int), ("n_unsat_min", C.c_int), ("side_max", C.c_int),
                 ("wts", C.POINTER(C.c_void_p)), ("wT", C.c_int), ("ranker", C.c_void_p),
                 ("dump", C.c_void_p), ("dump_n", C.c_void_p), ("dump_cap", C.c_int)]
 
@@ -60,6 +60,8 @@ def lib():
         L = C.CDLL(path)
         P = C.POINTER
         L.qdo_ranker_score.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+        L.qdo_n_paths.argtypes = [C.c_void_p]
+        L.qdo_path_dmax_all.argtypes = [C.c_void_p]
         L.qdo_dem_build.restype = C.c_void_p
         L.qdo_dem_build.argtypes = [P(QdoCode), C.c_double, C.c_int]
         L.qdo_dem_free.argtypes = [C.c_void_p]
@@ -111,6 +113,7 @@ def make_code(code):
 def make_params(p, weights=None, ranker=None):
     """weights: None or {window index: float32 array [T][n_edges of the window]};
     ranker: None or 641 float32 parameters of the decimation ranker."""
+    assert p.get("side_max", 0) == 0 or p["side_max"] >= p["k_guess"], "side_max must be 0 or >= k_guess"
     q = QdoParams()
     for name, _ in QdoParams._fields_:
         if name in ("wts", "wT", "ranker", "dump", "dump_n", "dump_cap"):
@@ -192,9 +195,9 @@ def gdg_graph(params, n_rows, col_ptr, col_rows, llr, synd):
     synd = np.ascontiguousarray(synd, np.uint8)
     n = len(col_ptr) - 1
     e = np.zeros(n, np.uint8)
-    nb = 1 << params["k_guess"]
-    br = (QdoBranch * nb)()
     P = make_params(params)
+    nb = lib().qdo_n_paths(C.byref(P))
+    br = (QdoBranch * nb)()
     best = lib().qdo_gdg_graph(C.byref(P), n_rows, n, _ptr(col_ptr), _ptr(col_rows), _ptr(llr),
                                _ptr(synd), _ptr(e), br)
     return best, e, [(b.status, b.depth, b.iters, b.pm) for b in br]
@@ -296,8 +299,8 @@ class OracleDEM:
             P.dump = dump.ctypes.data
             P.dump_n = dn.ctypes.data
             P.dump_cap = dump.shape[0]
-        nb = 1 << params["k_guess"]
-        dmx = max(params["d_max_main"], params["d_max_other"])
+        nb = lib().qdo_n_paths(C.byref(P))
+        dmx = lib().qdo_path_dmax_all(C.byref(P))
         if trace:
             sc = np.zeros(win["n_cols"], np.int32)
             br = (QdoBranch * nb)()

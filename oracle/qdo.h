@@ -44,6 +44,8 @@ typedef struct {
   float pa_main, pa_other, pb_main, pb_other, pb_d1, pc, pd; /* Alg. 3 */
   int pc_max_depth;      /* P_C test applies for D <= this (4)                 */
   int n_unsat_min;       /* unsatisfied-neighbour count of Alg. 3 (3)          */
+  int side_max;          /* side branches of Fig. 2 split off the main branch  */
+                         /* at D_split = k .. side_max (0: the 2^k tree only) */
   /* Learned weighted min-sum (no counterpart in the paper; alpha of Eq. (1)
    * replaced by w[t][e]): wts[k] is window k's array [wT][n_edges] over the
    * full-window edges (CSC order), or NULL for plain alpha.  Iteration t
@@ -149,6 +151,10 @@ int qdo_run_shots(const qdo_dem* d, const qdo_params* P, const uint32_t* det_bit
                   const uint32_t* obs_bits, int64_t n_shots, uint8_t* fail,
                   uint32_t* obs_pred, uint32_t* win_corr_words /* may be NULL */,
                   int corr_words_per_window);
+
+/* Number of decision paths (2^k tree + side branches) and the largest D_max. */
+int qdo_n_paths(const qdo_params* P);
+int qdo_path_dmax_all(const qdo_params* P);
 
 /* Ranker scores of n feature rows x [n][8] under raw parameters (641 floats,
  * rounded to the ranker's grids first). */

@@ -26,19 +26,23 @@ CODES = {
 # the message clip of 50, peeling and shortening to 2w' columns.
 _COMMON = dict(W=3, F=1, low_error_mode=0, peel_at_init=1, shorten=1, clip=50.0,
                pa_main=-3.0, pa_other=0.0, pb_main=-12.0, pb_other=-10.0, pb_d1=-16.0,
-               pc=30.0, pd=3.0, pc_max_depth=4, n_unsat_min=3)
+               pc=30.0, pd=3.0, pc_max_depth=4, n_unsat_min=3, side_max=0)
 
 # "configured": normalised min-sum alpha = 0.625, 100 BP iterations on the
 # full window, decimation steps of 10 iterations, 2^k guessing tree.
 CONFIGURED = dict(_COMMON, alpha=0.625, n_pre=100, iters_per_step=10, d_max_main=25)
 
-# "paper": the values of Sec. IV-C (alpha = 1.0, 8 pre-BP iterations for
-# N <= 144, 6 iterations per step, D_max 25 on the main path).
-PAPER = dict(_COMMON, alpha=1.0, n_pre=8, iters_per_step=6, d_max_main=25)
+# "paper": the values of Sec. IV-C and Fig. 2 for N <= 144 (alpha = 1.0, 8
+# pre-BP iterations, 6 iterations per step, D_max 25 on the main path, side
+# branches splitting off at D_split = k .. 10, every non-main path running 10
+# steps past its last guess).
+PAPER = dict(_COMMON, alpha=1.0, n_pre=8, iters_per_step=6, d_max_main=25, side_max=10)
 
 
 def preset(name, k_guess, p=None, **over):
-    """Decoder parameters; the non-main paths run 10 steps past depth k."""
+    """Decoder parameters; the non-main paths run 10 steps past depth k.
+    The "paper" preset of [[288,12,18]] (Sec. IV-C) is
+    preset("paper", 5, p, d_max_main=40, d_max_other=25, side_max=20, n_pre=16)."""
     base = {"configured": CONFIGURED, "paper": PAPER}[name]
     out = dict(base, k_guess=k_guess, d_max_other=k_guess + 10)
     if p is not None and p <= 0.002:

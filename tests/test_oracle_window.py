@@ -157,7 +157,7 @@ def test_main_branch_error_suppression():
     paper preset, k = 0; per-round rate p_L = 1 - (1 - P_L)^(1/R)
     (appendix "Stim circuit implementation"), 95% Wilson upper bound."""
     dem = oracle_dem("144", 0.002, 12)
-    P = preset("paper", k_guess=0, p=0.002)
+    P = preset("paper", k_guess=0, p=0.002, side_max=0)  # the main branch alone
     n = 1500
     det, obs = dem.sample(seed=144_002, shot_offset=0, n_shots=n)
     fail, _, _ = dem.run_shots(P, det, obs, threads=O.default_threads())
@@ -171,6 +171,6 @@ def test_guessing_tree_beats_main_branch():
     dem = oracle_dem("144", 0.003, 12)
     n = 600
     det, obs = dem.sample(seed=144_003, shot_offset=0, n_shots=n)
-    f0, _, _ = dem.run_shots(preset("paper", k_guess=0), det, obs, threads=O.default_threads())
+    f0, _, _ = dem.run_shots(preset("paper", k_guess=0, side_max=0), det, obs, threads=O.default_threads())
     f4, _, _ = dem.run_shots(preset("paper", k_guess=4), det, obs, threads=O.default_threads())
     assert int((f4 > 0).sum()) < int((f0 > 0).sum())
