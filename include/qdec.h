@@ -77,6 +77,11 @@ typedef struct {
   float pa_main, pa_other, pb_main, pb_other, pb_d1, pc, pd; /* Alg. 3 thresholds */
   int pc_max_depth;      /* P_C applies while D <= this                           */
   int n_unsat_min;       /* unsatisfied-neighbour count of Alg. 3                 */
+  int side_max;          /* side branches of Fig. 2 split off the main branch at  */
+                         /* D_split = k .. side_max and run D_split +            */
+                         /* (d_max_other - k) steps; 0: the 2^k tree only.       */
+                         /* With side branches id 1 (contrary only at D = k) is  */
+                         /* the D_split = k side branch; ids 2^k.. the others.   */
 } qd_gdg_params;
 
 typedef struct qd_dem qd_dem;
@@ -147,6 +152,9 @@ qd_status qd_decoder_destroy(qd_decoder* dec);
 qd_status qd_decoder_n_windows(const qd_decoder* dec, int* n_windows);
 /* Words per shot of the window-correction buffer (max over windows). */
 qd_status qd_decoder_corr_words(const qd_decoder* dec, int* corr_words);
+/* out = {number of decision paths (2^k + side branches), largest D_max}: the
+ * branch and step dimensions of the trace. */
+qd_status qd_decoder_path_info(const qd_decoder* dec, int out[2]);
 /* Window k's shape and, if gcols != NULL, its DEM column ids [n_cols]. */
 qd_status qd_window_info(const qd_decoder* dec, int k, qd_window_info_t* out, int* gcols);
 /* Bytes of the optional per-shot trace written by qd_decode_windows. */

@@ -507,10 +507,12 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
   // one lane per check for a warp; small lane groups per check for a CTA
   const int tpc = Grp::kWarp ? 1 : lanes_per_check(S, nr), sub = R & (tpc - 1);
   const int nr_rounds = (nr + S / tpc - 1) / (S / tpc) * (S / tpc);
-  const bool mainb = (id == 0);
-  const int dmax = mainb ? P.dmax_main : P.dmax_other;
-  const float PA = mainb ? P.pa_main : P.pa_other;
-  const float PB = mainb ? P.pb_main : P.pb_other;
+  // Fig. 2: main branch (id 0), tree branches, side branches (split > 0),
+  // which keep the main-branch thresholds up to and including their split
+  const int split = path_split(P, id);
+  const int dmax = id == 0 ? P.dmax_main : (split ? split + (P.dmax_other - P.k) : P.dmax_other);
+  auto main_rules = [&](int D) { return id == 0 || (split && D <= split); };
+  float PA = main_rules(1) ? P.pa_main : P.pa_other;
   for (int k = R; k < ns; k += S) {
     B.status[k] = -1;
     B.post[k] = G.llr[k];  // t = 0: mu_{i->j} = Lambda_i (Sec. II-A)
@@ -533,6 +535,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
   }
   for (int D = 1; D <= dmax; ++D) {
     depth = D;
+    PA = main_rules(D) ? P.pa_main : P.pa_other;  // read by this step's history flags
     for (int it = 1; it <= P.ips; ++it) {
       uint32_t* par = B.par + (iters & 1) * rw;
       for (int x = R; x < rw; x += S) par[x] = 0;
@@ -642,7 +645,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
       if (!P.low_err || P.rkq || P.dump)
         for (int x = R; x < rw; x += S) B.unsat[x] = lastpar[x] ^ B.sp[x];
       g.sync();
-      const float PBd = (D == 1) ? P.pb_d1 : PB;
+      const float PBd = (D == 1) ? P.pb_d1 : (main_rules(D) ? P.pb_main : P.pb_other);
       float bL = CUDART_INF_F, tL = CUDART_INF_F;
       int bk = kNone, tk = kNone, nagg = 0;
       for (int k = R; k < ns; k += S) {
@@ -698,7 +701,11 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
         g.sync();
       }
       int v = f;
-      if (D <= P.k) v = ((id >> (P.k - D)) & 1) ? 1 - f : f;  // b + (-1)^b f
+      if (split) {
+        if (D == split) v = 1 - f;  // the one contrary decision of a side branch
+      } else if (D <= P.k) {
+        v = ((id >> (P.k - D)) & 1) ? 1 - f : f;  // b + (-1)^b f
+      }
       if (R == 0) decimate_one(G, B, gsel, v);
       g.sync();
       const int np = peel(G, B, g);
@@ -1131,6 +1138,7 @@ __device__ void shot_body(const DecodeArgs& A, long long shot, char* sm) {
         if (lane == 0) id = atomicAdd(&misc[2], 1);
         id = __shfl_sync(FULL, id, 0);
         if (id >= A.P.nb) break;
+        id = path_at(A.P, id);
         PathOut o = trace_out(A, tr, id, shot);
         o.status = &res_status[id];
         o.pm = &res_pm[id];

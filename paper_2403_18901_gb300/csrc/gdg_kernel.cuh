@@ -20,7 +20,8 @@ constexpr int kMaxBatch = 16;  // decoders in one batched launch
 struct KParams {
   float alpha, clip, pa_main, pa_other, pb_main, pb_other, pb_d1, pc, pd;
   int n_pre, ips, dmax_main, dmax_other, k, low_err, peel_init, pc_max_depth, n_unsat_min;
-  int nb;  // 2^k
+  int nb;        // decision paths: 2^k tree + side branches
+  int side_max;  // side branches split off the main branch at D_split = k .. side_max (0: none)
   // learned decimation ranker (NULL: the argmin of Alg. 1): rkq = the
   // grid-rounded W1[64][8], b1[64], W2[64], b2; rkb[t][lane] = the BF16 pair
   // (W1[8t + lane/4][2 (lane%4)], W1[8t + lane/4][2 (lane%4) + 1]), the B
@@ -41,6 +42,25 @@ struct RankRec {
   int16_t depth, path;
   int32_t flags;
 };
+
+// Side-branch split depth of path `id` (Fig. 2): 0 for the main and tree
+// branches.  With side branches, id 1 (contrary only at D = k) is the one
+// splitting at D = k and ids 2^k.. split at D = k + 1 ...
+__host__ __device__ inline int path_split(const KParams& P, int id) {
+  if (P.side_max <= 0) return 0;
+  const int nt = 1 << P.k;
+  if (id >= nt) return P.k + 1 + (id - nt);
+  return (id == 1 && P.k >= 1) ? P.k : 0;
+}
+
+// Shot-mode queue order: the main branch, side branches from the deepest
+// split down, then the tree branches (longest paths first).
+__host__ __device__ inline int path_at(const KParams& P, int pos) {
+  const int nside = P.nb - (1 << P.k);
+  if (pos == 0) return 0;
+  if (pos <= nside) return P.nb - pos;
+  return pos - nside;
+}
 
 // One window's Tanner graph in global memory (read-only for all shots).
 struct WinDev {

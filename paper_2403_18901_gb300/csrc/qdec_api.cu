@@ -288,6 +288,9 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
     set_error("qd_decoder_create: iters_per_step < 4 is not implemented on the GPU");
     return QD_EUNSUPPORTED;
   }
+  QD_REQ(p->side_max == 0 || (p->side_max >= p->k_guess && p->side_max <= 32),
+         "qd_decoder_create: side_max must be 0 or in [k_guess, 32]");
+  QD_REQ(p->d_max_other >= p->k_guess, "qd_decoder_create: d_max_other < k_guess");
   if (p->k_guess < 0 || p->k_guess > 5) {
     set_error("qd_decoder_create: k_guess must be in [0, 5]");
     return QD_EUNSUPPORTED;
@@ -317,8 +320,10 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
   k.peel_init = p->peel_at_init;
   k.pc_max_depth = p->pc_max_depth;
   k.n_unsat_min = p->n_unsat_min;
-  k.nb = 1 << p->k_guess;
+  k.side_max = p->side_max;
+  k.nb = (1 << p->k_guess) + (p->side_max > p->k_guess ? p->side_max - p->k_guess : 0);
   dec->dmx = std::max(p->d_max_main, p->d_max_other);
+  if (p->side_max > 0) dec->dmx = std::max(dec->dmx, p->side_max + p->d_max_other - p->k_guess);
 
   int dev = 0, optin = 0;
   QD_CK(cudaGetDevice(&dev));
@@ -399,6 +404,13 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
 qd_status qd_decoder_n_windows(const qd_decoder* dec, int* n) {
   QD_REQ(dec && n, "null argument");
   *n = (int)dec->wins.size();
+  return QD_OK;
+}
+
+qd_status qd_decoder_path_info(const qd_decoder* dec, int out[2]) {
+  QD_REQ(dec && out, "null argument");
+  out[0] = dec->kp.nb;
+  out[1] = dec->dmx;
   return QD_OK;
 }
 

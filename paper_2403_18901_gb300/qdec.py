@@ -39,7 +39,7 @@ class GdgParams(C.Structure):
                 ("shorten", C.c_int), ("clip", C.c_float), ("pa_main", C.c_float),
                 ("pa_other", C.c_float), ("pb_main", C.c_float), ("pb_other", C.c_float),
                 ("pb_d1", C.c_float), ("pc", C.c_float), ("pd", C.c_float),
-                ("pc_max_depth", C.c_int), ("n_unsat_min", C.c_int)]
+                ("pc_max_depth", C.c_int), ("n_unsat_min", C.c_int), ("side_max", C.c_int)]
 
 
 class DemInfo(C.Structure):
@@ -65,6 +65,7 @@ _SIGS = {
     "qd_decoder_destroy": (_I, [_VP]),
     "qd_decoder_n_windows": (_I, [_VP, C.POINTER(_I)]),
     "qd_decoder_corr_words": (_I, [_VP, C.POINTER(_I)]),
+    "qd_decoder_path_info": (_I, [_VP, _VP]),
     "qd_window_info": (_I, [_VP, _I, C.POINTER(WindowInfo), _VP]),
     "qd_decoder_trace_bytes": (_I, [_VP, C.POINTER(_SZ)]),
     "qd_decode_windows": (_I, [_VP, _I, _VP, _I64, _VP, _VP, _VP, _VP]),
@@ -152,7 +153,7 @@ def make_code(code):
 def make_params(p):
     q = GdgParams()
     for name, _ in GdgParams._fields_:
-        setattr(q, name, p[name])
+        setattr(q, name, p.get(name, 0) if name == "side_max" else p[name])
     return q
 
 
@@ -316,8 +317,9 @@ class Decoder:
     # ---- trace decoding (layout of the per-shot trace buffer) ----
     def parse_trace(self, buf):
         """buf: numpy uint8 [trace_bytes] of one shot."""
-        nb = 1 << self.params["k_guess"]
-        dmx = max(self.params["d_max_main"], self.params["d_max_other"])
+        pi = np.zeros(2, np.int32)
+        _check(lib().qd_decoder_path_info(self.h, _ptr(pi)))
+        nb, dmx = int(pi[0]), int(pi[1])
         ns_max = self._ns_max()
         head = np.frombuffer(buf[:16].tobytes(), np.int32)
         br_dt = np.dtype([("status", "<i4"), ("depth", "<i4"), ("iters", "<i4"), ("pad", "<i4"),

@@ -265,3 +265,20 @@ def test_bb288_bit_exact(mode):
     decision-path slots per CTA; both launch shapes stay bit-exact."""
     params = preset("configured", k_guess=4, p=0.002)
     _pipeline("288", 3, 0.002, params, n=40, seed=288_002, trace_windows=(0, 1), mode=mode)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_full_decision_tree_bit_exact(mode):
+    """The decision tree of Fig. 2 with its side branches (D_split = 4..10,
+    22 paths), paper preset, both launch shapes, every path's log compared."""
+    params = preset("paper", k_guess=4, p=0.004)
+    assert params["side_max"] == 10
+    _pipeline("144", 12, 0.004, params, n=48 if mode == 1 else 24, seed=144_444, trace_windows=(1, 6, 10),
+              mode=mode)
+
+
+def test_bb288_paper_tree_bit_exact():
+    """[[288,12,18]] with its Sec. IV-C tree: D_max 40, tree depth 5, side
+    branches up to D_split = 20, 20 steps after a split (47 paths)."""
+    params = preset("paper", 5, p=0.002, d_max_main=40, d_max_other=25, side_max=20, n_pre=16)
+    _pipeline("288", 3, 0.003, params, n=16, seed=288_003, trace_windows=(0, 1), mode=1)
