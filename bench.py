@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--train-batch", type=int, default=4096)
     ap.add_argument("--ranker-steps", type=int, default=300,
                     help="Adam steps of the decimation ranker (0: skip)")
+    ap.add_argument("--paper-shots", type=int, default=20000,
+                    help="shots of the paper-preset (Fig. 2 tree) measurement (0: skip)")
     ap.add_argument("--batch-shots", type=int, default=30000,
                     help="shots per code of the batched uneven workload (0: skip)")
     ap.add_argument("--ranker-shots", type=int, default=4096,
@@ -290,6 +292,47 @@ def batched_uneven(args, torch, qdec, CODES, preset):
             "cuda_graph": "one graph of all window steps", "per_member": out_members}
 
 
+def paper_tree(args, torch, qdec, CODES, preset, latency_fn):
+    """The paper's own decoder (Sec. IV-C, Fig. 2): alpha = 1.0, 8 pre-BP
+    iterations, 6 iterations per step, main branch D_max 25, 2^4 tree, side
+    branches at D_split = 4..10 -- on the headline workload."""
+    params = preset("paper", k_guess=K_GUESS, p=P_PHYS)
+    dem = qdec.Dem(CODES[CODE_KEY], P_PHYS, ROUNDS)
+    n = args.paper_shots
+    dec = qdec.Decoder(dem, params, max_shots=n)
+    det, obs = dem.sample(args.seed + 1, 0, n)
+    work = torch.empty_like(det)
+    pred = torch.empty(n, dtype=torch.int32, device="cuda")
+    fail = torch.empty(n, dtype=torch.int32, device="cuda")
+    nf = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for _ in range(2):  # warm-up
+        work.copy_(det)
+        dec.decode_all(work, obs, n, pred, fail, nf)
+    work.copy_(det)
+    nf.zero_()
+    dec.reset_counters()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    dec.decode_all(work, obs, n, pred, fail, nf)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1000.0
+    c = dec.counters()
+    f = int(nf.item())
+    lo, hi = wilson(f, n)
+    pi = np.zeros(2, np.int32)
+    qdec._check(qdec.lib().qd_decoder_path_info(dec.h, qdec._ptr(pi)))
+    ldec = qdec.Decoder(dem, params, max_shots=1)
+    p50, p99, nl = latency_fn(ldec, det[:max(1, args.latency_shots)].clone())
+    return {"preset": "paper (alpha 1.0, n_pre 8, 6 iterations/step, Fig. 2 tree)", "paths": int(pi[0]),
+            "shots": n, "value": n * dec.n_windows / t, "unit": "windows/s", "seconds": t,
+            "gdg_windows_frac": float(c[3]) / (n * dec.n_windows),
+            "latency_ms": {"p50": p50, "p99": p99, "windows": nl},
+            "ler_per_round": {"failures": f, "shots": n, "p_L": per_round(f / n),
+                              "wilson95": [per_round(lo), per_round(hi)]}}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -305,7 +348,7 @@ def main():
         return
     import torch
     from paper_2403_18901_gb300 import build as qbuild
-    from paper_2403_18901_gb300 import qdec
+    from paper_2403_18901_gb300 import qdec, replicas
     from paper_2403_18901_gb300.workloads import CODES, preset
 
     rank, world, local = dist_env()
@@ -325,7 +368,7 @@ def main():
     # inputs resident in HBM before timing: one fresh batch per step
     pristine = []
     for b in range(n_batches):
-        d, o = dem.sample(args.seed, (rank * n_batches + b) * B, B)
+        d, o = dem.sample(args.seed, replicas.shot_offset(rank, n_batches, B, b), B)
         pristine.append((d, o))
     work = torch.empty((B, dw), dtype=torch.int32, device="cuda")
     pred = torch.empty(B, dtype=torch.int32, device="cuda")
@@ -359,11 +402,7 @@ def main():
             torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
-        t = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
-        if world > 1:
-            tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            t = float(tt.item())
+        t = replicas.max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1000.0, "cuda")
         return t, int(nfail.item()), clk.summary()
 
     t_wall0 = time.perf_counter()
@@ -454,10 +493,7 @@ def main():
     batched = None
     if args.batch_shots > 0 and rank == 0:
         batched = batched_uneven(args, torch, qdec, CODES, preset)
-    if world > 1:
-        fl = torch.tensor([failures], device="cuda")
-        torch.distributed.all_reduce(fl)
-        failures = int(fl[0].item())
+    failures = int(replicas.sum_over_ranks(failures, "cuda"))
 
     line = None
     if rank == 0:
@@ -485,7 +521,9 @@ def main():
         ldec = qdec.Decoder(dem, params, max_shots=1)
         lsrc = pristine[args.warmup][0][:L].clone()
 
-        def latency(ld):
+        def latency(ld, src=None):
+            src = lsrc if src is None else src
+            nwin = ld.n_windows
             ldet = torch.empty((1, dw), dtype=torch.int32, device="cuda")
             lcorr = torch.empty((1, ld.corr_words), dtype=torch.int32, device="cuda")
             lpred = torch.zeros(1, dtype=torch.int32, device="cuda")
@@ -504,8 +542,8 @@ def main():
                     ld.commit(k, lcorr, 1, ldet, lpred, lres)
                 graphs.append(g)
             lat = []
-            for sidx in range(L):
-                ldet.copy_(lsrc[sidx:sidx + 1])
+            for sidx in range(src.shape[0]):
+                ldet.copy_(src[sidx:sidx + 1])
                 for k in range(nwin):
                     a = torch.cuda.Event(enable_timing=True)
                     b2 = torch.cuda.Event(enable_timing=True)
@@ -552,6 +590,10 @@ def main():
                            "p_L": per_round(ranked["failures"] / (B * args.steps)),
                            "wilson95": [per_round(rlo), per_round(rhi)]}}
 
+        paper = None
+        if args.paper_shots > 0:
+            paper = paper_tree(args, torch, qdec, CODES, preset, latency)
+
         cpu_rate, cores, cpu_shots, cpu_s = cpu_oracle_rate(params, args.cpu_seconds, args.seed)
         line = {
             "metric": METRIC, "value": value, "unit": "windows/s", "n_gpus": world,
@@ -591,6 +633,7 @@ def main():
             "learned": learned,
             "ranker": ranked,
             "batched_uneven": batched,
+            "paper_tree": paper,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
