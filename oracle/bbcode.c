@@ -96,17 +96,14 @@ int qdo_gf2_rank(const uint8_t* M, int rows, int cols) {
 }
 
 /*
- * Logical Z operators: vectors z with H_X z = 0 (they commute with every
- * X check) that are independent modulo the row span of H_Z.  A kernel basis of
- * H_X comes from its reduced row echelon form; kernel vectors are then added
- * greedily whenever they raise the rank of [H_Z; chosen].  Returns K.
+ * Logical operators of one type: vectors v with Hk v = 0 (they commute with
+ * every check of Hk) that are independent modulo the row span of Hr.  A
+ * kernel basis of Hk comes from its reduced row echelon form (Hk is reduced in
+ * place); kernel vectors are then added greedily whenever they raise the rank
+ * of [Hr; chosen].  Both matrices are w x n.  Returns K.
  */
-int qdo_logical_z(const qdo_code* c, uint8_t* LZ, int max_k) {
-  int w = c->l * c->m, n = 2 * w;
-  uint8_t* HX = malloc((size_t)w * n);
-  uint8_t* HZ = malloc((size_t)w * n);
-  qdo_code_matrices(c, HX, HZ);
-  /* RREF of H_X */
+static int logical_basis(uint8_t* HX, const uint8_t* HZ, int w, int n, uint8_t* LZ, int max_k) {
+  /* RREF of the kernel matrix */
   int* pivcol = malloc(sizeof(int) * w);
   int rank = 0;
   for (int col = 0; col < n && rank < w; ++col) {
@@ -127,7 +124,7 @@ int qdo_logical_z(const qdo_code* c, uint8_t* LZ, int max_k) {
   }
   uint8_t* isp = calloc(n, 1);
   for (int r = 0; r < rank; ++r) isp[pivcol[r]] = 1;
-  /* stack = rows of H_Z followed by chosen logicals */
+  /* stack = rows of the row-span matrix followed by chosen logicals */
   int cap = w + max_k + 1;
   uint8_t* stack = malloc((size_t)cap * n);
   memcpy(stack, HZ, (size_t)w * n);
@@ -152,6 +149,30 @@ int qdo_logical_z(const qdo_code* c, uint8_t* LZ, int max_k) {
   free(stack);
   free(isp);
   free(pivcol);
+  return K;
+}
+
+/* Logical Z operators of the Z-basis memory: kernel of H_X modulo the row
+ * span of H_Z.  Returns K. */
+int qdo_logical_z(const qdo_code* c, uint8_t* LZ, int max_k) {
+  int w = c->l * c->m, n = 2 * w;
+  uint8_t* HX = malloc((size_t)w * n);
+  uint8_t* HZ = malloc((size_t)w * n);
+  qdo_code_matrices(c, HX, HZ);
+  int K = logical_basis(HX, HZ, w, n, LZ, max_k);
+  free(HX);
+  free(HZ);
+  return K;
+}
+
+/* Logical operators seen by errors decoded with H_X (appendices A and B):
+ * kernel of H_Z modulo the row span of H_X.  Returns K. */
+int qdo_logical_x(const qdo_code* c, uint8_t* LX, int max_k) {
+  int w = c->l * c->m, n = 2 * w;
+  uint8_t* HX = malloc((size_t)w * n);
+  uint8_t* HZ = malloc((size_t)w * n);
+  qdo_code_matrices(c, HX, HZ);
+  int K = logical_basis(HZ, HX, w, n, LX, max_k);
   free(HX);
   free(HZ);
   return K;

@@ -259,6 +259,42 @@ static int cmp_mech_q(const void* x, const void* y) {
   return a < b ? -1 : (a > b ? 1 : 0);
 }
 
+/* Sort the mechanisms by (detectors, observables, probability) so equal
+ * columns are adjacent with their probabilities ascending, merge them into
+ * the DEM's columns (Sec. II-B) and free them. */
+static void merge_mechanisms(qdo_dem* d, mech_t* ms, int nm) {
+  qsort(ms, nm, sizeof(mech_t), cmp_mech_q);
+  d->col_ptr = malloc(sizeof(int) * (nm + 1));
+  d->col_obs = malloc(sizeof(uint32_t) * nm);
+  d->col_p = malloc(sizeof(double) * nm);
+  d->col_llr = malloc(sizeof(float) * nm);
+  int tot = 0;
+  for (int k = 0; k < nm; ++k) tot += ms[k].n_det;
+  d->col_dets = malloc(sizeof(int) * (tot > 0 ? tot : 1));
+  int nc = 0, ne = 0;
+  d->col_ptr[0] = 0;
+  for (int k = 0; k < nm;) {
+    int e = k;
+    double pm = 0.0;
+    while (e < nm && cmp_mech(&ms[k], &ms[e]) == 0) {
+      double q = ms[e].p;
+      pm = pm * (1.0 - q) + q * (1.0 - pm);
+      ++e;
+    }
+    memcpy(d->col_dets + ne, ms[k].dets, sizeof(int) * ms[k].n_det);
+    ne += ms[k].n_det;
+    d->col_ptr[nc + 1] = ne;
+    d->col_obs[nc] = ms[k].obs;
+    d->col_p[nc] = pm;
+    d->col_llr[nc] = (float)log((1.0 - pm) / pm);
+    ++nc;
+    k = e;
+  }
+  d->n_cols = nc;
+  for (int k = 0; k < nm; ++k) free(ms[k].dets);
+  free(ms);
+}
+
 qdo_dem* qdo_dem_build(const qdo_code* c, double p, int rounds) {
   qdo_dem* d = calloc(1, sizeof(qdo_dem));
   d->code = *c;
@@ -299,38 +335,59 @@ qdo_dem* qdo_dem_build(const qdo_code* c, double p, int rounds) {
     }
   }
   free(tmp);
-  /* sort by (detectors, observables, probability) so equal columns are
-   * adjacent with their probabilities ascending, then merge */
-  qsort(ms, nm, sizeof(mech_t), cmp_mech_q);
-  d->col_ptr = malloc(sizeof(int) * (nm + 1));
-  d->col_obs = malloc(sizeof(uint32_t) * nm);
-  d->col_p = malloc(sizeof(double) * nm);
-  d->col_llr = malloc(sizeof(float) * nm);
-  int tot = 0;
-  for (int k = 0; k < nm; ++k) tot += ms[k].n_det;
-  d->col_dets = malloc(sizeof(int) * (tot > 0 ? tot : 1));
-  int nc = 0, ne = 0;
-  d->col_ptr[0] = 0;
-  for (int k = 0; k < nm;) {
-    int e = k;
-    double pm = 0.0;
-    while (e < nm && cmp_mech(&ms[k], &ms[e]) == 0) {
-      double q = ms[e].p;
-      pm = pm * (1.0 - q) + q * (1.0 - pm);
-      ++e;
-    }
-    memcpy(d->col_dets + ne, ms[k].dets, sizeof(int) * ms[k].n_det);
-    ne += ms[k].n_det;
-    d->col_ptr[nc + 1] = ne;
-    d->col_obs[nc] = ms[k].obs;
-    d->col_p[nc] = pm;
-    d->col_llr[nc] = (float)log((1.0 - pm) / pm);
-    ++nc;
-    k = e;
+  merge_mechanisms(d, ms, nm);
+  return d;
+}
+
+/*
+ * Code-capacity models of the appendices, decoded with H_X: every data qubit
+ * flips independently with probability pd (appendix "Data qubit noise",
+ * BSC(p_d)); block 0 holds the syndrome H_X e.  With ps > 0 every syndrome
+ * bit also flips with probability ps, one virtual column per check (appendix
+ * "Single shot syndrome noise", [H_X | I]), and a second, noiseless block
+ * holds H_X e of the data error alone: a window over block 0 decodes, and the
+ * Eq. (11) residue of block 1 after the commit is the appendix's success
+ * test (the data estimate must reproduce the true data syndrome).  The
+ * observables are the logical operators such errors can flip (kernel of H_Z
+ * modulo the row span of H_X).  Columns are merged and ordered like the
+ * circuit DEM's.
+ */
+qdo_dem* qdo_dem_code_capacity(const qdo_code* c, double pd, double ps) {
+  qdo_dem* d = calloc(1, sizeof(qdo_dem));
+  d->code = *c;
+  d->w = c->l * c->m;
+  d->R = ps > 0.0 ? 1 : 0;
+  d->p = pd;
+  d->n_det = (d->R + 1) * d->w;
+  int w = d->w, n = 2 * w;
+  uint8_t* HX = malloc((size_t)w * n);
+  d->HZ = malloc((size_t)w * n);
+  qdo_code_matrices(c, HX, d->HZ);
+  d->LZ = malloc((size_t)32 * n);
+  d->K = qdo_logical_x(c, d->LZ, 32);
+  int nm = n + (ps > 0.0 ? w : 0);
+  mech_t* ms = malloc(sizeof(mech_t) * nm);
+  for (int i = 0; i < n; ++i) {
+    ms[i].dets = malloc(sizeof(int) * 2 * w);
+    ms[i].n_det = 0;
+    for (int b = 0; b <= d->R; ++b)
+      for (int j = 0; j < w; ++j)
+        if (HX[(size_t)j * n + i]) ms[i].dets[ms[i].n_det++] = b * w + j;
+    ms[i].obs = 0;
+    for (int k = 0; k < d->K; ++k)
+      if (d->LZ[(size_t)k * n + i]) ms[i].obs |= 1u << k;
+    ms[i].p = pd;
   }
-  d->n_cols = nc;
-  for (int k = 0; k < nm; ++k) free(ms[k].dets);
-  free(ms);
+  for (int j = 0; ps > 0.0 && j < w; ++j) {
+    mech_t* m = &ms[n + j];
+    m->dets = malloc(sizeof(int));
+    m->dets[0] = j;
+    m->n_det = 1;
+    m->obs = 0;
+    m->p = ps;
+  }
+  free(HX);
+  merge_mechanisms(d, ms, nm);
   return d;
 }
 

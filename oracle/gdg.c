@@ -680,6 +680,12 @@ static int cmp_rank(const void* a, const void* b) {
 static int decode_window_impl(const window_t* wd, const qdo_params* P, const uint8_t* synd,
                               uint8_t* corr, int* info, int* short_cols, qdo_branch_summary* br,
                               qdo_step_record* steps, int8_t* fstat) {
+  if (wd->nc == 0) {
+    /* READING: a window without columns decides nothing; the commit's
+     * residue test sees its syndrome */
+    if (info) { info[0] = 1; info[1] = -1; info[2] = 0; info[3] = 0; }
+    return 0;
+  }
   graph_t g;
   graph_init(&g, wd->nr, wd->nc, wd->col_ptr, wd->col_rows, wd->llr);
   const float* W = (P->wts && P->wT > 0) ? P->wts[wd->k] : NULL;

@@ -63,6 +63,9 @@ def lib():
         L.qdo_n_paths.argtypes = [C.c_void_p]
         L.qdo_path_dmax_all.argtypes = [C.c_void_p]
         L.qdo_dem_build.restype = C.c_void_p
+        L.qdo_dem_code_capacity.restype = C.c_void_p
+        L.qdo_dem_code_capacity.argtypes = [P(QdoCode), C.c_double, C.c_double]
+        L.qdo_logical_x.argtypes = [P(QdoCode), C.c_void_p, C.c_int]
         L.qdo_dem_build.argtypes = [P(QdoCode), C.c_double, C.c_int]
         L.qdo_dem_free.argtypes = [C.c_void_p]
         L.qdo_dem_info.argtypes = [C.c_void_p, C.c_void_p]
@@ -166,6 +169,16 @@ def logical_z(code):
     return LZ[:K].copy()
 
 
+def logical_x(code):
+    """Logical operators flipped by errors decoded with H_X (kernel of H_Z
+    modulo the row span of H_X)."""
+    c = make_code(code)
+    w = code["l"] * code["m"]
+    LX = np.zeros((64, 2 * w), np.uint8)
+    K = lib().qdo_logical_x(C.byref(c), _ptr(LX), 64)
+    return LX[:K].copy()
+
+
 def philox4x32_10(ctr, key):
     c = np.asarray(ctr, np.uint32)
     k = np.asarray(key, np.uint32)
@@ -206,12 +219,18 @@ def gdg_graph(params, n_rows, col_ptr, col_rows, llr, synd):
 class OracleDEM:
     """Detector error model built by the oracle (direct per-fault simulation)."""
 
-    def __init__(self, code, p, rounds):
+    def __init__(self, code, p, rounds, capacity=None):
+        """Circuit-level DEM of the Z-basis memory (rounds noisy rounds), or,
+        with capacity=(p_data, p_synd), the code-capacity model of the
+        appendices decoded with H_X ([H_X | I] when p_synd > 0)."""
         self.code = code
         self.p = p
         self.rounds = rounds
         self._c = make_code(code)
-        self.h = lib().qdo_dem_build(C.byref(self._c), p, rounds)
+        if capacity is None:
+            self.h = lib().qdo_dem_build(C.byref(self._c), p, rounds)
+        else:
+            self.h = lib().qdo_dem_code_capacity(C.byref(self._c), float(capacity[0]), float(capacity[1]))
         info = np.zeros(6, np.int32)
         lib().qdo_dem_info(self.h, _ptr(info))
         self.n_det, self.n_cols, self.K, self.n_blocks, self.w, nnz = (int(x) for x in info)

@@ -96,9 +96,16 @@ typedef struct qdo_dem qdo_dem;
 int qdo_code_matrices(const qdo_code* c, uint8_t* HX, uint8_t* HZ); /* dense w x 2w each */
 int qdo_gf2_rank(const uint8_t* M, int rows, int cols);
 int qdo_logical_z(const qdo_code* c, uint8_t* LZ /* K x 2w */, int max_k);
+/* Logical operators flipped by errors decoded with H_X: kernel of H_Z modulo
+ * the row span of H_X (appendices A and B). */
+int qdo_logical_x(const qdo_code* c, uint8_t* LX /* K x 2w */, int max_k);
 
 /* ---- circuit / DEM ---- */
 qdo_dem* qdo_dem_build(const qdo_code* c, double p, int rounds);
+/* Code-capacity DEM (appendices A, B): BSC(pd) on the data qubits decoded with
+ * H_X, and with ps > 0 one virtual column per check ([H_X | I]); one block of
+ * w detectors. */
+qdo_dem* qdo_dem_code_capacity(const qdo_code* c, double pd, double ps);
 void qdo_dem_free(qdo_dem* d);
 /* out: n_det, n_cols, n_obs, n_blocks, w, total_col_edges */
 void qdo_dem_info(const qdo_dem* d, int* out);

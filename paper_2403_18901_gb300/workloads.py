@@ -39,6 +39,15 @@ CONFIGURED = dict(_COMMON, alpha=0.625, n_pre=100, iters_per_step=10, d_max_main
 PAPER = dict(_COMMON, alpha=1.0, n_pre=8, iters_per_step=6, d_max_main=25, side_max=10)
 
 
+# Code-capacity workloads of the appendices (data-qubit noise BSC(p_d) decoded
+# with H_X; single-shot syndrome noise with [H_X | I]): one window over the
+# whole matrix, no pre-BP and no shortening, alpha = 0.625, low-error mode,
+# main branch D_max 40, guessing tree of depth 5, side branches up to
+# D_split = 20, every non-main path running 30 steps past its last guess.
+CAPACITY = dict(_COMMON, W=1, F=1, alpha=0.625, n_pre=0, iters_per_step=6, d_max_main=40,
+                low_error_mode=1, shorten=0, side_max=20, k_guess=5, d_max_other=35)
+
+
 def preset(name, k_guess, p=None, **over):
     """Decoder parameters; the non-main paths run 10 steps past depth k.
     The "paper" preset of [[288,12,18]] (Sec. IV-C) is
