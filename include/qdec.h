@@ -120,6 +120,21 @@ const char* qd_last_error_message(void);
  * Errors: QD_EINVAL for l, m < 1, rounds < 1, p outside (0, 0.5).
  */
 qd_status qd_build_dem(const qd_bb_code* code, const qd_noise* noise, qd_dem** out);
+
+/*
+ * Code-capacity models of the appendices, decoded with H_X = [A|B]:
+ *   p_synd = 0: every data qubit flips with probability p_data (appendix
+ *     "Data qubit noise", BSC(p_d)); one block of w detectors, H_X e.
+ *   p_synd > 0: also every syndrome bit flips with probability p_synd, one
+ *     virtual column per check (appendix "Single shot syndrome noise",
+ *     [H_X | I]); block 0 holds the noisy syndrome H_X e + s', a noiseless
+ *     block 1 holds H_X e.  Decode with W = F = 1: window 0 decides every
+ *     column, window 1 has none and its commit's Eq. (11) residue is the
+ *     appendix's success test (the data estimate must have the data syndrome).
+ * Observables: a basis of the kernel of H_Z independent of the row span of
+ * H_X.  Same ownership and errors as qd_build_dem.
+ */
+qd_status qd_build_dem_code_capacity(const qd_bb_code* code, double p_data, double p_synd, qd_dem** out);
 qd_status qd_dem_info(const qd_dem* dem, qd_dem_info_t* out);
 /* Host copies of the DEM (CSC over detectors): col_ptr[n_cols+1],
  * col_dets[n_edges], obs[n_cols], prob[n_cols], llr[n_cols] (Lambda_i =

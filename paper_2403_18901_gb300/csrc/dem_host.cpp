@@ -139,6 +139,56 @@ bool mech_key_less(const Mech& x, const Mech& y) {
 }
 bool mech_key_eq(const Mech& x, const Mech& y) { return x.dets == y.dets && x.obs == y.obs; }
 
+// H_X = [A|B], H_Z = [B^T|A^T] as bitsets over the 2w data qubits (L then R).
+void code_matrices(const qd_bb_code& code, std::vector<Bits>& HX, std::vector<Bits>& HZ) {
+  const Group G{code.l, code.m};
+  const int w = code.l * code.m, n = 2 * w;
+  HX.assign(w, Bits(n));
+  HZ.assign(w, Bits(n));
+  for (int i = 0; i < w; ++i)
+    for (int k = 0; k < 3; ++k) {
+      HX[i].flip(G.add(i, code.a_x[k], code.a_y[k]));
+      HX[i].flip(w + G.add(i, code.b_x[k], code.b_y[k]));
+      HZ[i].flip(G.add(i, -code.b_x[k], -code.b_y[k]));
+      HZ[i].flip(w + G.add(i, -code.a_x[k], -code.a_y[k]));
+    }
+}
+
+// Merge mechanisms with identical (detectors, observables) as independent
+// flips, p <- p(1-q) + q(1-p) in ascending q (Sec. II-B), in canonical column
+// order (detector lists lexicographically, then observables); the prior is
+// Lambda = log((1-p)/p) (Sec. II-A) and the sampling threshold round(p 2^32).
+void finish_columns(std::vector<Mech>& mechs, DemHost& D) {
+  std::sort(mechs.begin(), mechs.end(), [](const Mech& x, const Mech& y) {
+    if (!mech_key_eq(x, y)) return mech_key_less(x, y);
+    return x.p < y.p;
+  });
+  D.col_ptr.assign(1, 0);
+  D.col_dets.clear();
+  D.col_obs.clear();
+  D.col_p.clear();
+  D.col_llr.clear();
+  D.col_thr.clear();
+  for (size_t a = 0; a < mechs.size();) {
+    size_t b = a;
+    double pm = 0.0;
+    while (b < mechs.size() && mech_key_eq(mechs[a], mechs[b])) {
+      double q = mechs[b].p;
+      pm = pm * (1.0 - q) + q * (1.0 - pm);
+      ++b;
+    }
+    D.col_dets.insert(D.col_dets.end(), mechs[a].dets.begin(), mechs[a].dets.end());
+    D.col_ptr.push_back((int)D.col_dets.size());
+    D.col_obs.push_back(mechs[a].obs);
+    D.col_p.push_back(pm);
+    D.col_llr.push_back((float)std::log((1.0 - pm) / pm));
+    double t = std::floor(pm * 4294967296.0 + 0.5);
+    D.col_thr.push_back(t >= 4294967295.0 ? 0xFFFFFFFFu : (t <= 0.0 ? 0u : (uint32_t)t));
+    a = b;
+  }
+  D.n_cols = (int)D.col_obs.size();
+}
+
 }  // namespace
 
 bool build_dem_host(const qd_bb_code& code, const qd_noise& noise, DemHost& D) {
@@ -156,15 +206,8 @@ bool build_dem_host(const qd_bb_code& code, const qd_noise& noise, DemHost& D) {
   auto fwd = [&](int i, std::pair<int, int> s) { return G.add(i, s.first, s.second); };
   auto bwd = [&](int i, std::pair<int, int> s) { return G.add(i, -s.first, -s.second); };
 
-  // H_X, H_Z as bitsets over the 2w data qubits (L then R)
-  std::vector<Bits> HX(w, Bits(n)), HZ(w, Bits(n));
-  for (int i = 0; i < w; ++i)
-    for (int k = 0; k < 3; ++k) {
-      HX[i].flip(fwd(i, a_sh(k)));
-      HX[i].flip(w + fwd(i, b_sh(k)));
-      HZ[i].flip(bwd(i, b_sh(k)));
-      HZ[i].flip(w + bwd(i, a_sh(k)));
-    }
+  std::vector<Bits> HX, HZ;
+  code_matrices(code, HX, HZ);
   std::vector<Bits> LZ = logical_z(HX, HZ, n);
   D.K = (int)LZ.size();
   if (D.K > 32) {
@@ -266,35 +309,47 @@ bool build_dem_host(const qd_bb_code& code, const qd_noise& noise, DemHost& D) {
     }
   }
 
-  // ---- merge identical columns, canonical order ----
-  std::sort(mechs.begin(), mechs.end(), [](const Mech& x, const Mech& y) {
-    if (!mech_key_eq(x, y)) return mech_key_less(x, y);
-    return x.p < y.p;
-  });
-  D.col_ptr.assign(1, 0);
-  D.col_dets.clear();
-  D.col_obs.clear();
-  D.col_p.clear();
-  D.col_llr.clear();
-  D.col_thr.clear();
-  for (size_t a = 0; a < mechs.size();) {
-    size_t b = a;
-    double pm = 0.0;
-    while (b < mechs.size() && mech_key_eq(mechs[a], mechs[b])) {
-      double q = mechs[b].p;
-      pm = pm * (1.0 - q) + q * (1.0 - pm);
-      ++b;
-    }
-    D.col_dets.insert(D.col_dets.end(), mechs[a].dets.begin(), mechs[a].dets.end());
-    D.col_ptr.push_back((int)D.col_dets.size());
-    D.col_obs.push_back(mechs[a].obs);
-    D.col_p.push_back(pm);
-    D.col_llr.push_back((float)std::log((1.0 - pm) / pm));
-    double t = std::floor(pm * 4294967296.0 + 0.5);
-    D.col_thr.push_back(t >= 4294967295.0 ? 0xFFFFFFFFu : (t <= 0.0 ? 0u : (uint32_t)t));
-    a = b;
+  finish_columns(mechs, D);
+  return true;
+}
+
+
+// Code-capacity models of the appendices, decoded with H_X: BSC(pd) on the
+// data qubits (block 0: H_X e) and, with ps > 0, BSC(ps) on the syndrome bits
+// as one virtual column per check ([H_X | I]) plus a noiseless block 1 holding
+// H_X e of the data error alone, whose Eq. (11) residue after the commit is
+// the appendix's success test.  Observables: the logical operators such
+// errors flip (kernel of H_Z modulo the row span of H_X).
+bool build_dem_code_capacity(const qd_bb_code& code, double pd, double ps, DemHost& D) {
+  const int w = code.l * code.m, n = 2 * w;
+  D.code = code;
+  D.noise = qd_noise{pd, 0};
+  D.w = w;
+  D.R = ps > 0.0 ? 1 : 0;
+  D.n_det = (D.R + 1) * w;
+  std::vector<Bits> HX, HZ;
+  code_matrices(code, HX, HZ);
+  std::vector<Bits> LX = logical_z(HZ, HX, n);
+  D.K = (int)LX.size();
+  if (D.K > 32) {
+    set_error("more than 32 logical qubits");
+    return false;
   }
-  D.n_cols = (int)D.col_obs.size();
+  std::vector<Mech> mechs;
+  for (int q = 0; q < n; ++q) {
+    Mech m;
+    m.obs = 0;
+    m.p = pd;
+    for (int b = 0; b <= D.R; ++b)
+      for (int j = 0; j < w; ++j)
+        if (HX[j].get(q)) m.dets.push_back(b * w + j);
+    for (int k = 0; k < D.K; ++k)
+      if (LX[k].get(q)) m.obs |= 1u << k;
+    mechs.push_back(std::move(m));
+  }
+  if (ps > 0.0)
+    for (int j = 0; j < w; ++j) mechs.push_back(Mech{{j}, 0u, ps});
+  finish_columns(mechs, D);
   return true;
 }
 

@@ -205,6 +205,23 @@ qd_status qd_build_dem(const qd_bb_code* code, const qd_noise* noise, qd_dem** o
   return QD_OK;
 }
 
+qd_status qd_build_dem_code_capacity(const qd_bb_code* code, double p_data, double p_synd, qd_dem** out) {
+  QD_REQ(code && out, "qd_build_dem_code_capacity: null argument");
+  QD_REQ(code->l >= 1 && code->m >= 1 && code->l * code->m <= 4096, "qd_build_dem_code_capacity: bad l, m");
+  QD_REQ(p_data > 0.0 && p_data < 0.5, "qd_build_dem_code_capacity: p_data outside (0, 0.5)");
+  QD_REQ(p_synd >= 0.0 && p_synd < 0.5, "qd_build_dem_code_capacity: p_synd outside [0, 0.5)");
+  std::unique_ptr<qd_dem> d(new (std::nothrow) qd_dem());
+  if (!d) return QD_ENOMEM;
+  if (!qd::build_dem_code_capacity(*code, p_data, p_synd, d->h)) return QD_EINVAL;
+  for (float l : d->h.col_llr)
+    if (!(l > std::ldexp(1.0f, -15) && l < 16.0f)) {
+      set_error("qd_build_dem_code_capacity: prior LLR outside (2^-15, 16); Eq. (5) would not be exact");
+      return QD_EUNSUPPORTED;
+    }
+  *out = d.release();
+  return QD_OK;
+}
+
 qd_status qd_dem_info(const qd_dem* d, qd_dem_info_t* o) {
   QD_REQ(d && o, "qd_dem_info: null argument");
   o->n_det = d->h.n_det;
@@ -444,6 +461,12 @@ qd_status qd_decode_windows(qd_decoder* dec, int k, const uint32_t* det_bits, in
   const WinGpu& g = dec->wins[k];
   cudaStream_t st = (cudaStream_t)stream;
   const int dw = (dec->dem->h.n_det + 31) / 32;
+  if (g.h.n_cols == 0) {
+    // a window without columns decides nothing (the commit tests its residue)
+    QD_CK(cudaMemsetAsync(win_correction, 0, sizeof(uint32_t) * (size_t)n_shots * dec->corr_words, st));
+    if (status) QD_CK(cudaMemsetAsync(status, 0xFF, sizeof(int32_t) * (size_t)n_shots, st));
+    return QD_OK;
+  }
   // path mode while the batch leaves most SMs idle in shot mode
   bool path_mode = dec->launch_mode == 2;
   if (dec->launch_mode == 0) path_mode = n_shots * 4 <= dec->sm_count;
@@ -685,7 +708,7 @@ extern "C" qd_status qd_decode_commit_static(qd_decoder* dec, int k, uint32_t* d
   QD_CK(cudaMemsetAsync(base, 0, kStaticHeader, st));
   long long grid = std::min<long long>(n_shots, (long long)dec->sm_count * g.grid_per_sm);
   const int dw = (dec->dem->h.n_det + 31) / 32;
-  QD_CK(qd::launch_decode(0, (int)grid, 32 * g.shot_warps, g.L.total, st, dec->kp, g.dv, g.L, det_bits, dw,
+  if (g.h.n_cols > 0) QD_CK(qd::launch_decode(0, (int)grid, 32 * g.shot_warps, g.L.total, st, dec->kp, g.dv, g.L, det_bits, dw,
                           n_shots, corr, dec->corr_words, nullptr, nullptr, 0, dec->dmx, dec->ns_max, work, stats,
                           nullptr, nullptr, dec->sw_max));
   const int w = dec->dem->h.w;
@@ -787,8 +810,13 @@ int batch_members(qd_batch* b, int j, uint32_t* const* det, const int64_t* n, ui
   return (int)out.size();
 }
 
-qd_status batch_decode(qd_batch* b, int j, const std::vector<qd::BatchMember>& m, cudaStream_t st) {
+qd_status batch_decode(qd_batch* b, int j, const std::vector<qd::BatchMember>& all, cudaStream_t st) {
   const qd_batch::Step& S = b->steps[j];
+  // windows without columns decide nothing; their commits still test the residue
+  std::vector<qd::BatchMember> m;
+  for (const auto& x : all)
+    if (x.W->n_cols > 0) m.push_back(x);
+  if (m.empty()) return QD_OK;
   long long tot = 0;
   for (const auto& x : m) tot += x.n;
   QD_CK(cudaMemsetAsync(b->d_work + j, 0, sizeof(int), st));

@@ -45,6 +45,8 @@ struct RankRec;
 
 // Build the merged DEM (backward sensitivity sweep over the circuit).
 bool build_dem_host(const qd_bb_code& code, const qd_noise& noise, DemHost& out);
+// Code-capacity models of the appendices (BSC on data qubits; [H_X | I]).
+bool build_dem_code_capacity(const qd_bb_code& code, double p_data, double p_synd, DemHost& out);
 int n_windows(const DemHost& d, int W, int F);
 bool build_window(const DemHost& d, int W, int F, int k, bool shorten, WindowHost& out);
 

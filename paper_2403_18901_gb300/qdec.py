@@ -57,6 +57,7 @@ _VP, _I, _I64, _U64, _SZ = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_size_
 _SIGS = {
     "qd_last_error_message": (C.c_char_p, []),
     "qd_build_dem": (_I, [C.POINTER(BBCode), C.POINTER(Noise), C.POINTER(_VP)]),
+    "qd_build_dem_code_capacity": (_I, [C.POINTER(BBCode), C.c_double, C.c_double, C.POINTER(_VP)]),
     "qd_dem_info": (_I, [_VP, C.POINTER(DemInfo)]),
     "qd_dem_columns": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "qd_dem_destroy": (_I, [_VP]),
@@ -158,12 +159,18 @@ def make_params(p):
 
 
 class Dem:
-    """Detector error model of the Z-basis memory experiment (qd_build_dem)."""
+    """Detector error model of the Z-basis memory experiment (qd_build_dem),
+    or with capacity=(p_data, p_synd) the code-capacity model of the
+    appendices (qd_build_dem_code_capacity; p and rounds are then ignored)."""
 
-    def __init__(self, code, p, rounds):
+    def __init__(self, code, p, rounds, capacity=None):
         self.code, self.p, self.rounds = code, p, rounds
         h = C.c_void_p()
-        _check(lib().qd_build_dem(C.byref(make_code(code)), C.byref(Noise(p, rounds)), C.byref(h)))
+        if capacity is None:
+            _check(lib().qd_build_dem(C.byref(make_code(code)), C.byref(Noise(p, rounds)), C.byref(h)))
+        else:
+            _check(lib().qd_build_dem_code_capacity(C.byref(make_code(code)), float(capacity[0]),
+                                                    float(capacity[1]), C.byref(h)))
         self.h = h
         inf = DemInfo()
         _check(lib().qd_dem_info(self.h, C.byref(inf)))

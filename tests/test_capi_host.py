@@ -58,6 +58,20 @@ def test_dem_equals_oracle(lib, key, R, p):
     assert (c["llr"] == o.col_llr).all()
 
 
+@pytest.mark.parametrize("key,pd,ps", [("288", 0.04, 1e-3), ("144", 0.02, 0.0), ("72", 0.05, 0.01)])
+def test_code_capacity_dem_equals_oracle(lib, key, pd, ps):
+    from oracle import oracle as O
+    d = qdec.Dem(CODES[key], 0, 0, capacity=(pd, ps))
+    o = O.OracleDEM(CODES[key], pd, 0, capacity=(pd, ps))
+    c = d.columns()
+    assert d.n_cols == o.n_cols and d.n_det == o.n_det and d.K == o.K and d.n_blocks == o.n_blocks
+    assert (c["col_ptr"] == o.col_ptr).all()
+    assert (c["col_dets"] == o.col_dets[:len(c["col_dets"])]).all()
+    assert (c["obs"] == o.col_obs).all()
+    assert (c["prob"] == o.col_p).all()
+    assert (c["llr"] == o.col_llr).all()
+
+
 def test_every_single_fault_is_a_dem_column(lib):
     """Fault by fault: the direct Pauli-frame simulation of every single fault
     (oracle) lands on a column of the library's merged DEM."""

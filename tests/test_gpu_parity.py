@@ -61,12 +61,16 @@ def test_sampler_bit_exact(key, R, n, off):
     assert (_u32(obs) == oo).all()
 
 
-def _pipeline(key, R, p, params, n, seed, trace_windows=(), mode=0, weights=None, ranker=None):
+def _pipeline(key, R, p, params, n, seed, trace_windows=(), mode=0, weights=None, ranker=None, capacity=None):
     """Run both implementations window by window on the same oracle-sampled
     shots; compare everything.  mode: launch shape (0 automatic, 1 one warp per
     decision path, 2 one CTA per decision path).  Returns (oracle fail, gpu fail)."""
-    o = oracle_dem(key, p, R)
-    d = qdec.Dem(CODES[key], p, R)
+    if capacity is None:
+        o = oracle_dem(key, p, R)
+    else:
+        from oracle import oracle as O
+        o = O.OracleDEM(CODES[key], capacity[0], 0, capacity=capacity)
+    d = qdec.Dem(CODES[key], p, R, capacity=capacity)
     dec = qdec.Decoder(d, params, max_shots=n)
     dec.set_launch(mode)
     if weights is not None:
@@ -282,3 +286,14 @@ def test_bb288_paper_tree_bit_exact():
     branches up to D_split = 20, 20 steps after a split (47 paths)."""
     params = preset("paper", 5, p=0.002, d_max_main=40, d_max_other=25, side_max=20, n_pre=16)
     _pipeline("288", 3, 0.003, params, n=16, seed=288_003, trace_windows=(0, 1), mode=1)
+
+
+@pytest.mark.parametrize("key,pd,ps,mode", [("288", 0.04, 1e-3, 1), ("288", 0.05, 3e-3, 2), ("144", 0.06, 0.0, 1)])
+def test_code_capacity_bit_exact(key, pd, ps, mode):
+    """Appendix workloads: BSC(p_d) decoded with H_X, and [H_X | I] with
+    syndrome noise; one window over the whole matrix (plus the residue-only
+    window of the single-shot model), GDG with the appendix's tree (D_max 40,
+    depth-5 guessing tree, side branches to D_split 20, 47 paths)."""
+    from paper_2403_18901_gb300.workloads import CAPACITY
+    _pipeline(key, 0, pd, dict(CAPACITY), n=64 if mode == 1 else 24, seed=288_100, trace_windows=(0,), mode=mode,
+              capacity=(pd, ps))
