@@ -53,13 +53,15 @@ __device__ __forceinline__ float c2v_msg(float alpha, float clip, const CNState&
 // (each edge applies its own weight); for the plain decoder they are stored
 // already multiplied by alpha (alpha * clip for a single active input), the
 // same FP32 products c2v_msg forms, so a message is one select and a sign.
+// `rows` (the check's CSR range, begin | end << 16) rides along in the
+// record's last word, so the check pass loads it with the state.
 template <bool LW>
 __device__ __forceinline__ CNState cn_store(float alpha, float clip, float m1, float m2, int am, uint32_t par,
-                                            bool single) {
-  if (LW) return CNState{m1, m2, (uint32_t)am | (par << 16) | ((uint32_t)single << 17), 0u};
+                                            bool single, uint32_t rows) {
+  if (LW) return CNState{m1, m2, (uint32_t)am | (par << 16) | ((uint32_t)single << 17), rows};
   const float s1 = __fmul_rn(alpha, single ? clip : m1);
   const float s2 = single ? s1 : __fmul_rn(alpha, m2);
-  return CNState{s1, s2, (uint32_t)am | (par << 16), 0u};
+  return CNState{s1, s2, (uint32_t)am | (par << 16), rows};
 }
 
 template <bool LW>
@@ -517,7 +519,10 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
     B.status[k] = -1;
     B.post[k] = G.llr[k];  // t = 0: mu_{i->j} = Lambda_i (Sec. II-A)
   }
-  for (int j = R; j < nr; j += S) B.deg[j] = G.rowptr[j + 1] - G.rowptr[j];
+  for (int j = R; j < nr; j += S) {
+    B.deg[j] = G.rowptr[j + 1] - G.rowptr[j];
+    B.cns[j].pad = (uint32_t)G.rowptr[j] | ((uint32_t)G.rowptr[j + 1] << 16);
+  }
   for (int x = R; x < rw; x += S) B.sp[x] = G.sbits[x];
   if (out.st)
     for (int q = R; q < dmx; q += S) out.st[q] = StepTrace{-2, -1, 0, 0, 0};
@@ -569,8 +574,8 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
           neg ^= sgn;
           B.sign[e] = (uint8_t)sgn;
         };
-        const int qe = d ? G.rowptr[j + 1] : 0;
-        for (int q = (d ? G.rowptr[j] : 0) + 2 * sub; q < qe; q += 2 * tpc) {
+        const int qe = d ? (int)(oc.pad >> 16) : 0;
+        for (int q = (d ? (int)(oc.pad & 0xFFFFu) : 0) + 2 * sub; q < qe; q += 2 * tpc) {
           const bool two = q + 1 < qe;
           const uint32_t e0 = G.rowent[q], e1 = two ? G.rowent[q + 1] : e0;
           const float p0 = B.post[e0 >> 16], p1 = B.post[e1 >> 16];
@@ -580,7 +585,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
         }
         if (tpc > 1) group_min2(m1, m2, am, neg, tpc);
         if (sub == 0 && d > 0)
-          B.cns[j] = cn_store<LW>(P.alpha, P.clip, m1, m2, am, neg ^ bit_of(B.sp, j), d == 1);
+          B.cns[j] = cn_store<LW>(P.alpha, P.clip, m1, m2, am, neg ^ bit_of(B.sp, j), d == 1, oc.pad);
       }
       g.sync();
       // ---- variable-node update, Eq. (2)-(3); history of Sec. IV-A ----
@@ -837,6 +842,35 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
   for (int x = tid; x < L.cw; x += NT) cbits[x] = 0;
   __syncthreads();
 
+  // the window graph in shared memory for the pre-BP loop when the union
+  // region has room (shot mode); the ranking and shortening below read W
+  WinDev Wg = W;
+  if (L.pre_stage) {
+    uint16_t* cp = (uint16_t*)(U + L.q_colptr);
+    uint16_t* cr = (uint16_t*)(U + L.q_colrows);
+    uint16_t* rp = (uint16_t*)(U + L.q_rowptr);
+    uint32_t* re = (uint32_t*)(U + L.q_rowent);
+    float* ll = (float*)(U + L.q_llr);
+    uint16_t* vp = (uint16_t*)(U + L.q_vperm);
+    for (int x = tid; x <= nc; x += NT) cp[x] = W.col_ptr[x];
+    for (int x = tid; x <= nr; x += NT) rp[x] = W.row_ptr[x];
+    for (int x = tid; x < W.n_edges; x += NT) {
+      cr[x] = W.col_rows[x];
+      re[x] = W.row_ent[x];
+    }
+    for (int x = tid; x < nc; x += NT) {
+      ll[x] = W.llr[x];
+      vp[x] = W.vperm[x];
+    }
+    Wg.col_ptr = cp;
+    Wg.col_rows = cr;
+    Wg.row_ptr = rp;
+    Wg.row_ent = re;
+    Wg.llr = ll;
+    Wg.vperm = vp;
+    __syncthreads();
+  }
+
   // ---- a2: pre-BP on the full window ----
   const int tpc_pre = WIDE ? lanes_per_check(NT, nr) : 1, sub_pre = tid & (tpc_pre - 1);
   const int nr_rounds = (nr + NT / tpc_pre - 1) / (NT / tpc_pre) * (NT / tpc_pre);
@@ -848,12 +882,12 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
     for (int x = tid; x < L.rw; x += NT) pb[x] = 0;
     __syncthreads();
     for (int i = tid; i < nc; i += NT) {
-      const float li = W.llr[i];
+      const float li = Wg.llr[i];
       post[i] = li;
       key[i] = __fadd_rn(__fadd_rn(__fadd_rn(li, li), li), li);
       if (li <= 0.0f)
-        for (int e = W.col_ptr[i]; e < W.col_ptr[i + 1]; ++e) {
-          const int j = W.col_rows[e];
+        for (int e = Wg.col_ptr[i]; e < Wg.col_ptr[i + 1]; ++e) {
+          const int j = Wg.col_rows[e];
           atomicXor(&pb[j >> 5], 1u << (j & 31));
         }
     }
@@ -867,7 +901,7 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
     for (int x = tid; x < L.rw; x += NT) pb[x] = 0;
     for (int j0 = tid / tpc_pre; j0 < nr_rounds; j0 += NT / tpc_pre) {
       const int j = j0 < nr ? j0 : nr - 1;
-      const int beg = W.row_ptr[j], end = j0 < nr ? W.row_ptr[j + 1] : beg;
+      const int beg = Wg.row_ptr[j], end = j0 < nr ? Wg.row_ptr[j + 1] : beg;
       const CNState oc = cns[j];
       float m1 = CUDART_INF_F, m2 = CUDART_INF_F;
       int am = 0xFFFF;
@@ -877,11 +911,11 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
         float pv[4];
         uint32_t sg[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) ent[u] = (q + u < end) ? W.row_ent[q + u] : 0u;
+        for (int u = 0; u < 4; ++u) ent[u] = (q + u < end) ? Wg.row_ent[q + u] : 0u;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int i = (int)(ent[u] >> 16), e = (int)(ent[u] & 0xFFFFu);
-          pv[u] = (t == 1) ? W.llr[i] : post[i];
+          pv[u] = (t == 1) ? Wg.llr[i] : post[i];
           sg[u] = sign[e];
         }
 #pragma unroll
@@ -905,17 +939,17 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
       }
       if (tpc_pre > 1) group_min2(m1, m2, am, neg, tpc_pre);
       if (sub_pre == 0 && j0 < nr)
-        cns[j] = cn_store<LW>(P.alpha, P.clip, m1, m2, am, neg ^ bit_of(sbits, j), end - beg == 1);
+        cns[j] = cn_store<LW>(P.alpha, P.clip, m1, m2, am, neg ^ bit_of(sbits, j), end - beg == 1, 0u);
     }
     __syncthreads();
     const bool kacc = t >= tk0;
     for (int i0 = tid; i0 < nc; i0 += NT) {
-      const int i = W.vperm[i0];  // descending degree: the lanes of a round loop alike
-      float p = W.llr[i];
-      const int eb = W.col_ptr[i], ee = W.col_ptr[i + 1];
+      const int i = Wg.vperm[i0];  // descending degree: the lanes of a round loop alike
+      float p = Wg.llr[i];
+      const int eb = Wg.col_ptr[i], ee = Wg.col_ptr[i + 1];
       auto msg = [&](int e) {
         const float wt = LW ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t, e) : P.alpha;
-        return c2v<LW>(wt, P.clip, cns[W.col_rows[e]], e, sign[e]);
+        return c2v<LW>(wt, P.clip, cns[Wg.col_rows[e]], e, sign[e]);
       };
       int e = eb;  // ascending check order (Eq. (2))
       for (; e + 1 < ee; e += 2) {
@@ -929,7 +963,7 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
         float kv;
         if (t == tk0) {
           if (P.n_pre < 4) {
-            const float li = W.llr[i];
+            const float li = Wg.llr[i];
             float s = li;
             for (int r = 1; r < 4 - P.n_pre; ++r) s = __fadd_rn(s, li);
             kv = __fadd_rn(s, p);
@@ -943,7 +977,7 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
       }
       if (p <= 0.0f)
         for (int e = eb; e < ee; ++e) {
-          const int j = W.col_rows[e];
+          const int j = Wg.col_rows[e];
           atomicXor(&pb[j >> 5], 1u << (j & 31));
         }
     }

@@ -117,6 +117,9 @@ struct Layout {
   unsigned U;  // start of the union region
   // pre-BP (relative to U)
   unsigned p_post, p_key, p_cns, p_sign, p_par, p_sort, p_end;
+  // the window graph staged for the pre-BP loop in otherwise idle union bytes
+  // (from p_sort on; overwritten by the sort that follows); pre_stage = 0: none
+  unsigned pre_stage, q_colptr, q_colrows, q_rowptr, q_rowent, q_llr, q_vperm;
   // one path slot (relative to the slot base)
   unsigned b_post, b_acc, b_hfl, b_status, b_sign, b_cns, b_deg, b_sp, b_par, b_unsat, b_hq, b_size;
   unsigned total;
@@ -186,6 +189,16 @@ __host__ __device__ inline Layout make_layout(int nr, int nc, int ne, int ns, in
   L.b_hq = b; b = al16(b + (ranker ? 4u * ns : 0u));
   L.b_size = b;
   unsigned ub = L.p_end > b * (unsigned)nslots ? L.p_end : b * (unsigned)nslots;
+  if (!stage_graph) {
+    unsigned q = L.p_sort;
+    L.q_colptr = q; q = al16(q + 2u * (nc + 1));
+    L.q_colrows = q; q = al16(q + 2u * ne);
+    L.q_rowptr = q; q = al16(q + 2u * (nr + 1));
+    L.q_rowent = q; q = al16(q + 4u * ne);
+    L.q_llr = q; q = al16(q + 4u * nc);
+    L.q_vperm = q; q = al16(q + 2u * nc);
+    L.pre_stage = q <= ub ? 1u : 0u;
+  }
   L.total = L.U + ub;
   return L;
 }
