@@ -456,10 +456,12 @@ qd_status qd_decoder_set_launch(qd_decoder* dec, int mode);
  * path mode, out[4] its threads, out[5] SM count. */
 qd_status qd_decoder_launch_info(const qd_decoder* dec, int k, int out[6]);
 
-/* Counters of the last qd_decode_windows call of window k, summed over shots:
- * out[0] pre-BP edge-iterations, out[1] GDG edge-iterations, out[2] windows
- * whose pre-BP converged, out[3] windows that ran GDG.  Synchronous. */
-qd_status qd_decoder_counters(qd_decoder* dec, long long out[4]);
+/* Counters summed over every decode since the last reset: out[0] pre-BP
+ * edge-iterations, out[1] GDG edge-iterations, out[2] windows whose pre-BP
+ * converged, out[3] windows that ran GDG, out[4] bulk (TMA) staging copies
+ * whose bounded wait ran out (then copied with plain loads; expected 0).
+ * Synchronous. */
+qd_status qd_decoder_counters(qd_decoder* dec, long long out[5]);
 qd_status qd_decoder_reset_counters(qd_decoder* dec, qd_stream_t stream);
 
 #ifdef __cplusplus

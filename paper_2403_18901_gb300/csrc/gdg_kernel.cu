@@ -73,6 +73,87 @@ __device__ __forceinline__ float c2v(float w, float clip, const CNState& c, int 
 
 __device__ __forceinline__ uint32_t bit_of(const uint32_t* w, int j) { return (w[j >> 5] >> (j & 31)) & 1u; }
 
+// ---- bulk asynchronous copies global -> shared (TMA, cp.async.bulk) ----
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// A CTA's staging state: its mbarrier (one arrival + transaction bytes per
+// phase), the parity of the phase in flight, a shared flag that turns the
+// bulk path off after a wait ran out, and the counter such events go to.
+struct Stager {
+  uint64_t* bar;
+  int* off;
+  long long* err;
+  unsigned phase;
+};
+
+__device__ __forceinline__ Stager stager_init(char* where, long long* err) {
+  Stager st{(uint64_t*)where, (int*)(where + 8), err, 0u};
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(st.bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *st.off = 0;
+  }
+  __syncthreads();
+  return st;
+}
+
+struct StagePiece {
+  void* dst;
+  const void* src;
+  unsigned bytes;
+};
+
+// Copies the pieces into shared memory, all threads calling: one bulk copy
+// per piece issued by thread 0, completion tracked on the mbarrier, every
+// thread waiting with a bound of ~2^31 cycles.  Pieces that are not 16-byte
+// aligned in address and size, an empty list, or a wait that ran out (counted
+// in *err; the bulk path then stays off for this CTA) use plain loads.
+__device__ void stage_pieces(Stager& st, const StagePiece* pc, int n) {
+  bool aligned = true;
+  unsigned tot = 0;
+  for (int i = 0; i < n; ++i) {
+    aligned = aligned && (((smem_u32(pc[i].dst) | (unsigned)(uintptr_t)pc[i].src | pc[i].bytes) & 15u) == 0u);
+    tot += pc[i].bytes;
+  }
+  __syncthreads();  // every earlier access to these bytes has finished
+  if (aligned && tot > 0 && !*st.off) {
+    if (threadIdx.x == 0) {
+      unsigned long long state;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                   : "=l"(state)
+                   : "r"(smem_u32(st.bar)), "r"(tot)
+                   : "memory");
+      for (int i = 0; i < n; ++i)
+        if (pc[i].bytes)
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                           smem_u32(pc[i].dst)),
+                       "l"(pc[i].src), "r"(pc[i].bytes), "r"(smem_u32(st.bar))
+                       : "memory");
+    }
+    unsigned ok = 0;
+    const long long t0 = clock64();
+    while (!ok && clock64() - t0 < (1ll << 31)) {
+      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                   : "=r"(ok)
+                   : "r"(smem_u32(st.bar)), "r"(st.phase)
+                   : "memory");
+    }
+    st.phase ^= 1u;
+    if (__syncthreads_and(ok != 0)) return;
+    if (threadIdx.x == 0) {
+      *st.off = 1;
+      atomicAdd((unsigned long long*)st.err, 1ull);
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    const uint16_t* s16 = (const uint16_t*)pc[i].src;
+    uint16_t* d16 = (uint16_t*)pc[i].dst;
+    for (unsigned x = threadIdx.x; x < pc[i].bytes / 2; x += blockDim.x) d16[x] = s16[x];
+  }
+  __syncthreads();
+}
+
 // Multiplier of Eq. (1) at iteration t >= 1 for full-window edge ef: alpha, or
 // the learned weight w[min(t, T)][ef].
 __device__ __forceinline__ float edge_weight(const float* wts, int wT, int wE, float alpha, int t, int ef) {
@@ -774,7 +855,8 @@ struct DecodeArgs {
   size_t tr_bytes;
   int dmx, ns_max;
   int* work;            // shot mode: work counter
-  long long* counters;  // [0] pre-BP edge-iterations, [1] GDG edge visits, [2] pre-BP converged, [3] GDG windows
+  long long* counters;  // [0] pre-BP edge-iterations, [1] GDG edge visits, [2] pre-BP converged,
+                        // [3] GDG windows, [4] bulk staging waits that ran out
   char* path_res;       // path mode: results [shot][path]
   int* arrive;          // path mode: per-shot arrival counters (0 between launches)
   int sw_max;
@@ -811,7 +893,8 @@ struct CommitBatch {
 // a1 + a2 (+ a3 when not converged): the shared prefix of both launch shapes.
 // Returns true when the pre-BP converged (cbits then hold its decision).
 template <bool LW, bool WIDE>
-__device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, long long shot, int* t_run_out) {
+__device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, long long shot, int* t_run_out,
+                              Stager& stg) {
   const KParams& P = A.P;
   const Layout& L = A.L;
   const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5;
@@ -852,23 +935,16 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
     uint32_t* re = (uint32_t*)(U + L.q_rowent);
     float* ll = (float*)(U + L.q_llr);
     uint16_t* vp = (uint16_t*)(U + L.q_vperm);
-    for (int x = tid; x <= nc; x += NT) cp[x] = W.col_ptr[x];
-    for (int x = tid; x <= nr; x += NT) rp[x] = W.row_ptr[x];
-    for (int x = tid; x < W.n_edges; x += NT) {
-      cr[x] = W.col_rows[x];
-      re[x] = W.row_ent[x];
-    }
-    for (int x = tid; x < nc; x += NT) {
-      ll[x] = W.llr[x];
-      vp[x] = W.vperm[x];
-    }
+    const StagePiece pc[6] = {{cp, W.col_ptr, al16(2u * (nc + 1))},       {cr, W.col_rows, al16(2u * W.n_edges)},
+                              {rp, W.row_ptr, al16(2u * (nr + 1))},       {re, W.row_ent, al16(4u * W.n_edges)},
+                              {ll, W.llr, al16(4u * nc)},                 {vp, W.vperm, al16(2u * nc)}};
+    stage_pieces(stg, pc, 6);
     Wg.col_ptr = cp;
     Wg.col_rows = cr;
     Wg.row_ptr = rp;
     Wg.row_ent = re;
     Wg.llr = ll;
     Wg.vperm = vp;
-    __syncthreads();
   }
 
   // ---- a2: pre-BP on the full window ----
@@ -1147,7 +1223,7 @@ __device__ void write_outputs(const DecodeArgs& A, char* sm, long long shot, boo
 // One shot of one window by the whole CTA (every thread calls).  misc[2], the
 // decision-path queue, must be 0 on entry.
 template <bool LW>
-__device__ void shot_body(const DecodeArgs& A, long long shot, char* sm) {
+__device__ void shot_body(const DecodeArgs& A, long long shot, char* sm, Stager& stg) {
   const Layout& L = A.L;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int* misc = (int*)(sm + L.misc);
@@ -1158,7 +1234,7 @@ __device__ void shot_body(const DecodeArgs& A, long long shot, char* sm) {
   const uint16_t* sel = (const uint16_t*)(sm + L.sel);
   char* tr = A.trace ? A.trace + (size_t)shot * A.tr_bytes : nullptr;
   int t_run = 0;
-  const bool conv = window_prefix<LW, false>(A, A.W, sm, shot, &t_run);
+  const bool conv = window_prefix<LW, false>(A, A.W, sm, shot, &t_run, stg);
   int winner = -1;
   const int n_short = conv ? 0 : A.W.n_short;
   if (!conv) {
@@ -1206,6 +1282,7 @@ template <bool LW>
 __global__ void __launch_bounds__(256, 2) decode_shot_kernel(DecodeArgs A) {
   extern __shared__ __align__(16) char sm[];
   int* misc = (int*)(sm + A.L.misc);
+  Stager stg = stager_init((char*)(misc + 8), &A.counters[4]);
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1215,7 +1292,7 @@ __global__ void __launch_bounds__(256, 2) decode_shot_kernel(DecodeArgs A) {
     __syncthreads();
     const long long shot = misc[0];
     if (shot >= A.n_shots) break;
-    shot_body<LW>(A, shot, sm);
+    shot_body<LW>(A, shot, sm, stg);
   }
 }
 
@@ -1229,6 +1306,7 @@ template <bool LW>
 __global__ void __launch_bounds__(256, 2) decode_batch_kernel(const __grid_constant__ BatchArgs B) {
   extern __shared__ __align__(16) char sm[];
   int* q = (int*)(sm + B.q_off);
+  Stager stg = stager_init((char*)(q + 4), &B.seg[0].counters[4]);
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) q[0] = atomicAdd(B.work, 1);
@@ -1241,7 +1319,7 @@ __global__ void __launch_bounds__(256, 2) decode_batch_kernel(const __grid_const
     const long long shot = g - (m ? B.seg_end[m - 1] : 0);
     if (threadIdx.x == 0) ((int*)(sm + A.L.misc))[2] = 0;
     __syncthreads();
-    shot_body<LW>(A, shot, sm);
+    shot_body<LW>(A, shot, sm, stg);
   }
 }
 
@@ -1256,6 +1334,7 @@ __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
   const int id = blockIdx.x % nb;
   int* misc = (int*)(sm + L.misc);
   char* tr = A.trace ? A.trace + (size_t)shot * A.tr_bytes : nullptr;
+  Stager stg = stager_init((char*)(misc + 8), &A.counters[4]);
   // stage the window graph in shared memory (one CTA per SM in this mode)
   WinDev W = A.W;
   if (L.g_bytes) {
@@ -1265,22 +1344,18 @@ __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
     uint16_t* rp = (uint16_t*)(sm + L.g_rowptr);
     uint32_t* re = (uint32_t*)(sm + L.g_rowent);
     float* ll = (float*)(sm + L.g_llr);
-    for (int x = tid; x <= G.n_cols; x += blockDim.x) cp[x] = G.col_ptr[x];
-    for (int x = tid; x <= G.n_rows; x += blockDim.x) rp[x] = G.row_ptr[x];
-    for (int x = tid; x < G.n_edges; x += blockDim.x) {
-      cr[x] = G.col_rows[x];
-      re[x] = G.row_ent[x];
-    }
-    for (int x = tid; x < G.n_cols; x += blockDim.x) ll[x] = G.llr[x];
+    const StagePiece pc[5] = {{cp, G.col_ptr, al16(2u * (G.n_cols + 1))}, {cr, G.col_rows, al16(2u * G.n_edges)},
+                              {rp, G.row_ptr, al16(2u * (G.n_rows + 1))}, {re, G.row_ent, al16(4u * G.n_edges)},
+                              {ll, G.llr, al16(4u * G.n_cols)}};
+    stage_pieces(stg, pc, 5);
     W.col_ptr = cp;
     W.col_rows = cr;
     W.row_ptr = rp;
     W.row_ent = re;
     W.llr = ll;
-    __syncthreads();
   }
   int t_run = 0;
-  const bool conv = window_prefix<LW, true>(A, W, sm, shot, &t_run);
+  const bool conv = window_prefix<LW, true>(A, W, sm, shot, &t_run, stg);
   if (conv) {
     if (id == 0) write_outputs(A, sm, shot, true, -1, 0, t_run, tr);
     return;

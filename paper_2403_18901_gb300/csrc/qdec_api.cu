@@ -357,9 +357,12 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
     dec->ns_max = std::max(dec->ns_max, h.n_short);
     dec->sw_max = std::max(dec->sw_max, (h.n_short + 31) / 32);
     // graph arrays in one allocation
-    size_t o_cp = 0, o_cr = o_cp + 2 * h.col_ptr.size(), o_rp = o_cr + 2 * h.col_rows.size(),
-           o_re = (o_rp + 2 * h.row_ptr.size() + 15) & ~(size_t)15, o_ll = o_re + 4 * h.row_ent.size(),
-           o_vp = o_ll + 4 * h.llr.size(), tot = o_vp + 2 * (size_t)h.n_cols;
+    // every array starts on a 16-byte boundary and is padded to a multiple of
+    // 16 bytes, as the kernels' bulk (TMA) copies into shared memory require
+    auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    size_t o_cp = 0, o_cr = a16(o_cp + 2 * h.col_ptr.size()), o_rp = a16(o_cr + 2 * h.col_rows.size()),
+           o_re = a16(o_rp + 2 * h.row_ptr.size()), o_ll = a16(o_re + 4 * h.row_ent.size()),
+           o_vp = a16(o_ll + 4 * h.llr.size()), tot = a16(o_vp + 2 * (size_t)h.n_cols);
     // pre-BP processing order of the variables: descending degree, ties by index
     std::vector<uint16_t> vperm(h.n_cols);
     for (int c = 0; c < h.n_cols; ++c) vperm[c] = (uint16_t)c;
@@ -404,8 +407,8 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
   QD_CK(cudaMalloc(&dec->d_path_res, qd::path_result_bytes(dec->sw_max) * k.nb * pm_shots));
   QD_CK(cudaMalloc(&dec->d_arrive, sizeof(int) * pm_shots));
   QD_CK(cudaMemset(dec->d_arrive, 0, sizeof(int) * pm_shots));
-  QD_CK(cudaMalloc(&dec->d_counters, sizeof(long long) * 4));
-  QD_CK(cudaMemset(dec->d_counters, 0, sizeof(long long) * 4));
+  QD_CK(cudaMalloc(&dec->d_counters, sizeof(long long) * 5));
+  QD_CK(cudaMemset(dec->d_counters, 0, sizeof(long long) * 5));
   const int dw = (dem->h.n_det + 31) / 32;
   QD_CK(cudaMalloc(&dec->d_corr, sizeof(uint32_t) * (size_t)max_shots * dec->corr_words));
   QD_CK(cudaMalloc(&dec->d_det, sizeof(uint32_t) * (size_t)max_shots * dw));
@@ -634,15 +637,15 @@ qd_status qd_decoder_set_launch(qd_decoder* dec, int mode) {
   return QD_OK;
 }
 
-qd_status qd_decoder_counters(qd_decoder* dec, long long out[4]) {
+qd_status qd_decoder_counters(qd_decoder* dec, long long out[5]) {
   QD_REQ(dec && out, "null argument");
-  QD_CK(cudaMemcpy(out, dec->d_counters, sizeof(long long) * 4, cudaMemcpyDeviceToHost));
+  QD_CK(cudaMemcpy(out, dec->d_counters, sizeof(long long) * 5, cudaMemcpyDeviceToHost));
   return QD_OK;
 }
 
 qd_status qd_decoder_reset_counters(qd_decoder* dec, qd_stream_t stream) {
   QD_REQ(dec, "null argument");
-  QD_CK(cudaMemsetAsync(dec->d_counters, 0, sizeof(long long) * 4, (cudaStream_t)stream));
+  QD_CK(cudaMemsetAsync(dec->d_counters, 0, sizeof(long long) * 5, (cudaStream_t)stream));
   return QD_OK;
 }
 
@@ -748,18 +751,18 @@ qd_status batch_plan(qd_batch* b, int j, int warps, size_t budget) {
     for (; s >= 1; --s) {
       S.L[i] = qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, d->kp.nb, s, false,
                                d->hist_on);
-      if (qd::al16(S.L[i].total) + 16 <= budget) break;
+      if (qd::al16(S.L[i].total) + 32 <= budget) break;
     }
     if (s < 1) {
       set_error("qd_batch: member " + std::to_string(i) + " window " + std::to_string(j) + " needs " +
-                std::to_string(S.L[i].total + 16) + " B of shared memory with one path slot (budget " +
+                std::to_string(S.L[i].total + 32) + " B of shared memory with one path slot (budget " +
                 std::to_string(budget) + ")");
       return QD_EUNSUPPORTED;
     }
     mx = std::max(mx, S.L[i].total);
   }
   S.q_off = qd::al16(mx);
-  S.smem = S.q_off + 16;
+  S.smem = S.q_off + 32;  // work slot, then the staging mbarrier and its flag
   S.warps = warps;
   S.budget = budget;
   int blocks = 0;

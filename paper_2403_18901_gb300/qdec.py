@@ -314,7 +314,9 @@ class Decoder:
         _check(lib().qd_decoder_set_launch(self.h, int(mode)))
 
     def counters(self):
-        out = np.zeros(4, np.int64)
+        """[pre-BP edge-iterations, GDG edge-iterations, pre-BP converged
+        windows, GDG windows, bulk staging waits that ran out]"""
+        out = np.zeros(5, np.int64)
         _check(lib().qd_decoder_counters(self.h, _ptr(out)))
         return out
 

@@ -142,6 +142,7 @@ def _pipeline(key, R, p, params, n, seed, trace_windows=(), mode=0, weights=None
     gfail = _u32(fail)
     assert (_u32(pred) == opred).all()
     assert (gfail == ofail).all()
+    assert dec.counters()[4] == 0  # every bulk (TMA) staging copy completed
     return ofail, gfail
 
 
