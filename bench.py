@@ -58,6 +58,8 @@ def parse():
                     help="Adam steps of the decimation ranker (0: skip)")
     ap.add_argument("--paper-shots", type=int, default=20000,
                     help="shots of the paper-preset (Fig. 2 tree) measurement (0: skip)")
+    ap.add_argument("--capacity-shots", type=int, default=20000,
+                    help="shots of each appendix code-capacity measurement (0: skip)")
     ap.add_argument("--batch-shots", type=int, default=30000,
                     help="shots per code of the batched uneven workload (0: skip)")
     ap.add_argument("--ranker-shots", type=int, default=4096,
@@ -333,6 +335,42 @@ def paper_tree(args, torch, qdec, CODES, preset, latency_fn):
                               "wilson95": [per_round(lo), per_round(hi)]}}
 
 
+def code_capacity(args, torch, qdec, CODES):
+    """Appendix workloads on [[288,12,18]]: BSC(p_d) decoded with H_X, and
+    [H_X | I] with syndrome noise p_s (the appendix's decoder: alpha 0.625,
+    low-error mode, D_max 40, depth-5 tree, side branches to D_split 20)."""
+    from paper_2403_18901_gb300.workloads import CAPACITY
+    out = []
+    n = args.capacity_shots
+    for pd, ps in [(0.04, 0.0), (0.04, 1e-3)]:
+        dem = qdec.Dem(CODES["288"], 0, 0, capacity=(pd, ps))
+        dec = qdec.Decoder(dem, dict(CAPACITY), max_shots=n)
+        det, obs = dem.sample(args.seed + 288, 0, n)
+        work = torch.empty_like(det)
+        pred = torch.empty(n, dtype=torch.int32, device="cuda")
+        fail = torch.empty(n, dtype=torch.int32, device="cuda")
+        nf = torch.zeros(1, dtype=torch.int64, device="cuda")
+        work.copy_(det)
+        dec.decode_all(work, obs, n, pred, fail, nf)  # warm-up
+        work.copy_(det)
+        nf.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dec.decode_all(work, obs, n, pred, fail, nf)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1000.0
+        f = int(nf.item())
+        lo, hi = wilson(f, n)
+        r = {"code": "[[288,12,18]]", "p_data": pd, "p_synd": ps, "shots": n, "shots_per_s": n / t,
+             "failures": f, "p_fail": f / n, "wilson95": [lo, hi]}
+        if ps > 0:
+            r["lower_bound_terms_864_2592"] = 864 * ps * ps + 2592 * pd * ps * ps
+        out.append(r)
+    return out
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -590,6 +628,7 @@ def main():
                            "p_L": per_round(ranked["failures"] / (B * args.steps)),
                            "wilson95": [per_round(rlo), per_round(rhi)]}}
 
+        capacity = code_capacity(args, torch, qdec, CODES) if args.capacity_shots > 0 else None
         paper = None
         if args.paper_shots > 0:
             paper = paper_tree(args, torch, qdec, CODES, preset, latency)
@@ -634,6 +673,7 @@ def main():
             "ranker": ranked,
             "batched_uneven": batched,
             "paper_tree": paper,
+            "code_capacity": capacity,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
