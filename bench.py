@@ -58,6 +58,8 @@ def parse():
                     help="Adam steps of the decimation ranker (0: skip)")
     ap.add_argument("--paper-shots", type=int, default=20000,
                     help="shots of the paper-preset (Fig. 2 tree) measurement (0: skip)")
+    ap.add_argument("--sweep-shots", type=int, default=100000,
+                    help="shots per physical error rate of the [[144]] LER sweep (0: skip)")
     ap.add_argument("--capacity-shots", type=int, default=20000,
                     help="shots of each appendix code-capacity measurement (0: skip)")
     ap.add_argument("--batch-shots", type=int, default=30000,
@@ -333,6 +335,39 @@ def paper_tree(args, torch, qdec, CODES, preset, latency_fn):
             "latency_ms": {"p50": p50, "p99": p99, "windows": nl},
             "ler_per_round": {"failures": f, "shots": n, "p_L": per_round(f / n),
                               "wilson95": [per_round(lo), per_round(hi)]}}
+
+
+def ler_sweep(args, torch, qdec, CODES, preset):
+    """[[144,12,12]], 12 rounds, (3,1) windows, k = 4, configured preset: LER per
+    round at p = 0.001 .. 0.004 (seeds 144_00{1..4}), shots decoded in batches
+    with the whole pass on the GPU; windows/s of each point."""
+    from paper_2403_18901_gb300.workloads import SWEEP_144
+    out = []
+    B = min(args.shots, args.sweep_shots)
+    for w in SWEEP_144:
+        p = w["p"]
+        dem = qdec.Dem(CODES[CODE_KEY], p, ROUNDS)
+        dec = qdec.Decoder(dem, preset("configured", k_guess=K_GUESS, p=p), max_shots=B)
+        pred = torch.empty(B, dtype=torch.int32, device="cuda")
+        fail = torch.empty(B, dtype=torch.int32, device="cuda")
+        nf = torch.zeros(1, dtype=torch.int64, device="cuda")
+        n_done, t = 0, 0.0
+        while n_done < args.sweep_shots:
+            n = min(B, args.sweep_shots - n_done)
+            det, obs = dem.sample(w["seed"], n_done, n)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            dec.decode_all(det, obs, n, pred, fail, nf)
+            e1.record()
+            torch.cuda.synchronize()
+            t += e0.elapsed_time(e1) / 1000.0
+            n_done += n
+        f = int(nf.item())
+        lo, hi = wilson(f, n_done)
+        out.append({"p": p, "shots": n_done, "failures": f, "p_L": per_round(f / n_done),
+                    "wilson95": [per_round(lo), per_round(hi)], "windows_per_s": n_done * dec.n_windows / t,
+                    "low_error_mode": p <= 0.002})
+    return out
 
 
 def code_capacity(args, torch, qdec, CODES):
@@ -629,6 +664,7 @@ def main():
                            "wilson95": [per_round(rlo), per_round(rhi)]}}
 
         capacity = code_capacity(args, torch, qdec, CODES) if args.capacity_shots > 0 else None
+        sweep = ler_sweep(args, torch, qdec, CODES, preset) if args.sweep_shots > 0 else None
         paper = None
         if args.paper_shots > 0:
             paper = paper_tree(args, torch, qdec, CODES, preset, latency)
@@ -674,6 +710,7 @@ def main():
             "batched_uneven": batched,
             "paper_tree": paper,
             "code_capacity": capacity,
+            "ler_sweep_144": sweep,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

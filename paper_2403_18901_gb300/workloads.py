@@ -66,3 +66,6 @@ WORKLOADS = {
     "bb144_r12_p3e-3": dict(code="144", rounds=12, p=0.003, k_guess=4, shots=100_000,
                             seed=144_003),
 }
+# [[144,12,12]], 12 rounds, (3,1) windows, k = 4: the physical error rates of
+# the LER sweep, 1e5 shots each, seeds 144_00{1..4}
+SWEEP_144 = [dict(p=p, seed=144_000 + i, shots=100_000) for i, p in enumerate((0.001, 0.002, 0.003, 0.004), 1)]

@@ -298,3 +298,19 @@ def test_code_capacity_bit_exact(key, pd, ps, mode):
     from paper_2403_18901_gb300.workloads import CAPACITY
     _pipeline(key, 0, pd, dict(CAPACITY), n=64 if mode == 1 else 24, seed=288_100, trace_windows=(0,), mode=mode,
               capacity=(pd, ps))
+
+
+def test_bb72_2000_shots_bit_exact():
+    """[[72,12,6]], 6 rounds, p = 0.003, 2000 seeded shots (seed 72003):
+    corrections of every window, committed syndromes, predictions and failures."""
+    from paper_2403_18901_gb300.workloads import WORKLOADS
+    w = WORKLOADS["bb72_r6_p3e-3"]
+    _pipeline(w["code"], w["rounds"], w["p"], preset("configured", k_guess=w["k_guess"], p=w["p"]), n=w["shots"],
+              seed=w["seed"])
+
+
+@pytest.mark.parametrize("p,seed", [(0.002, 144_002), (0.003, 144_003)])
+def test_bb144_2000_shot_subset_bit_exact(p, seed):
+    """[[144,12,12]], 12 rounds, k = 4: the 2000-shot subset of the LER sweep,
+    every window's corrections, committed syndromes, predictions, failures."""
+    _pipeline("144", 12, p, preset("configured", k_guess=4, p=p), n=2000, seed=seed, mode=1)
