@@ -356,14 +356,14 @@ struct Slot {
   int8_t* status;
   CNState* cns;
   int* deg;
-  uint32_t *sp, *par, *unsat;
+  uint32_t *sp, *unsat;
   int8_t* hq;  // ranker only: the last four posteriors as round(2 clamp(x, 63.5)), oldest first
 };
 
 __device__ __forceinline__ Slot make_slot(char* base, const Layout& L) {
   return Slot{(float*)(base + L.b_post),   (float*)(base + L.b_acc),     (uint8_t*)(base + L.b_hfl),
               (uint8_t*)(base + L.b_sign), (int8_t*)(base + L.b_status), (CNState*)(base + L.b_cns),
-              (int*)(base + L.b_deg),      (uint32_t*)(base + L.b_sp),   (uint32_t*)(base + L.b_par),
+              (int*)(base + L.b_deg),      (uint32_t*)(base + L.b_sp),
               (uint32_t*)(base + L.b_unsat), (int8_t*)(base + L.b_hq)};
 }
 
@@ -569,6 +569,41 @@ __device__ void dump_candidates(const KParams& P, const ShortG& G, const Slot& B
   }
 }
 
+// Eq. (5): the summed priors of the path's estimate (decimated values and the
+// hard decisions of the active VNs), in FP64 (exact: every prior lies in
+// (2^-15, 16), so every partial sum is exact in any order).
+template <class Grp>
+__device__ double path_metric(const ShortG& G, const Slot& B, const Grp& g) {
+  double s = 0.0;
+  for (int k = g.rank; k < G.ns; k += g.size) {
+    const int st8 = B.status[k];
+    if (st8 == 1 || (st8 == -1 && B.post[k] <= 0.0f)) s += (double)G.llr[k];
+  }
+  return g.sum_d(s);
+}
+
+// H e = s for the current decisions (Eq. (4), decimated VNs through s'):
+// writes every check's unsatisfied bit to B.unsat and returns whether any is
+// unsatisfied.  Checks in natural order, one per lane.
+template <class Grp>
+__device__ bool parity_pass(const ShortG& G, const Slot& B, const Grp& g) {
+  bool any = false;
+  for (int base = 0; base < G.nr; base += g.size) {
+    const int j = base + g.rank;
+    bool u = false;
+    if (j < G.nr) {
+      uint32_t hp = bit_of(B.sp, j);
+      for (int q = G.rowptr[j]; q < G.rowptr[j + 1]; ++q) hp ^= B.post[G.rowent[q] >> 16] <= 0.0f;  // NaN: decimated
+      u = hp != 0u;
+    }
+    const unsigned m = __ballot_sync(FULL, u);
+    const int w0 = base + (g.rank & ~31);
+    if ((g.rank & 31) == 0 && w0 < G.nr) B.unsat[w0 >> 5] = m;
+    any |= u;
+  }
+  return g.any(any);
+}
+
 struct PathOut {
   int* status;
   double* pm;
@@ -623,22 +658,28 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
     depth = D;
     PA = main_rules(D) ? P.pa_main : P.pa_other;  // read by this step's history flags
     for (int it = 1; it <= P.ips; ++it) {
-      uint32_t* par = B.par + (iters & 1) * rw;
-      for (int x = R; x < rw; x += S) par[x] = 0;
       // ---- check-node update, Eq. (1), over active VNs; tpc lanes per check ----
-      // checks in descending static degree, so the lanes of a round loop alike
+      // checks in descending static degree, so the lanes of a round loop alike.
+      // Each check also takes the parity of its active VNs' hard decisions
+      // (Eq. (4)) from the posteriors it reads: for it >= 2 this pass is the
+      // convergence test H e = s of the previous iteration (Sec. II-A).
+      bool unsat = false;
       for (int j0 = R / tpc; j0 < nr_rounds; j0 += S / tpc) {
         const int j = G.cperm[j0 < nr ? j0 : nr - 1];
         const int d = j0 < nr ? B.deg[j] : 0;
-        if (tpc == 1 && d == 0) continue;  // no shuffle partner waits for this lane
+        if (tpc == 1 && d == 0) {  // no shuffle partner waits for this lane
+          if (j0 < nr) unsat |= bit_of(B.sp, j) != 0u;
+          continue;
+        }
         const CNState oc = B.cns[j];
         float m1 = CUDART_INF_F, m2 = CUDART_INF_F;
         int am = 0xFFFF;
-        uint32_t neg = 0;
+        uint32_t neg = 0, hp = 0;
         // one row entry; the (min1, min2) pair and so every message do not
         // depend on the order in which a check sees its inputs
         auto take = [&](uint32_t ent, float pv, uint32_t sg) {
           if (pv != pv) return;  // stale message of a decimated VN
+          hp ^= pv <= 0.0f;
           const int e = (int)(ent & 0xFFFFu);
           ++visits;
           const float wprev = LW ? edge_weight(G.wts, G.wT, G.wE, P.alpha, iters, G.efull[e]) : P.alpha;
@@ -664,11 +705,19 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
           take(e0, p0, s0);
           if (two) take(e1, p1, s1);
         }
-        if (tpc > 1) group_min2(m1, m2, am, neg, tpc);
+        if (tpc > 1) {
+          group_min2(m1, m2, am, neg, tpc);
+          for (int off = tpc >> 1; off; off >>= 1) hp ^= __shfl_xor_sync(FULL, hp, off);
+        }
+        if (sub == 0 && j0 < nr) unsat |= (hp ^ bit_of(B.sp, j)) != 0u;
         if (sub == 0 && d > 0)
           B.cns[j] = cn_store<LW>(P.alpha, P.clip, m1, m2, am, neg ^ bit_of(B.sp, j), d == 1, oc.pad);
       }
-      g.sync();
+      if (!g.any(unsat) && it >= 2) {  // the previous iteration's decisions satisfy H e = s
+        status = BR_CONVERGED;
+        pm = path_metric(G, B, g);
+        goto done;
+      }
       // ---- variable-node update, Eq. (2)-(3); history of Sec. IV-A ----
       const bool hist = it > P.ips - 4;
       const bool hist0 = it == P.ips - 3;
@@ -702,35 +751,21 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
             B.hfl[k] &= f;
           }
         }
-        if (p <= 0.0f)
-          for (int e = G.colptr[k]; e < ee; ++e) {
-            const int j = G.colrows[e];
-            atomicXor(&par[j >> 5], 1u << (j & 31));
-          }
       }
       g.sync();
       ++iters;
       first = false;
-      bool ok = true;
-      for (int x = R; x < rw; x += S) ok &= (par[x] == B.sp[x]);
-      if (g.all(ok)) {
-        status = BR_CONVERGED;
-        double s = 0.0;
-        for (int k = R; k < ns; k += S) {
-          const int st8 = B.status[k];
-          if (st8 == 1 || (st8 == -1 && B.post[k] <= 0.0f)) s += (double)G.llr[k];
-        }
-        pm = g.sum_d(s);
-        goto done;
-      }
+    }
+    // the step's last iteration: its own convergence test, which also leaves
+    // the unsatisfied-check words for Alg. 3 and the ranker
+    if (!parity_pass(G, B, g)) {
+      status = BR_CONVERGED;
+      pm = path_metric(G, B, g);
+      goto done;
     }
     if (D == dmax) break;  // no decimation after the last BP step
     {
       // ---- SELECT-VN (Alg. 1) with AGG-DEC (Alg. 3) ----
-      const uint32_t* lastpar = B.par + ((iters - 1) & 1) * rw;
-      if (!P.low_err || P.rkq || P.dump)
-        for (int x = R; x < rw; x += S) B.unsat[x] = lastpar[x] ^ B.sp[x];
-      g.sync();
       const float PBd = (D == 1) ? P.pb_d1 : (main_rules(D) ? P.pb_main : P.pb_other);
       float bL = CUDART_INF_F, tL = CUDART_INF_F;
       int bk = kNone, tk = kNone, nagg = 0;
@@ -972,16 +1007,18 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
     for (int x = 0; x < L.rw; ++x) ok &= (pb[x] == sbits[x]);
     conv = ok;
   }
+  int t_conv = 0;
   for (t = 1; t <= P.n_pre; ++t) {
-    uint32_t* pb = parb + (t & 1) * L.rw;
-    for (int x = tid; x < L.rw; x += NT) pb[x] = 0;
+    // check nodes; each check also takes the parity of the hard decisions it
+    // reads, so for t >= 2 the pass is the convergence test of iteration t-1
+    bool unsat = false;
     for (int j0 = tid / tpc_pre; j0 < nr_rounds; j0 += NT / tpc_pre) {
       const int j = j0 < nr ? j0 : nr - 1;
       const int beg = Wg.row_ptr[j], end = j0 < nr ? Wg.row_ptr[j + 1] : beg;
       const CNState oc = cns[j];
       float m1 = CUDART_INF_F, m2 = CUDART_INF_F;
       int am = 0xFFFF;
-      uint32_t neg = 0;
+      uint32_t neg = 0, hp = 0;
       for (int q = beg + 4 * sub_pre; q < end; q += 4 * tpc_pre) {
         uint32_t ent[4];
         float pv[4];
@@ -998,6 +1035,7 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
         for (int u = 0; u < 4; ++u) {
           if (q + u >= end) break;
           const int e = (int)(ent[u] & 0xFFFFu);
+          hp ^= pv[u] <= 0.0f;
           const float wprev = (LW && t > 1) ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t - 1, e) : P.alpha;
           const float v = (t == 1) ? pv[u] : clipf(__fsub_rn(pv[u], c2v<LW>(wprev, P.clip, oc, e, sg[u])), P.clip);
           const float a = fabsf(v);
@@ -1013,11 +1051,20 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
           sign[e] = (uint8_t)sgn;
         }
       }
-      if (tpc_pre > 1) group_min2(m1, m2, am, neg, tpc_pre);
-      if (sub_pre == 0 && j0 < nr)
+      if (tpc_pre > 1) {
+        group_min2(m1, m2, am, neg, tpc_pre);
+        for (int off = tpc_pre >> 1; off; off >>= 1) hp ^= __shfl_xor_sync(FULL, hp, off);
+      }
+      if (sub_pre == 0 && j0 < nr) {
         cns[j] = cn_store<LW>(P.alpha, P.clip, m1, m2, am, neg ^ bit_of(sbits, j), end - beg == 1, 0u);
+        unsat |= (hp ^ bit_of(sbits, j)) != 0u;
+      }
     }
-    __syncthreads();
+    if (!__syncthreads_or(unsat) && t >= 2) {  // iteration t-1 satisfies H e = s
+      conv = true;
+      t_conv = t - 1;
+      break;
+    }
     const bool kacc = t >= tk0;
     for (int i0 = tid; i0 < nc; i0 += NT) {
       const int i = Wg.vperm[i0];  // descending degree: the lanes of a round loop alike
@@ -1051,20 +1098,22 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
         }
         key[i] = kv;
       }
-      if (p <= 0.0f)
-        for (int e = eb; e < ee; ++e) {
-          const int j = Wg.col_rows[e];
-          atomicXor(&pb[j >> 5], 1u << (j & 31));
-        }
     }
     __syncthreads();
-    bool ok = true;
-    for (int x = 0; x < L.rw; ++x) ok &= (pb[x] == sbits[x]);
-    if (ok) {
+  }
+  if (!conv && P.n_pre > 0) {  // the convergence test of the last iteration
+    bool unsat = false;
+    for (int j = tid; j < nr; j += NT) {
+      uint32_t hp = bit_of(sbits, j);
+      for (int q = Wg.row_ptr[j]; q < Wg.row_ptr[j + 1]; ++q) hp ^= post[Wg.row_ent[q] >> 16] <= 0.0f;
+      unsat |= hp != 0u;
+    }
+    if (!__syncthreads_or(unsat)) {
       conv = true;
-      break;
+      t_conv = P.n_pre;
     }
   }
+  if (conv && P.n_pre > 0) t = t_conv;
   *t_run_out = conv ? (P.n_pre == 0 ? 0 : t) : P.n_pre;
   if (conv) {
     for (int base = warp * 32; base < nc; base += NT) {

@@ -121,7 +121,7 @@ struct Layout {
   // (from p_sort on; overwritten by the sort that follows); pre_stage = 0: none
   unsigned pre_stage, q_colptr, q_colrows, q_rowptr, q_rowent, q_llr, q_vperm;
   // one path slot (relative to the slot base)
-  unsigned b_post, b_acc, b_hfl, b_status, b_sign, b_cns, b_deg, b_sp, b_par, b_unsat, b_hq, b_size;
+  unsigned b_post, b_acc, b_hfl, b_status, b_sign, b_cns, b_deg, b_sp, b_unsat, b_hq, b_size;
   unsigned total;
   int rw, cw, sw, sortn, nslots;
 };
@@ -184,7 +184,6 @@ __host__ __device__ inline Layout make_layout(int nr, int nc, int ne, int ns, in
   L.b_cns = b; b = al16(b + 16u * nr);
   L.b_deg = b; b = al16(b + 4u * nr);
   L.b_sp = b; b = al16(b + 4u * L.rw);
-  L.b_par = b; b = al16(b + 8u * L.rw);
   L.b_unsat = b; b = al16(b + 4u * L.rw);
   L.b_hq = b; b = al16(b + (ranker ? 4u * ns : 0u));
   L.b_size = b;
