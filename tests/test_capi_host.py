@@ -90,3 +90,31 @@ def test_every_single_fault_is_a_dem_column(lib):
                 assert (dets, obs) in cols
                 n += 1
     assert n > 1000
+
+
+def test_parameter_validation_without_a_gpu(lib):
+    """Checks that fail before any device call, so they run on the host."""
+    from paper_2403_18901_gb300.workloads import preset
+    d = qdec.Dem(CODES["72"], 0.003, 6)
+    bad = [dict(preset("paper", k_guess=4), side_max=2),          # side branches start at k
+           dict(preset("configured", k_guess=3), F=4),            # F > W
+           dict(preset("configured", k_guess=3), iters_per_step=0),
+           dict(preset("configured", k_guess=3), alpha=0.0),
+           dict(preset("configured", k_guess=3), d_max_other=1)]  # d_max_other < k
+    for params in bad:
+        with pytest.raises(qdec.QdError) as e:
+            qdec.Decoder(d, params, max_shots=4)
+        assert e.value.code == qdec.QD_EINVAL, params
+    with pytest.raises(qdec.QdError) as e:
+        qdec.Dem(CODES["288"], 0, 0, capacity=(0.6, 0.0))
+    assert e.value.code == qdec.QD_EINVAL
+    with pytest.raises(qdec.QdError) as e:
+        qdec.Dem(CODES["288"], 0, 0, capacity=(0.04, -1e-3))
+    assert e.value.code == qdec.QD_EINVAL
+    # a prior outside (2^-15, 16) would make Eq. (5) inexact
+    with pytest.raises(qdec.QdError) as e:
+        qdec.Dem(CODES["288"], 0, 0, capacity=(0.04, 1e-9))
+    assert e.value.code == qdec.QD_EUNSUPPORTED
+    h = ctypes.c_void_p()
+    assert lib.qd_batch_create((ctypes.c_void_p * 1)(), 0, ctypes.byref(h)) == qdec.QD_EINVAL
+    assert lib.qd_ranker_eval(None, None, None, 0, 0, 1.0, 1.0, None, None, None, None) == qdec.QD_EINVAL
