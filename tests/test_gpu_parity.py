@@ -314,3 +314,12 @@ def test_bb144_2000_shot_subset_bit_exact(p, seed):
     """[[144,12,12]], 12 rounds, k = 4: the 2000-shot subset of the LER sweep,
     every window's corrections, committed syndromes, predictions, failures."""
     _pipeline("144", 12, p, preset("configured", k_guess=4, p=p), n=2000, seed=seed, mode=1)
+
+
+def test_other_window_shapes_of_the_paper():
+    """Sec. IV-C: (5,2) windows for [[144,12,12]] and (4,1) windows for
+    [[288,12,18]] with the paper's decision tree for that code."""
+    _pipeline("144", 6, 0.003, preset("paper", k_guess=4, W=5, F=2), n=40, seed=144_052, trace_windows=(0, 1),
+              mode=1)
+    p288 = preset("paper", 5, p=0.002, d_max_main=40, d_max_other=25, side_max=20, n_pre=16, W=4, F=1)
+    _pipeline("288", 4, 0.003, p288, n=12, seed=288_041, trace_windows=(0, 1), mode=1)
