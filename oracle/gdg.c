@@ -497,10 +497,28 @@ static int side_split(const qdo_params* P, int id) {
   return 0;
 }
 
+/*
+ * READING (reinit_on_split = 1, the appendix's multi-thread implementation):
+ * a path that continues from another path's status snapshot starts its BP
+ * messages afresh there -- a side branch at D_split, and the second branch of
+ * each neighbouring pair of tree branches (odd id, contrary at D = k).  Right
+ * after that decimation (and its peeling) mu_{i->j} = Lambda_i for every
+ * active VN, and the iteration count of the learned weights restarts.
+ * Returns 0 for paths that never restart.
+ */
+static int reinit_depth(const qdo_params* P, int id, int split) {
+  if (!P->reinit_on_split) return 0;
+  if (split) return split;
+  if (id >= 1 && (id & 1) && P->k_guess >= 1) return P->k_guess;
+  return 0;
+}
+
 /* One decision path of Alg. 2 on graph g (the shortened window). */
 static void run_branch(const graph_t* g, const uint8_t* synd, const qdo_params* P, int id,
                        state_t* s, qdo_branch_summary* out, qdo_step_record* steps) {
   const int split = side_split(P, id);
+  const int d_reinit = reinit_depth(P, id, split);
+  int tw = 0; /* iterations since the messages were (re)initialised */
   int dmax = id == 0 ? P->d_max_main : (split ? split + (P->d_max_other - P->k_guess) : P->d_max_other);
   state_reset(s, g, synd);
   out->status = BR_MAXDEPTH;
@@ -514,7 +532,7 @@ static void run_branch(const graph_t* g, const uint8_t* synd, const qdo_params* 
   for (int D = 1; D <= dmax; ++D) {
     out->depth = D;
     for (int it = 0; it < P->iters_per_step; ++it) {
-      bp_iteration(g, s, P->alpha, P->clip, out->iters + 1);
+      bp_iteration(g, s, P->alpha, P->clip, ++tw);
       out->iters++;
       if (converged(g, s)) {
         out->status = BR_CONVERGED;
@@ -545,6 +563,11 @@ static void run_branch(const graph_t* g, const uint8_t* synd, const qdo_params* 
     if (np < 0) {
       out->status = BR_CONTRADICTION;
       return;
+    }
+    if (D == d_reinit) {
+      for (int e = 0; e < g->ne; ++e)
+        if (s->status[g->edge_col[e]] == -1) s->v2c[e] = g->llr[g->edge_col[e]];
+      tw = 0;
     }
   }
 }

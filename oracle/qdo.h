@@ -46,6 +46,8 @@ typedef struct {
   int n_unsat_min;       /* unsatisfied-neighbour count of Alg. 3 (3)          */
   int side_max;          /* side branches of Fig. 2 split off the main branch  */
                          /* at D_split = k .. side_max (0: the 2^k tree only) */
+  int reinit_on_split;   /* 1: a path restarts its messages where it splits    */
+                         /* off another (appendix, multi-thread snapshots)     */
   /* Learned weighted min-sum (no counterpart in the paper; alpha of Eq. (1)
    * replaced by w[t][e]): wts[k] is window k's array [wT][n_edges] over the
    * full-window edges (CSC order), or NULL for plain alpha.  Iteration t

@@ -84,3 +84,40 @@ def test_side_branches_follow_the_main_branch_until_their_split(key, R, k, p):
             if m_depth < split:  # the main branch ended first: the side branch is the main branch
                 assert tr["branches"][b] == tr["branches"][0]
     assert seen_split > 0, "no side branch reached its split; pick another seed"
+
+
+@pytest.mark.parametrize("key,R,k,p", [("72", 6, 3, 0.004), ("144", 12, 4, 0.004)])
+def test_message_restart_at_splits(key, R, k, p):
+    """reinit_on_split (the appendix's snapshot implementation): only the
+    paths that continue from another path's status -- side branches at their
+    split, odd tree ids at D = k -- change, and only after that decimation."""
+    o = oracle_dem(key, p, R)
+    params = preset("paper", k_guess=k, p=p)
+    re_params = dict(params, reinit_on_split=1)
+    nt = 1 << k
+    restarts = {1: k}
+    restarts.update({nt + i: k + 1 + i for i in range(params["side_max"] - k)})
+    restarts.update({b: k for b in range(3, nt, 2)})
+    changed = 0
+    for s in _window_syndromes(o, params, 1, 40, seed=991 + k):
+        _, info, tr = o.decode_window(params, 1, s, trace=True)
+        if info["prebp_converged"]:
+            continue
+        _, _, tr1 = o.decode_window(re_params, 1, s, trace=True)
+        for b in range(len(tr["branches"])):
+            if b not in restarts:
+                assert tr1["branches"][b] == tr["branches"][b] and tr1["steps"][b] == tr["steps"][b], b
+                continue
+            D = restarts[b]
+            assert tr1["steps"][b][:D] == tr["steps"][b][:D], b  # identical through the split decimation
+            changed += tr1["steps"][b][D:] != tr["steps"][b][D:]
+    assert changed > 0, "no restart changed a path; pick another seed"
+
+
+def test_message_restart_without_splits_changes_nothing():
+    o = oracle_dem("72", 0.004, 6)
+    params = preset("paper", k_guess=0, p=0.004, side_max=0)
+    for s in _window_syndromes(o, params, 1, 10, seed=5):
+        a = o.decode_window(params, 1, s, trace=True)
+        b = o.decode_window(dict(params, reinit_on_split=1), 1, s, trace=True)
+        assert (a[0] == b[0]).all() and a[2]["branches"] == b[2]["branches"]
