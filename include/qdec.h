@@ -82,6 +82,10 @@ typedef struct {
                          /* (d_max_other - k) steps; 0: the 2^k tree only.       */
                          /* With side branches id 1 (contrary only at D = k) is  */
                          /* the D_split = k side branch; ids 2^k.. the others.   */
+  int reinit_on_split;   /* 1: a path that continues from another's status (side  */
+                         /* branches at D_split, odd tree ids at D = k) restarts  */
+                         /* its messages there, mu = Lambda (the appendix's       */
+                         /* multi-thread snapshots); 0: continuous messages.      */
 } qd_gdg_params;
 
 typedef struct qd_dem qd_dem;

@@ -628,6 +628,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
   // Fig. 2: main branch (id 0), tree branches, side branches (split > 0),
   // which keep the main-branch thresholds up to and including their split
   const int split = path_split(P, id);
+  const int d_reinit = path_reinit(P, id, split);
   const int dmax = id == 0 ? P.dmax_main : (split ? split + (P.dmax_other - P.k) : P.dmax_other);
   auto main_rules = [&](int D) { return id == 0 || (split && D <= split); };
   float PA = main_rules(1) ? P.pa_main : P.pa_other;
@@ -644,6 +645,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
     for (int q = R; q < dmx; q += S) out.st[q] = StepTrace{-2, -1, 0, 0, 0};
   g.sync();
   int status = BR_MAXDEPTH, depth = 0, iters = 0;
+  int tw = 0;  // iterations since the messages were (re)initialised (learned weights)
   long long visits = 0;
   double pm = CUDART_INF;
   bool first = true;
@@ -682,7 +684,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
           hp ^= pv <= 0.0f;
           const int e = (int)(ent & 0xFFFFu);
           ++visits;
-          const float wprev = LW ? edge_weight(G.wts, G.wT, G.wE, P.alpha, iters, G.efull[e]) : P.alpha;
+          const float wprev = LW ? edge_weight(G.wts, G.wT, G.wE, P.alpha, tw, G.efull[e]) : P.alpha;
           const float v = first ? pv : clipf(__fsub_rn(pv, c2v<LW>(wprev, P.clip, oc, e, sg)), P.clip);
           const float a = fabsf(v);
           if (a < m1) {
@@ -728,7 +730,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
         float p = G.llr[k];
         const int eb = G.colptr[k], ee = G.colptr[k + 1];
         auto msg = [&](int e) {
-          const float wt = LW ? edge_weight(G.wts, G.wT, G.wE, P.alpha, iters + 1, G.efull[e]) : P.alpha;
+          const float wt = LW ? edge_weight(G.wts, G.wT, G.wE, P.alpha, tw + 1, G.efull[e]) : P.alpha;
           return c2v<LW>(wt, P.clip, B.cns[G.colrows[e]], e, B.sign[e]);
         };
         // ascending check order (Eq. (2)); most short columns have degree 1 or 2
@@ -754,6 +756,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
       }
       g.sync();
       ++iters;
+      ++tw;
       first = false;
     }
     // the step's last iteration: its own convergence test, which also leaves
@@ -835,6 +838,13 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
       if (np < 0) {
         status = np == -1 ? BR_CONTRADICTION : BR_INTERNAL;
         goto done;
+      }
+      if (D == d_reinit) {  // mu_{i->j} = Lambda_i again: the next pass reads the priors
+        for (int k = R; k < ns; k += S)
+          if (B.status[k] == -1) B.post[k] = G.llr[k];
+        tw = 0;
+        first = true;
+        g.sync();
       }
     }
   }

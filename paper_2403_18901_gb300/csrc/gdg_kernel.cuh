@@ -22,6 +22,7 @@ struct KParams {
   int n_pre, ips, dmax_main, dmax_other, k, low_err, peel_init, pc_max_depth, n_unsat_min;
   int nb;        // decision paths: 2^k tree + side branches
   int side_max;  // side branches split off the main branch at D_split = k .. side_max (0: none)
+  int reinit;    // 1: a path continuing from another's snapshot restarts its messages there
   // learned decimation ranker (NULL: the argmin of Alg. 1): rkq = the
   // grid-rounded W1[64][8], b1[64], W2[64], b2; rkb[t][lane] = the BF16 pair
   // (W1[8t + lane/4][2 (lane%4)], W1[8t + lane/4][2 (lane%4) + 1]), the B
@@ -51,6 +52,14 @@ __host__ __device__ inline int path_split(const KParams& P, int id) {
   const int nt = 1 << P.k;
   if (id >= nt) return P.k + 1 + (id - nt);
   return (id == 1 && P.k >= 1) ? P.k : 0;
+}
+
+// Depth after whose decimation path `id` restarts its messages (reinit
+// reading: side branches at their split, odd tree ids at D = k); 0: never.
+__host__ __device__ inline int path_reinit(const KParams& P, int id, int split) {
+  if (!P.reinit) return 0;
+  if (split) return split;
+  return (id >= 1 && (id & 1) && P.k >= 1) ? P.k : 0;
 }
 
 // Shot-mode queue order: the main branch, side branches from the deepest

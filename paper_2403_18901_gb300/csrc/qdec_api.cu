@@ -338,6 +338,7 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
   k.pc_max_depth = p->pc_max_depth;
   k.n_unsat_min = p->n_unsat_min;
   k.side_max = p->side_max;
+  k.reinit = p->reinit_on_split != 0;
   k.nb = (1 << p->k_guess) + (p->side_max > p->k_guess ? p->side_max - p->k_guess : 0);
   dec->dmx = std::max(p->d_max_main, p->d_max_other);
   if (p->side_max > 0) dec->dmx = std::max(dec->dmx, p->side_max + p->d_max_other - p->k_guess);

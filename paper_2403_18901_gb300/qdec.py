@@ -39,7 +39,8 @@ class GdgParams(C.Structure):
                 ("shorten", C.c_int), ("clip", C.c_float), ("pa_main", C.c_float),
                 ("pa_other", C.c_float), ("pb_main", C.c_float), ("pb_other", C.c_float),
                 ("pb_d1", C.c_float), ("pc", C.c_float), ("pd", C.c_float),
-                ("pc_max_depth", C.c_int), ("n_unsat_min", C.c_int), ("side_max", C.c_int)]
+                ("pc_max_depth", C.c_int), ("n_unsat_min", C.c_int), ("side_max", C.c_int),
+                ("reinit_on_split", C.c_int)]
 
 
 class DemInfo(C.Structure):
@@ -154,7 +155,7 @@ def make_code(code):
 def make_params(p):
     q = GdgParams()
     for name, _ in GdgParams._fields_:
-        setattr(q, name, p.get(name, 0) if name == "side_max" else p[name])
+        setattr(q, name, p.get(name, 0) if name in ("side_max", "reinit_on_split") else p[name])
     return q
 
 

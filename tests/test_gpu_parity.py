@@ -323,3 +323,21 @@ def test_other_window_shapes_of_the_paper():
               mode=1)
     p288 = preset("paper", 5, p=0.002, d_max_main=40, d_max_other=25, side_max=20, n_pre=16, W=4, F=1)
     _pipeline("288", 4, 0.003, p288, n=12, seed=288_041, trace_windows=(0, 1), mode=1)
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_message_restart_at_splits_bit_exact(mode):
+    """reinit_on_split: side branches and odd tree ids restart their messages
+    where they split off (the appendix's snapshot implementation)."""
+    params = preset("paper", k_guess=4, p=0.004, reinit_on_split=1)
+    _pipeline("144", 12, 0.004, params, n=40 if mode == 1 else 20, seed=144_555, trace_windows=(1, 5), mode=mode)
+
+
+def test_message_restart_with_learned_weights_bit_exact():
+    """The learned weights' iteration count restarts with the messages."""
+    params = preset("configured", k_guess=3, p=0.003, reinit_on_split=1)
+    o = oracle_dem("72", 0.003, 6)
+    rng = np.random.default_rng(9)
+    weights = {k: rng.uniform(0.45, 0.9, size=(25, o.window(3, 1, k)["n_edges"])).astype(np.float32)
+               for k in range(o.n_windows(3, 1))}
+    _pipeline("72", 6, 0.003, params, n=120, seed=7272, trace_windows=(0, 2), mode=1, weights=weights)
