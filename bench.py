@@ -329,7 +329,22 @@ def paper_tree(args, torch, qdec, CODES, preset, latency_fn):
     qdec._check(qdec.lib().qd_decoder_path_info(dec.h, qdec._ptr(pi)))
     ldec = qdec.Decoder(dem, params, max_shots=1)
     p50, p99, nl = latency_fn(ldec, det[:max(1, args.latency_shots)].clone())
+    # the appendix's snapshot variant: paths restart their messages where they split
+    rdec = qdec.Decoder(dem, dict(params, reinit_on_split=1), max_shots=n)
+    work.copy_(det)
+    nf.zero_()
+    e0.record()
+    rdec.decode_all(work, obs, n, pred, fail, nf)
+    e1.record()
+    torch.cuda.synchronize()
+    tr_ = e0.elapsed_time(e1) / 1000.0
+    fr = int(nf.item())
+    rlo, rhi = wilson(fr, n)
+    reinit = {"value": n * rdec.n_windows / tr_, "unit": "windows/s",
+              "ler_per_round": {"failures": fr, "shots": n, "p_L": per_round(fr / n),
+                                "wilson95": [per_round(rlo), per_round(rhi)]}}
     return {"preset": "paper (alpha 1.0, n_pre 8, 6 iterations/step, Fig. 2 tree)", "paths": int(pi[0]),
+            "reinit_on_split": reinit,
             "shots": n, "value": n * dec.n_windows / t, "unit": "windows/s", "seconds": t,
             "gdg_windows_frac": float(c[3]) / (n * dec.n_windows),
             "latency_ms": {"p50": p50, "p99": p99, "windows": nl},
