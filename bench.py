@@ -324,6 +324,7 @@ def paper_tree(args, torch, qdec, CODES, preset, latency_fn):
     t = e0.elapsed_time(e1) / 1000.0
     c = dec.counters()
     f = int(nf.item())
+    resid_only = int((fail == 1).sum().item())  # Eq. (11) failed, Eq. (12) held
     lo, hi = wilson(f, n)
     pi = np.zeros(2, np.int32)
     qdec._check(qdec.lib().qd_decoder_path_info(dec.h, qdec._ptr(pi)))
@@ -348,6 +349,7 @@ def paper_tree(args, torch, qdec, CODES, preset, latency_fn):
             "shots": n, "value": n * dec.n_windows / t, "unit": "windows/s", "seconds": t,
             "gdg_windows_frac": float(c[3]) / (n * dec.n_windows),
             "latency_ms": {"p50": p50, "p99": p99, "windows": nl},
+            "failures_eq11_only": resid_only,
             "ler_per_round": {"failures": f, "shots": n, "p_L": per_round(f / n),
                               "wilson95": [per_round(lo), per_round(hi)]}}
 
@@ -366,7 +368,7 @@ def ler_sweep(args, torch, qdec, CODES, preset):
         pred = torch.empty(B, dtype=torch.int32, device="cuda")
         fail = torch.empty(B, dtype=torch.int32, device="cuda")
         nf = torch.zeros(1, dtype=torch.int64, device="cuda")
-        n_done, t = 0, 0.0
+        n_done, t, resid_only = 0, 0.0, 0
         while n_done < args.sweep_shots:
             n = min(B, args.sweep_shots - n_done)
             det, obs = dem.sample(w["seed"], n_done, n)
@@ -376,10 +378,12 @@ def ler_sweep(args, torch, qdec, CODES, preset):
             e1.record()
             torch.cuda.synchronize()
             t += e0.elapsed_time(e1) / 1000.0
+            resid_only += int((fail[:n] == 1).sum().item())  # Eq. (11) failed, Eq. (12) held
             n_done += n
         f = int(nf.item())
         lo, hi = wilson(f, n_done)
         out.append({"p": p, "shots": n_done, "failures": f, "p_L": per_round(f / n_done),
+                    "failures_eq11_only": resid_only,
                     "wilson95": [per_round(lo), per_round(hi)], "windows_per_s": n_done * dec.n_windows / t,
                     "low_error_mode": p <= 0.002})
     return out

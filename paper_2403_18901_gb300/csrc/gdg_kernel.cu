@@ -158,7 +158,8 @@ __device__ void stage_pieces(Stager& st, const StagePiece* pc, int n) {
 // the learned weight w[min(t, T)][ef].
 __device__ __forceinline__ float edge_weight(const float* wts, int wT, int wE, float alpha, int t, int ef) {
   if (!wts) return alpha;
-  return wts[(size_t)((t < wT ? t : wT) - 1) * wE + ef];
+  const int row = t < 1 ? 0 : (t < wT ? t : wT) - 1;  // never a row before the first
+  return wts[(size_t)row * wE + ef];
 }
 
 // order-preserving map of a float to uint32 (-0 and +0 equal)
@@ -684,7 +685,8 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
           hp ^= pv <= 0.0f;
           const int e = (int)(ent & 0xFFFFu);
           ++visits;
-          const float wprev = LW ? edge_weight(G.wts, G.wT, G.wE, P.alpha, tw, G.efull[e]) : P.alpha;
+          // the previous iteration's multiplier, only when there was one (tw >= 1)
+          const float wprev = (LW && !first) ? edge_weight(G.wts, G.wT, G.wE, P.alpha, tw, G.efull[e]) : P.alpha;
           const float v = first ? pv : clipf(__fsub_rn(pv, c2v<LW>(wprev, P.clip, oc, e, sg)), P.clip);
           const float a = fabsf(v);
           if (a < m1) {
