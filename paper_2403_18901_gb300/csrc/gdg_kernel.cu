@@ -907,7 +907,16 @@ struct DecodeArgs {
   char* path_res;       // path mode: results [shot][path]
   int* arrive;          // path mode: per-shot arrival counters (0 between launches)
   int sw_max;
+  // windows too large for shared memory: the union region (pre-BP scratch and
+  // path slots) of CTA b lives at uglob + b * ubytes in global memory
+  // (L2-resident at these sizes) instead of after the persistent part
+  char* uglob;
+  size_t ubytes;
 };
+
+__device__ __forceinline__ char* union_base(const DecodeArgs& A, char* sm) {
+  return A.uglob ? A.uglob + (size_t)blockIdx.x * A.ubytes : sm + A.L.U;
+}
 
 // One window step of several decoders in one launch (kernel parameter).
 struct BatchArgs {
@@ -949,7 +958,7 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
   uint32_t* sbits = (uint32_t*)(sm + L.sbits);
   uint32_t* cbits = (uint32_t*)(sm + L.cbits);
   uint16_t* sel = (uint16_t*)(sm + L.sel);
-  char* U = sm + L.U;
+  char* U = union_base(A, sm);
   float* post = (float*)(U + L.p_post);
   float* key = (float*)(U + L.p_key);
   CNState* cns = (CNState*)(U + L.p_cns);
@@ -1302,7 +1311,7 @@ __device__ void shot_body(const DecodeArgs& A, long long shot, char* sm, Stager&
     // warps beyond the layout's path slots (batched launches) sit out the paths
     if (warp < L.nslots) {
       const ShortG G = short_graph(sm, L, A.W, n_short);
-      const Slot B = make_slot(sm + L.U + (size_t)warp * L.b_size, L);
+      const Slot B = make_slot(union_base(A, sm) + (size_t)warp * L.b_size, L);
       const WarpGrp g{lane};
       while (true) {
         int id = 0;
@@ -1423,7 +1432,7 @@ __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
   }
   const int n_short = A.W.n_short;
   const ShortG G = short_graph(sm, L, A.W, n_short);
-  const Slot B = make_slot(sm + L.U, L);
+  const Slot B = make_slot(union_base(A, sm), L);
   const CtaGrp g{tid, (int)blockDim.x, sm + L.red};
   const size_t rb = path_result_bytes(A.sw_max);
   char* mine = A.path_res + ((size_t)shot * nb + id) * rb;
@@ -1624,7 +1633,7 @@ cudaError_t launch_decode_batch(cudaStream_t st, int grid, int threads, size_t s
     B.seg_end[i] = end;
     B.seg[i] = dev::DecodeArgs{*x.P,   *x.W,   *x.L,     x.det,      x.det_words, x.n,      x.corr,
                                x.corr_words, nullptr, nullptr, 0,     x.dmx,    x.ns_max, nullptr,
-                               x.counters, nullptr, nullptr, x.sw_max};
+                               x.counters, nullptr, nullptr, x.sw_max, nullptr, 0};
     lw = lw || x.W->wts != nullptr;
   }
   if (lw) dev::decode_batch_kernel<true><<<grid, threads, smem, st>>>(B);
@@ -1659,9 +1668,11 @@ cudaError_t decode_occupancy(int mode, int threads, size_t smem, int* blocks) {
 cudaError_t launch_decode(int mode, int grid, int threads, size_t smem, cudaStream_t st, const KParams& P,
                           const WinDev& W, const Layout& L, const uint32_t* det, int det_words, long long n,
                           uint32_t* corr, int corr_words, int32_t* status, char* trace, size_t tr_bytes, int dmx,
-                          int ns_max, int* work, long long* counters, char* path_res, int* arrive, int sw_max) {
+                          int ns_max, int* work, long long* counters, char* path_res, int* arrive, int sw_max,
+                          char* uglob, size_t ubytes) {
   const dev::DecodeArgs A{P,     W,        L,     det,      det_words, n,     corr,     corr_words, status,
-                          trace, tr_bytes, dmx,   ns_max,   work,      counters, path_res, arrive,     sw_max};
+                          trace, tr_bytes, dmx,   ns_max,   work,      counters, path_res, arrive,     sw_max,
+                          uglob, ubytes};
   const bool lw = W.wts != nullptr;
   if (mode == 1) {
     if (lw) dev::decode_path_kernel<true><<<grid, threads, smem, st>>>(A);

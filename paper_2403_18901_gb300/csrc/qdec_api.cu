@@ -73,6 +73,12 @@ struct WinGpu {
   int grid_per_sm = 1;
   int shot_warps = kShotWarps;
   uint32_t* d_wthr = nullptr;  // window-local sampling thresholds (on first use)
+  // union region in global memory (windows too large for shared memory, or
+  // launch mode 3): layout, CTAs per SM, and whether the shared-memory
+  // layouts fit at all
+  qd::Layout Lg{};
+  int grid_g = 1;
+  bool fits = true, path_fits = true;
 };
 
 template <class T>
@@ -102,7 +108,9 @@ struct qd_decoder {
   long long max_shots = 0;
   std::vector<WinGpu> wins;
   int corr_words = 0, dmx = 0, ns_max = 0, sm_count = 0, sw_max = 0;
-  int launch_mode = 0;  // 0 automatic, 1 shot mode, 2 path mode
+  int launch_mode = 0;  // 0 automatic, 1 shot mode, 2 path mode, 3 shot mode with the union region in global memory
+  char* d_uscratch = nullptr;  // global union regions (one per resident CTA)
+  size_t uscratch_bytes = 0;
   char* d_path_res = nullptr;
   int* d_arrive = nullptr;
   size_t trace_bytes = 0, smem_max = 0;
@@ -121,10 +129,27 @@ namespace {
 // as fit in shot mode, then the path-mode layout with the window graph staged
 // in shared memory when it fits too.  The ranker and the candidate dump add
 // the quantised history (4 bytes per short column) to every slot.
+// Global union regions for the windows that need them (all windows when
+// `all`): one region per resident CTA, allocated once, never on a decode call.
+qd_status ensure_uscratch(qd_decoder* dec, bool all) {
+  size_t need = 0;
+  for (const WinGpu& g : dec->wins)
+    if (all || !g.fits)
+      need = std::max(need, (size_t)dec->sm_count * g.grid_g * (size_t)(g.Lg.total - g.Lg.U));
+  if (need <= dec->uscratch_bytes) return QD_OK;
+  cudaFree(dec->d_uscratch);
+  dec->d_uscratch = nullptr;
+  dec->uscratch_bytes = 0;
+  QD_CK(cudaMalloc(&dec->d_uscratch, need));
+  dec->uscratch_bytes = need;
+  return QD_OK;
+}
+
 qd_status configure_layouts(qd_decoder* dec, bool hist, const char* who) {
   struct Conf {
-    qd::Layout L, Lp;
-    int shot_warps, grid_per_sm;
+    qd::Layout L, Lp, Lg;
+    int shot_warps, grid_per_sm, grid_g;
+    bool fits, path_fits;
   };
   const int optin = dec->smem_optin;
   const int nb = dec->kp.nb;
@@ -150,27 +175,42 @@ qd_status configure_layouts(qd_decoder* dec, bool hist, const char* who) {
         c.shot_warps = sw;
       }
     }
-    c.L = lay(c.shot_warps, false);
-    c.Lp = lay(1, true);
-    if (c.Lp.total > (unsigned)optin) c.Lp = lay(1, false);
-    if (c.L.total > (unsigned)optin || c.Lp.total > (unsigned)optin) {
-      set_error(std::string(who) + ": window " + std::to_string(w) + " needs " +
-                std::to_string(std::max(c.L.total, c.Lp.total)) + " B of shared memory (limit " +
+    // the union region in global memory: eight path slots, shared memory for
+    // the persistent part only, no pre-BP staging (its copies need shared memory)
+    c.Lg = lay(kShotWarps, false);
+    c.Lg.pre_stage = 0;
+    if (c.Lg.U > (unsigned)optin) {
+      set_error(std::string(who) + ": window " + std::to_string(w) + " needs " + std::to_string(c.Lg.U) +
+                " B of shared memory even with its path state in global memory (limit " +
                 std::to_string(optin) + ")");
       return QD_EUNSUPPORTED;
     }
-    smem_max = std::max<size_t>(smem_max, std::max(c.L.total, c.Lp.total));
+    int bg = 0;
+    QD_CK(qd::decode_occupancy(0, 32 * kShotWarps, c.Lg.U, &bg));
+    c.grid_g = std::max(1, bg);
+    c.L = lay(c.shot_warps, false);
+    c.fits = c.L.total <= (unsigned)optin;
+    if (!c.fits) c.L = c.Lg;  // shot mode streams the path state through L2 / HBM
+    c.Lp = lay(1, true);
+    if (c.Lp.total > (unsigned)optin) c.Lp = lay(1, false);
+    c.path_fits = c.Lp.total <= (unsigned)optin;
+    smem_max = std::max<size_t>(smem_max, std::max(c.fits ? c.L.total : c.Lg.U, c.path_fits ? c.Lp.total : 0u));
     int blocks = 0;
-    QD_CK(qd::decode_occupancy(0, 32 * c.shot_warps, c.L.total, &blocks));
+    QD_CK(qd::decode_occupancy(0, 32 * (c.fits ? c.shot_warps : kShotWarps), c.fits ? c.L.total : c.Lg.U, &blocks));
     c.grid_per_sm = std::max(1, blocks);
   }
   for (size_t w = 0; w < cf.size(); ++w) {
     WinGpu& g = dec->wins[w];
     g.L = cf[w].L;
     g.Lp = cf[w].Lp;
-    g.shot_warps = cf[w].shot_warps;
+    g.Lg = cf[w].Lg;
+    g.grid_g = cf[w].grid_g;
+    g.fits = cf[w].fits;
+    g.path_fits = cf[w].path_fits;
+    g.shot_warps = cf[w].fits ? cf[w].shot_warps : kShotWarps;
     g.grid_per_sm = cf[w].grid_per_sm;
   }
+  QD_CK_ST(ensure_uscratch(dec, dec->launch_mode == 3));
   dec->smem_max = smem_max;
   dec->hist_on = hist;
   return QD_OK;
@@ -278,6 +318,7 @@ qd_status qd_decoder_destroy(qd_decoder* dec) {
     cudaFree(w.d_wthr);
   }
   cudaFree(dec->d_work);
+  cudaFree(dec->d_uscratch);
   cudaFree(dec->d_ranker);
   cudaFree(dec->d_path_res);
   cudaFree(dec->d_arrive);
@@ -471,10 +512,22 @@ qd_status qd_decode_windows(qd_decoder* dec, int k, const uint32_t* det_bits, in
     if (status) QD_CK(cudaMemsetAsync(status, 0xFF, sizeof(int32_t) * (size_t)n_shots, st));
     return QD_OK;
   }
-  // path mode while the batch leaves most SMs idle in shot mode
+  // the path state in global memory when the window does not fit shared memory
+  // (or on request); otherwise path mode while a batch leaves most SMs idle
+  const bool global = !g.fits || dec->launch_mode == 3;
   bool path_mode = dec->launch_mode == 2;
   if (dec->launch_mode == 0) path_mode = n_shots * 4 <= dec->sm_count;
-  if (path_mode && n_shots > std::min<long long>(dec->max_shots, kPathModeMaxShots)) path_mode = false;
+  if (path_mode && (n_shots > std::min<long long>(dec->max_shots, kPathModeMaxShots) || !g.path_fits || global))
+    path_mode = false;
+  if (global) {
+    QD_CK(cudaMemsetAsync(dec->d_work + k, 0, sizeof(int), st));
+    const long long grid = std::min<long long>(n_shots, (long long)dec->sm_count * g.grid_g);
+    QD_CK(qd::launch_decode(0, (int)grid, 32 * kShotWarps, g.Lg.U, st, dec->kp, g.dv, g.Lg, det_bits, dw, n_shots,
+                            win_correction, dec->corr_words, status, (char*)trace, dec->trace_bytes, dec->dmx,
+                            dec->ns_max, dec->d_work + k, dec->d_counters, nullptr, nullptr, dec->sw_max,
+                            dec->d_uscratch, g.Lg.total - g.Lg.U));
+    return QD_OK;
+  }
   if (path_mode) {
     QD_CK(qd::launch_decode(1, (int)(n_shots * dec->kp.nb), kPathThreads, g.Lp.total, st, dec->kp, g.dv, g.Lp,
                             det_bits, dw, n_shots, win_correction, dec->corr_words, status, (char*)trace,
@@ -633,7 +686,8 @@ qd_status qd_decoder_launch_info(const qd_decoder* dec, int k, int out[6]) {
 
 qd_status qd_decoder_set_launch(qd_decoder* dec, int mode) {
   QD_REQ(dec, "null argument");
-  QD_REQ(mode >= 0 && mode <= 2, "qd_decoder_set_launch: mode must be 0, 1 or 2");
+  QD_REQ(mode >= 0 && mode <= 3, "qd_decoder_set_launch: mode must be 0, 1, 2 or 3");
+  if (mode == 3) QD_CK_ST(ensure_uscratch(dec, true));
   dec->launch_mode = mode;
   return QD_OK;
 }
@@ -710,11 +764,18 @@ extern "C" qd_status qd_decode_commit_static(qd_decoder* dec, int k, uint32_t* d
   cudaStream_t st = (cudaStream_t)stream;
   // the array keeps the previous call's contents: the counters must restart at 0
   QD_CK(cudaMemsetAsync(base, 0, kStaticHeader, st));
-  long long grid = std::min<long long>(n_shots, (long long)dec->sm_count * g.grid_per_sm);
   const int dw = (dec->dem->h.n_det + 31) / 32;
-  if (g.h.n_cols > 0) QD_CK(qd::launch_decode(0, (int)grid, 32 * g.shot_warps, g.L.total, st, dec->kp, g.dv, g.L, det_bits, dw,
-                          n_shots, corr, dec->corr_words, nullptr, nullptr, 0, dec->dmx, dec->ns_max, work, stats,
-                          nullptr, nullptr, dec->sw_max));
+  if (g.h.n_cols > 0) {
+    // the global union regions, when used, were allocated with the decoder
+    const bool global = !g.fits || dec->launch_mode == 3;
+    const qd::Layout& L = global ? g.Lg : g.L;
+    const long long grid =
+        std::min<long long>(n_shots, (long long)dec->sm_count * (global ? g.grid_g : g.grid_per_sm));
+    QD_CK(qd::launch_decode(0, (int)grid, 32 * (global ? kShotWarps : g.shot_warps), global ? L.U : L.total, st,
+                            dec->kp, g.dv, L, det_bits, dw, n_shots, corr, dec->corr_words, nullptr, nullptr, 0,
+                            dec->dmx, dec->ns_max, work, stats, nullptr, nullptr, dec->sw_max,
+                            global ? dec->d_uscratch : nullptr, global ? L.total - L.U : 0));
+  }
   const int w = dec->dem->h.w;
   QD_CK(qd::launch_commit(st, g.h.n_commit, g.d_ccptr, g.d_ccdet, g.d_ccobs, dec->corr_words, corr, n_shots,
                           det_bits, dw, obs_pred, residue_fail, g.h.r0 * w, g.h.commit_b1 * w));

@@ -56,7 +56,8 @@ cudaError_t decode_occupancy(int mode, int threads, size_t smem, int* blocks);
 cudaError_t launch_decode(int mode, int grid, int threads, size_t smem, cudaStream_t st, const KParams& P,
                           const WinDev& W, const Layout& L, const uint32_t* det, int det_words, long long n,
                           uint32_t* corr, int corr_words, int32_t* status, char* trace, size_t tr_bytes, int dmx,
-                          int ns_max, int* work, long long* counters, char* path_res, int* arrive, int sw_max);
+                          int ns_max, int* work, long long* counters, char* path_res, int* arrive, int sw_max,
+                          char* uglob = nullptr, size_t ubytes = 0);
 // One decoder's share of a batched window step (decode + commit).
 struct BatchMember {
   const KParams* P;

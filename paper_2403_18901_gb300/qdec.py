@@ -311,7 +311,8 @@ class Decoder:
                     path_smem=int(out[3]), path_threads=int(out[4]), sms=int(out[5]))
 
     def set_launch(self, mode):
-        """0 automatic, 1 shot mode (throughput), 2 path mode (latency)."""
+        """0 automatic, 1 shot mode (throughput), 2 path mode (latency), 3 shot
+        mode with the path states in global memory."""
         _check(lib().qd_decoder_set_launch(self.h, int(mode)))
 
     def counters(self):

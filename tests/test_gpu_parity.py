@@ -341,3 +341,20 @@ def test_message_restart_with_learned_weights_bit_exact():
     weights = {k: rng.uniform(0.45, 0.9, size=(25, o.window(3, 1, k)["n_edges"])).astype(np.float32)
                for k in range(o.n_windows(3, 1))}
     _pipeline("72", 6, 0.003, params, n=120, seed=7272, trace_windows=(0, 2), mode=1, weights=weights)
+
+
+
+def test_path_state_in_global_memory_bit_exact():
+    """Launch mode 3: the pre-BP scratch and the decision-path states of every
+    CTA in global memory (the shape of windows too large for shared memory)."""
+    _pipeline("144", 12, 0.003, preset("configured", k_guess=4, p=0.003), n=120, seed=144_333,
+              trace_windows=(0, 5), mode=3)
+    _pipeline("72", 6, 0.004, preset("paper", k_guess=3, p=0.004), n=120, seed=72_333, trace_windows=(1,), mode=3)
+
+
+def test_window_too_large_for_shared_memory_bit_exact():
+    """[[288,12,18]] with (6,1) windows: the pre-BP scratch of a 6-round window
+    (8.6k columns) exceeds shared memory, so the decoder streams every CTA's
+    union region through global memory on its own."""
+    params = preset("configured", k_guess=2, p=0.002, W=6, F=1, d_max_main=12)
+    _pipeline("288", 6, 0.002, params, n=8, seed=288_006, trace_windows=(0,), mode=1)
