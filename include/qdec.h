@@ -461,8 +461,10 @@ qd_status qd_decoder_set_launch(qd_decoder* dec, int mode);
 
 /* Launch plan of window k: out[0] shared bytes per CTA in shot mode,
  * out[1] its threads, out[2] its CTAs per SM, out[3] shared bytes per CTA in
- * path mode, out[4] its threads, out[5] SM count. */
-qd_status qd_decoder_launch_info(const qd_decoder* dec, int k, int out[6]);
+ * path mode, out[4] its threads, out[5] SM count, out[6] CTAs per cluster in
+ * path mode (they split each shot's pre-BP; 1: every path CTA runs it whole),
+ * out[7] path-mode CTAs per shot (the paths rounded up to whole clusters). */
+qd_status qd_decoder_launch_info(const qd_decoder* dec, int k, int out[8]);
 
 /* Counters summed over every decode since the last reset: out[0] pre-BP
  * edge-iterations, out[1] GDG edge-iterations, out[2] windows whose pre-BP

@@ -118,11 +118,8 @@ __device__ void stage_pieces(Stager& st, const StagePiece* pc, int n) {
   __syncthreads();  // every earlier access to these bytes has finished
   if (aligned && tot > 0 && !*st.off) {
     if (threadIdx.x == 0) {
-      unsigned long long state;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                   : "=l"(state)
-                   : "r"(smem_u32(st.bar)), "r"(tot)
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(st.bar)), "r"(tot)
                    : "memory");
       for (int i = 0; i < n; ++i)
         if (pc[i].bytes)
@@ -912,6 +909,9 @@ struct DecodeArgs {
   // (L2-resident at these sizes) instead of after the persistent part
   char* uglob;
   size_t ubytes;
+  // path mode: CTAs per shot (the paths, then idle CTAs up to a whole number
+  // of clusters, which only help with the pre-BP)
+  int cps;
 };
 
 __device__ __forceinline__ char* union_base(const DecodeArgs& A, char* sm) {
@@ -945,6 +945,226 @@ struct CommitBatch {
   long long seg_end[kMaxBatch];
   CommitArgs seg[kMaxBatch];
 };
+
+// ---- thread-block clusters: distributed shared memory ----
+__device__ __forceinline__ unsigned cl_size() {
+  unsigned n;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+  return n;
+}
+__device__ __forceinline__ unsigned cl_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// every thread of every CTA of the cluster; orders the shared-memory writes
+// before it with the reads (local or remote) after it
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// the address of `p` (a shared-memory location of this CTA) in CTA `rank`
+__device__ __forceinline__ unsigned cl_map(const void* p, unsigned rank) {
+  unsigned a;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_u32(p)), "r"(rank));
+  return a;
+}
+__device__ __forceinline__ float cl_ld_f32(unsigned a) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t cl_ld_u32(unsigned a) {
+  uint32_t v;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t cl_ld_u8(unsigned a) {
+  uint16_t v;
+  asm volatile("ld.shared::cluster.u8 %0, [%1];" : "=h"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void cl_st_u32(unsigned a, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ CNState cl_ld_cns(unsigned a) {
+  CNState c;
+  asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(c.m1), "=f"(c.m2), "=r"(c.ac), "=r"(c.pad)
+               : "r"(a));
+  return c;
+}
+
+// a2 split over the CTAs of a cluster (path mode, one cluster per shot): CTA
+// r owns the r-th slice of the checks and of the variables, runs the check
+// pass of Eq. (1) for its checks and the variable pass of Eq. (2)-(3) for its
+// variables, and reads the inputs it does not own (posteriors in the check
+// pass; check states and signs in the variable pass) from their owners'
+// shared memory.  Two cluster barriers per iteration separate the passes, so
+// every value read was written in the pass before.  The arithmetic of every
+// message and posterior is that of the single-CTA loop.  At the end every
+// CTA holds the whole posterior and ranking key.  A remote load costs a round
+// trip of ~1200 cycles (a cluster barrier ~470), so each pass makes one: a
+// check's inputs and a variable's messages are requested together, and the
+// per-CTA "unsatisfied" flags are pushed to every CTA before the barrier
+// rather than read remotely after it.  Returns t as the loop leaves it; conv
+// and t_conv as in the caller.
+template <bool LW>
+__device__ int prebp_cluster(const DecodeArgs& A, const WinDev& W, const WinDev& Wg, char* sm, char* U,
+                             const uint32_t* sbits, bool& conv, int& t_conv) {
+  const KParams& P = A.P;
+  const Layout& L = A.L;
+  const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
+  const int nr = W.n_rows, nc = W.n_cols;
+  const unsigned C = cl_size(), r = cl_rank();
+  float* post = (float*)(U + L.p_post);
+  float* key = (float*)(U + L.p_key);
+  CNState* cns = (CNState*)(U + L.p_cns);
+  uint8_t* sign = (uint8_t*)(U + L.p_sign);
+  // flags[8 * parity + c]: CTA c found an unsatisfied check (in the reduction
+  // scratch of the path phase, idle until the pre-BP ends)
+  int* flags = (int*)(sm + L.red);
+  // slices: owner(x) = floor(x / slice) = umulhi(x, ceil(2^32 / slice)), exact for x, slice < 2^16
+  const int sc = (nr + (int)C - 1) / (int)C, sv = (nc + (int)C - 1) / (int)C;
+  const unsigned mc = (unsigned)((0x100000000ull + sc - 1) / sc), mv = (unsigned)((0x100000000ull + sv - 1) / sv);
+  const int jb = min(nr, (int)r * sc), je = min(nr, jb + sc);
+  const int ib = min(nc, (int)r * sv), ie = min(nc, ib + sv);
+  const int tpc = lanes_per_check(NT, max(1, je - jb)), sub = tid & (tpc - 1);
+  const int nrr = (je - jb + NT / tpc - 1) / (NT / tpc) * (NT / tpc);
+  const int tk0 = P.n_pre - 3 > 1 ? P.n_pre - 3 : 1;
+  int t;
+  for (t = 1; t <= P.n_pre; ++t) {
+    bool unsat = false;
+    for (int j0 = tid / tpc; j0 < nrr; j0 += NT / tpc) {
+      const bool real = jb + j0 < je;
+      const int j = real ? jb + j0 : je - 1;
+      const int beg = Wg.row_ptr[j], end = real ? Wg.row_ptr[j + 1] : beg;
+      const CNState oc = cns[j];
+      float m1 = CUDART_INF_F, m2 = CUDART_INF_F;
+      int am = 0xFFFF;
+      uint32_t neg = 0, hp = 0;
+      for (int q = beg + 4 * sub; q < end; q += 4 * tpc) {
+        uint32_t ent[4];
+        float pv[4];
+        uint32_t sg[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ent[u] = (q + u < end) ? Wg.row_ent[q + u] : 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const unsigned i = ent[u] >> 16, e = ent[u] & 0xFFFFu;
+          pv[u] = 0.0f;
+          sg[u] = 0u;
+          if (q + u < end) {
+            pv[u] = (t == 1) ? Wg.llr[i] : cl_ld_f32(cl_map(&post[i], __umulhi(i, mv)));
+            sg[u] = sign[e];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (q + u >= end) break;
+          const int e = (int)(ent[u] & 0xFFFFu);
+          hp ^= pv[u] <= 0.0f;
+          const float wprev = (LW && t > 1) ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t - 1, e) : P.alpha;
+          const float v = (t == 1) ? pv[u] : clipf(__fsub_rn(pv[u], c2v<LW>(wprev, P.clip, oc, e, sg[u])), P.clip);
+          const float a = fabsf(v);
+          if (a < m1) {
+            m2 = m1;
+            m1 = a;
+            am = e;
+          } else if (a < m2) {
+            m2 = a;
+          }
+          const uint32_t sgn = v < 0.0f;
+          neg ^= sgn;
+          sign[e] = (uint8_t)sgn;
+        }
+      }
+      if (tpc > 1) {
+        group_min2(m1, m2, am, neg, tpc);
+        for (int off = tpc >> 1; off; off >>= 1) hp ^= __shfl_xor_sync(FULL, hp, off);
+      }
+      if (sub == 0 && real) {
+        cns[j] = cn_store<LW>(P.alpha, P.clip, m1, m2, am, neg ^ bit_of(sbits, j), end - beg == 1, 0u);
+        unsat |= (hp ^ bit_of(sbits, j)) != 0u;
+      }
+    }
+    const int lu = __syncthreads_or(unsat);
+    if (tid < (int)C) cl_st_u32(cl_map(&flags[8 * (t & 1) + (int)r], (unsigned)tid), (uint32_t)lu);
+    cl_sync();  // check states, signs and flags of pass t
+    const bool any = __any_sync(FULL, lane < (int)C && flags[8 * (t & 1) + lane] != 0);
+    if (!any && t >= 2) {  // iteration t-1 satisfies H e = s in every slice
+      conv = true;
+      t_conv = t - 1;
+      break;
+    }
+    const bool kacc = t >= tk0;
+    for (int i = ib + tid; i < ie; i += NT) {
+      float p = Wg.llr[i];
+      const int eb = Wg.col_ptr[i], ee = Wg.col_ptr[i + 1];
+      // up to six messages requested at once (the column degree of these
+      // windows), then added in ascending check order (Eq. (2))
+      for (int e0 = eb; e0 < ee; e0 += 6) {
+        CNState c[6];
+        uint32_t sg[6];
+#pragma unroll
+        for (int u = 0; u < 6; ++u)
+          if (e0 + u < ee) {
+            const unsigned j = Wg.col_rows[e0 + u], o = __umulhi(j, mc);
+            c[u] = cl_ld_cns(cl_map(&cns[j], o));
+            sg[u] = cl_ld_u8(cl_map(&sign[e0 + u], o));
+          }
+#pragma unroll
+        for (int u = 0; u < 6; ++u)
+          if (e0 + u < ee) {
+            const float wt = LW ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t, e0 + u) : P.alpha;
+            p = __fadd_rn(p, c2v<LW>(wt, P.clip, c[u], e0 + u, sg[u]));
+          }
+      }
+      post[i] = p;
+      if (kacc) {
+        float kv;
+        if (t == tk0) {
+          if (P.n_pre < 4) {
+            const float li = Wg.llr[i];
+            float s = li;
+            for (int q = 1; q < 4 - P.n_pre; ++q) s = __fadd_rn(s, li);
+            kv = __fadd_rn(s, p);
+          } else {
+            kv = p;
+          }
+        } else {
+          kv = __fadd_rn(key[i], p);
+        }
+        key[i] = kv;
+      }
+    }
+    cl_sync();  // posteriors of pass t
+  }
+  // the whole posterior and key in every CTA, then no CTA reuses its shared
+  // memory while another may still read it
+  for (int i0 = tid; i0 < nc; i0 += 4 * NT) {  // four round trips in flight
+    float pv[4], kv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * NT;
+      const unsigned o = i < nc ? __umulhi((unsigned)i, mv) : r;
+      pv[u] = kv[u] = 0.0f;
+      if (o != r) {
+        pv[u] = cl_ld_f32(cl_map(&post[i], o));
+        kv[u] = cl_ld_f32(cl_map(&key[i], o));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * NT;
+      if (i < nc && __umulhi((unsigned)i, mv) != r) {
+        post[i] = pv[u];
+        key[i] = kv[u];
+      }
+    }
+  }
+  cl_sync();
+  return t;
+}
 
 // a1 + a2 (+ a3 when not converged): the shared prefix of both launch shapes.
 // Returns true when the pre-BP converged (cbits then hold its decision).
@@ -1029,6 +1249,9 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
     conv = ok;
   }
   int t_conv = 0;
+  if (WIDE && P.n_pre > 0 && !A.uglob && cl_size() > 1 && nr >= 2 * (int)cl_size() && nc >= 2 * (int)cl_size()) {
+    t = prebp_cluster<LW>(A, W, Wg, sm, U, sbits, conv, t_conv);
+  } else {
   for (t = 1; t <= P.n_pre; ++t) {
     // check nodes; each check also takes the parity of the hard decisions it
     // reads, so for t >= 2 the pass is the convergence test of iteration t-1
@@ -1121,6 +1344,7 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
       }
     }
     __syncthreads();
+  }
   }
   if (!conv && P.n_pre > 0) {  // the convergence test of the last iteration
     bool unsat = false;
@@ -1400,8 +1624,8 @@ __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
   const Layout& L = A.L;
   const int tid = threadIdx.x;
   const int nb = A.P.nb;
-  const long long shot = blockIdx.x / nb;
-  const int id = blockIdx.x % nb;
+  const long long shot = blockIdx.x / A.cps;
+  const int id = blockIdx.x % A.cps;
   int* misc = (int*)(sm + L.misc);
   char* tr = A.trace ? A.trace + (size_t)shot * A.tr_bytes : nullptr;
   Stager stg = stager_init((char*)(misc + 8), &A.counters[4]);
@@ -1426,6 +1650,7 @@ __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
   }
   int t_run = 0;
   const bool conv = window_prefix<LW, true>(A, W, sm, shot, &t_run, stg);
+  if (id >= nb) return;  // a CTA that only shared the pre-BP of its cluster
   if (conv) {
     if (id == 0) write_outputs(A, sm, shot, true, -1, 0, t_run, tr);
     return;
@@ -1665,18 +1890,45 @@ cudaError_t decode_occupancy(int mode, int threads, size_t smem, int* blocks) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::decode_shot_kernel<false>, threads, smem);
 }
 
+cudaError_t path_cluster_occupancy(int threads, size_t smem, int cluster, int* clusters) {
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute at[1];
+  cfg.gridDim = dim3((unsigned)cluster);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaOccupancyMaxActiveClusters(clusters, dev::decode_path_kernel<false>, &cfg);
+}
+
 cudaError_t launch_decode(int mode, int grid, int threads, size_t smem, cudaStream_t st, const KParams& P,
                           const WinDev& W, const Layout& L, const uint32_t* det, int det_words, long long n,
                           uint32_t* corr, int corr_words, int32_t* status, char* trace, size_t tr_bytes, int dmx,
                           int ns_max, int* work, long long* counters, char* path_res, int* arrive, int sw_max,
-                          char* uglob, size_t ubytes) {
+                          char* uglob, size_t ubytes, int cps, int cluster) {
   const dev::DecodeArgs A{P,     W,        L,     det,      det_words, n,     corr,     corr_words, status,
                           trace, tr_bytes, dmx,   ns_max,   work,      counters, path_res, arrive,     sw_max,
-                          uglob, ubytes};
+                          uglob, ubytes,   cps};
   const bool lw = W.wts != nullptr;
-  if (mode == 1) {
-    if (lw) dev::decode_path_kernel<true><<<grid, threads, smem, st>>>(A);
-    else dev::decode_path_kernel<false><<<grid, threads, smem, st>>>(A);
+  if (mode == 1) {  // one cluster of `cluster` CTAs shares each shot's pre-BP
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (lw) return cudaLaunchKernelEx(&cfg, dev::decode_path_kernel<true>, A);
+    return cudaLaunchKernelEx(&cfg, dev::decode_path_kernel<false>, A);
   } else {
     if (lw) dev::decode_shot_kernel<true><<<grid, threads, smem, st>>>(A);
     else dev::decode_shot_kernel<false><<<grid, threads, smem, st>>>(A);

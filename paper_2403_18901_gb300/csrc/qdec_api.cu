@@ -79,6 +79,7 @@ struct WinGpu {
   qd::Layout Lg{};
   int grid_g = 1;
   bool fits = true, path_fits = true;
+  int pcl = 1;  // path mode: CTAs per cluster sharing a shot's pre-BP
 };
 
 template <class T>
@@ -148,7 +149,7 @@ qd_status ensure_uscratch(qd_decoder* dec, bool all) {
 qd_status configure_layouts(qd_decoder* dec, bool hist, const char* who) {
   struct Conf {
     qd::Layout L, Lp, Lg;
-    int shot_warps, grid_per_sm, grid_g;
+    int shot_warps, grid_per_sm, grid_g, pcl;
     bool fits, path_fits;
   };
   const int optin = dec->smem_optin;
@@ -157,6 +158,7 @@ qd_status configure_layouts(qd_decoder* dec, bool hist, const char* who) {
   std::vector<Conf> cf(dec->wins.size());
   for (size_t w = 0; w < cf.size(); ++w) {
     Conf& c = cf[w];
+    c.pcl = 1;
     const auto& h = dec->wins[w].h;
     auto lay = [&](int slots, bool stage) {
       return qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, nb, slots, stage, hist);
@@ -194,6 +196,21 @@ qd_status configure_layouts(qd_decoder* dec, bool hist, const char* who) {
     c.Lp = lay(1, true);
     if (c.Lp.total > (unsigned)optin) c.Lp = lay(1, false);
     c.path_fits = c.Lp.total <= (unsigned)optin;
+    // path mode: the largest cluster (8, 4 or 2 CTAs, at most the number of
+    // paths) that can be resident, its CTAs splitting the pre-BP of a shot
+    c.pcl = 1;
+    for (int C = 8; C >= 2 && c.path_fits; C >>= 1) {
+      if (C > nb || h.n_rows < 2 * C || h.n_cols < 2 * C) continue;
+      int ncl = 0;
+      if (qd::path_cluster_occupancy(kPathThreads, c.Lp.total, C, &ncl) != cudaSuccess) {
+        (void)cudaGetLastError();
+        continue;
+      }
+      if (ncl >= 1) {
+        c.pcl = C;
+        break;
+      }
+    }
     smem_max = std::max<size_t>(smem_max, std::max(c.fits ? c.L.total : c.Lg.U, c.path_fits ? c.Lp.total : 0u));
     int blocks = 0;
     QD_CK(qd::decode_occupancy(0, 32 * (c.fits ? c.shot_warps : kShotWarps), c.fits ? c.L.total : c.Lg.U, &blocks));
@@ -207,6 +224,7 @@ qd_status configure_layouts(qd_decoder* dec, bool hist, const char* who) {
     g.grid_g = cf[w].grid_g;
     g.fits = cf[w].fits;
     g.path_fits = cf[w].path_fits;
+    g.pcl = cf[w].pcl;
     g.shot_warps = cf[w].fits ? cf[w].shot_warps : kShotWarps;
     g.grid_per_sm = cf[w].grid_per_sm;
   }
@@ -529,10 +547,11 @@ qd_status qd_decode_windows(qd_decoder* dec, int k, const uint32_t* det_bits, in
     return QD_OK;
   }
   if (path_mode) {
-    QD_CK(qd::launch_decode(1, (int)(n_shots * dec->kp.nb), kPathThreads, g.Lp.total, st, dec->kp, g.dv, g.Lp,
-                            det_bits, dw, n_shots, win_correction, dec->corr_words, status, (char*)trace,
-                            dec->trace_bytes, dec->dmx, dec->ns_max, nullptr, dec->d_counters, dec->d_path_res,
-                            dec->d_arrive, dec->sw_max));
+    const int cps = (dec->kp.nb + g.pcl - 1) / g.pcl * g.pcl;
+    QD_CK(qd::launch_decode(1, (int)(n_shots * cps), kPathThreads, g.Lp.total, st, dec->kp, g.dv, g.Lp, det_bits,
+                            dw, n_shots, win_correction, dec->corr_words, status, (char*)trace, dec->trace_bytes,
+                            dec->dmx, dec->ns_max, nullptr, dec->d_counters, dec->d_path_res, dec->d_arrive,
+                            dec->sw_max, nullptr, 0, cps, g.pcl));
     return QD_OK;
   }
   QD_CK(cudaMemsetAsync(dec->d_work + k, 0, sizeof(int), st));
@@ -671,7 +690,7 @@ qd_status qd_decoder_set_dump(qd_decoder* dec, void* records, int* count, int ca
   return QD_OK;
 }
 
-qd_status qd_decoder_launch_info(const qd_decoder* dec, int k, int out[6]) {
+qd_status qd_decoder_launch_info(const qd_decoder* dec, int k, int out[8]) {
   QD_REQ(dec && out, "null argument");
   QD_REQ(k >= 0 && k < (int)dec->wins.size(), "qd_decoder_launch_info: window out of range");
   const WinGpu& g = dec->wins[k];
@@ -681,6 +700,8 @@ qd_status qd_decoder_launch_info(const qd_decoder* dec, int k, int out[6]) {
   out[3] = (int)g.Lp.total;
   out[4] = kPathThreads;
   out[5] = dec->sm_count;
+  out[6] = g.pcl;
+  out[7] = (dec->kp.nb + g.pcl - 1) / g.pcl * g.pcl;
   return QD_OK;
 }
 

@@ -305,10 +305,11 @@ class Decoder:
                                       else None, _stream(stream)))
 
     def launch_info(self, k=0):
-        out = np.zeros(6, np.int32)
+        out = np.zeros(8, np.int32)
         _check(lib().qd_decoder_launch_info(self.h, k, _ptr(out)))
         return dict(shot_smem=int(out[0]), shot_threads=int(out[1]), shot_ctas_per_sm=int(out[2]),
-                    path_smem=int(out[3]), path_threads=int(out[4]), sms=int(out[5]))
+                    path_smem=int(out[3]), path_threads=int(out[4]), sms=int(out[5]),
+                    path_cluster=int(out[6]), path_ctas_per_shot=int(out[7]))
 
     def set_launch(self, mode):
         """0 automatic, 1 shot mode (throughput), 2 path mode (latency), 3 shot

@@ -173,6 +173,18 @@ def test_path_per_cta_launch_bit_exact(key, R, k, pname, n):
               trace_windows=(0, 1, 2, 3), mode=2)
 
 
+@pytest.mark.parametrize("key,R,pname,k,cluster,cps", [("144", 12, "configured", 4, 8, 16),
+                                                       ("72", 6, "paper", 3, 8, 16),
+                                                       ("72", 6, "configured", 1, 2, 2)])
+def test_path_launch_splits_the_prebp_over_a_cluster(key, R, pname, k, cluster, cps):
+    """Path mode runs each shot's pre-BP on a cluster of CTAs (the paths,
+    rounded up to whole clusters); the parity tests above run this launch."""
+    d = qdec.Dem(CODES[key], 0.003, R)
+    dec = qdec.Decoder(d, preset(pname, k_guess=k), max_shots=4)
+    info = dec.launch_info(1)
+    assert info["path_cluster"] == cluster and info["path_ctas_per_shot"] == cps
+
+
 def test_bb144_paper_preset_k5_bit_exact():
     params = preset("paper", k_guess=5)
     _pipeline("144", 12, 0.004, params, n=60, seed=144_004, trace_windows=tuple(range(11)))
