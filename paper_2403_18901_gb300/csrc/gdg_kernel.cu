@@ -914,8 +914,12 @@ struct DecodeArgs {
   int cps;
 };
 
+// UG (a template parameter, so that shared-memory kernels keep shared-memory
+// instructions for every union access): the region lives in global memory.
+template <bool UG>
 __device__ __forceinline__ char* union_base(const DecodeArgs& A, char* sm) {
-  return A.uglob ? A.uglob + (size_t)blockIdx.x * A.ubytes : sm + A.L.U;
+  if (UG) return A.uglob + (size_t)blockIdx.x * A.ubytes;
+  return sm + A.L.U;
 }
 
 // One window step of several decoders in one launch (kernel parameter).
@@ -945,6 +949,151 @@ struct CommitBatch {
   long long seg_end[kMaxBatch];
   CommitArgs seg[kMaxBatch];
 };
+
+// ---- ascending sort of n = 2^m 64-bit keys in shared memory (all threads) ----
+// A bitonic network.  Every stage of stride < 256 runs in registers: a warp
+// holds a segment of 256 keys, lane L the keys L + 32 r (r < 8), so strides
+// 32..128 pair two registers of a lane and strides 1..16 two lanes (shuffles).
+// Strides >= 256 pass through shared memory, up to three stages per pass.
+// Keys that differ sort the same under any correct network.
+__device__ __forceinline__ unsigned long long shfl_u64(unsigned long long v, int m) {
+  const unsigned lo = __shfl_xor_sync(FULL, (unsigned)v, m), hi = __shfl_xor_sync(FULL, (unsigned)(v >> 32), m);
+  return ((unsigned long long)hi << 32) | lo;
+}
+
+// stride 32 RJ: registers r and r | RJ of a lane
+template <int RJ>
+__device__ __forceinline__ void reg_stage(unsigned long long (&v)[8], int base, int lane, int kk) {
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+    if (!(r & RJ)) {
+      const bool up = ((base + 32 * r + lane) & kk) == 0;
+      const unsigned long long a = v[r], b = v[r | RJ];
+      const bool sw = (a > b) == up;
+      v[r] = sw ? b : a;
+      v[r | RJ] = sw ? a : b;
+    }
+}
+
+// the stages of block size kk with strides j0 >= j >= 1 (j0 < 256) of one
+// register segment whose first key has global index base
+__device__ __forceinline__ void seg_stages(unsigned long long (&v)[8], int base, int lane, int kk, int j0) {
+  for (int j = j0; j > 0; j >>= 1) {
+    if (j == 128) {
+      reg_stage<4>(v, base, lane, kk);
+    } else if (j == 64) {
+      reg_stage<2>(v, base, lane, kk);
+    } else if (j == 32) {
+      reg_stage<1>(v, base, lane, kk);
+    } else {
+      const bool low = (lane & j) == 0;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const unsigned long long o = shfl_u64(v[r], j);
+        const bool up = ((base + 32 * r + lane) & kk) == 0;
+        const bool keep_min = low == up;
+        v[r] = keep_min ? (o < v[r] ? o : v[r]) : (o > v[r] ? o : v[r]);
+      }
+    }
+  }
+}
+
+// M stages of strides j, j/2, ..., j/2^(M-1) (all >= 256) through shared memory
+template <int M>
+__device__ __forceinline__ void smem_stages(unsigned long long* s, int n, int kk, int j) {
+  const int b1 = __ffs(j) - 1;
+  for (int g = threadIdx.x; g < (n >> M); g += blockDim.x) {
+    int base = g;
+#pragma unroll
+    for (int q = M - 1; q >= 0; --q) {  // zero bits at b1-M+1 .. b1, lowest first
+      const int b = b1 - q;
+      base = ((base >> b) << (b + 1)) | (base & ((1 << b) - 1));
+    }
+    const bool up = (base & kk) == 0;
+    unsigned long long v[1 << M];
+#pragma unroll
+    for (int t = 0; t < (1 << M); ++t) {
+      int off = 0;
+#pragma unroll
+      for (int l = 0; l < M; ++l) off += ((t >> l) & 1) * (j >> (M - 1 - l));
+      v[t] = s[base + off];
+    }
+#pragma unroll
+    for (int l = M - 1; l >= 0; --l)  // bit l of t <-> stride j >> (M - 1 - l), largest first
+#pragma unroll
+      for (int t = 0; t < (1 << M); ++t)
+        if (!((t >> l) & 1)) {
+          const unsigned long long a = v[t], b = v[t | (1 << l)];
+          const bool sw = (a > b) == up;
+          v[t] = sw ? b : a;
+          v[t | (1 << l)] = sw ? a : b;
+        }
+#pragma unroll
+    for (int t = 0; t < (1 << M); ++t) {
+      int off = 0;
+#pragma unroll
+      for (int l = 0; l < M; ++l) off += ((t >> l) & 1) * (j >> (M - 1 - l));
+      s[base + off] = v[t];
+    }
+  }
+}
+
+// Call with every thread; s holds n keys (n a power of two); returns after a barrier.
+__device__ void block_sort_u64(unsigned long long* s, int n) {
+  const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = NT >> 5;
+  if (n < 256) {  // tiny windows: the plain network
+    for (int kk = 2; kk <= n; kk <<= 1)
+      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+        for (int i = tid; i < n; i += NT) {
+          const int ixj = i ^ jj;
+          if (ixj > i) {
+            const unsigned long long a = s[i], b = s[ixj];
+            if ((a > b) == ((i & kk) == 0)) {
+              s[i] = b;
+              s[ixj] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    return;
+  }
+  // every block size up to 256 inside the segments
+  for (int sg = warp; sg < (n >> 8); sg += nw) {
+    const int base = sg << 8;
+    unsigned long long v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = s[base + 32 * r + lane];
+    for (int kk = 2; kk <= 256; kk <<= 1) seg_stages(v, base, lane, kk, kk >> 1);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) s[base + 32 * r + lane] = v[r];
+  }
+  __syncthreads();
+  for (int kk = 512; kk <= n; kk <<= 1) {
+    int j = kk >> 1;
+    for (; j >= 256 * 4; j >>= 3) {  // three stages, all of stride >= 256
+      smem_stages<3>(s, n, kk, j);
+      __syncthreads();
+    }
+    if (j >= 512) {
+      smem_stages<2>(s, n, kk, j);
+      __syncthreads();
+    } else if (j == 256) {
+      smem_stages<1>(s, n, kk, j);
+      __syncthreads();
+    }
+    for (int sg = warp; sg < (n >> 8); sg += nw) {
+      const int base = sg << 8;
+      unsigned long long v[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[r] = s[base + 32 * r + lane];
+      seg_stages(v, base, lane, kk, 128);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) s[base + 32 * r + lane] = v[r];
+    }
+    __syncthreads();
+  }
+}
 
 // ---- thread-block clusters: distributed shared memory ----
 __device__ __forceinline__ unsigned cl_size() {
@@ -1168,7 +1317,7 @@ __device__ int prebp_cluster(const DecodeArgs& A, const WinDev& W, const WinDev&
 
 // a1 + a2 (+ a3 when not converged): the shared prefix of both launch shapes.
 // Returns true when the pre-BP converged (cbits then hold its decision).
-template <bool LW, bool WIDE>
+template <bool LW, bool WIDE, bool UG>
 __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, long long shot, int* t_run_out,
                               Stager& stg) {
   const KParams& P = A.P;
@@ -1178,7 +1327,7 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
   uint32_t* sbits = (uint32_t*)(sm + L.sbits);
   uint32_t* cbits = (uint32_t*)(sm + L.cbits);
   uint16_t* sel = (uint16_t*)(sm + L.sel);
-  char* U = union_base(A, sm);
+  char* U = union_base<UG>(A, sm);
   float* post = (float*)(U + L.p_post);
   float* key = (float*)(U + L.p_key);
   CNState* cns = (CNState*)(U + L.p_cns);
@@ -1249,7 +1398,7 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
     conv = ok;
   }
   int t_conv = 0;
-  if (WIDE && P.n_pre > 0 && !A.uglob && cl_size() > 1 && nr >= 2 * (int)cl_size() && nc >= 2 * (int)cl_size()) {
+  if (WIDE && !UG && P.n_pre > 0 && cl_size() > 1 && nr >= 2 * (int)cl_size() && nc >= 2 * (int)cl_size()) {
     t = prebp_cluster<LW>(A, W, Wg, sm, U, sbits, conv, t_conv);
   } else {
   for (t = 1; t <= P.n_pre; ++t) {
@@ -1376,21 +1525,7 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
   for (int i = tid; i < L.sortn; i += NT)
     sortb[i] = i < nc ? (((unsigned long long)ordkey(key[i]) << 32) | (unsigned)i) : ~0ull;
   __syncthreads();
-  for (int kk = 2; kk <= L.sortn; kk <<= 1)
-    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-      for (int i = tid; i < L.sortn; i += NT) {
-        const int ixj = i ^ jj;
-        if (ixj > i) {
-          const unsigned long long a = sortb[i], b = sortb[ixj];
-          const bool up = (i & kk) == 0;
-          if ((a > b) == up) {
-            sortb[i] = b;
-            sortb[ixj] = a;
-          }
-        }
-      }
-      __syncthreads();
-    }
+  block_sort_u64(sortb, L.sortn);
   for (int k = tid; k < n_short; k += NT) sel[k] = (uint16_t)(sortb[k] & 0xFFFFu);
   __syncthreads();
   // ---- shortened matrix in shared memory ----
@@ -1516,7 +1651,7 @@ __device__ void write_outputs(const DecodeArgs& A, char* sm, long long shot, boo
 // ---- shot mode: persistent CTAs of up to 8 warps, one warp per decision path ----
 // One shot of one window by the whole CTA (every thread calls).  misc[2], the
 // decision-path queue, must be 0 on entry.
-template <bool LW>
+template <bool LW, bool UG>
 __device__ void shot_body(const DecodeArgs& A, long long shot, char* sm, Stager& stg) {
   const Layout& L = A.L;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1528,14 +1663,14 @@ __device__ void shot_body(const DecodeArgs& A, long long shot, char* sm, Stager&
   const uint16_t* sel = (const uint16_t*)(sm + L.sel);
   char* tr = A.trace ? A.trace + (size_t)shot * A.tr_bytes : nullptr;
   int t_run = 0;
-  const bool conv = window_prefix<LW, false>(A, A.W, sm, shot, &t_run, stg);
+  const bool conv = window_prefix<LW, false, UG>(A, A.W, sm, shot, &t_run, stg);
   int winner = -1;
   const int n_short = conv ? 0 : A.W.n_short;
   if (!conv) {
     // warps beyond the layout's path slots (batched launches) sit out the paths
     if (warp < L.nslots) {
       const ShortG G = short_graph(sm, L, A.W, n_short);
-      const Slot B = make_slot(union_base(A, sm) + (size_t)warp * L.b_size, L);
+      const Slot B = make_slot(union_base<UG>(A, sm) + (size_t)warp * L.b_size, L);
       const WarpGrp g{lane};
       while (true) {
         int id = 0;
@@ -1572,7 +1707,7 @@ __device__ void shot_body(const DecodeArgs& A, long long shot, char* sm, Stager&
   write_outputs(A, sm, shot, conv, winner, n_short, t_run, tr);
 }
 
-template <bool LW>
+template <bool LW, bool UG>
 __global__ void __launch_bounds__(256, 2) decode_shot_kernel(DecodeArgs A) {
   extern __shared__ __align__(16) char sm[];
   int* misc = (int*)(sm + A.L.misc);
@@ -1586,7 +1721,7 @@ __global__ void __launch_bounds__(256, 2) decode_shot_kernel(DecodeArgs A) {
     __syncthreads();
     const long long shot = misc[0];
     if (shot >= A.n_shots) break;
-    shot_body<LW>(A, shot, sm, stg);
+    shot_body<LW, UG>(A, shot, sm, stg);
   }
 }
 
@@ -1613,7 +1748,7 @@ __global__ void __launch_bounds__(256, 2) decode_batch_kernel(const __grid_const
     const long long shot = g - (m ? B.seg_end[m - 1] : 0);
     if (threadIdx.x == 0) ((int*)(sm + A.L.misc))[2] = 0;
     __syncthreads();
-    shot_body<LW>(A, shot, sm, stg);
+    shot_body<LW, false>(A, shot, sm, stg);
   }
 }
 
@@ -1649,7 +1784,7 @@ __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
     W.llr = ll;
   }
   int t_run = 0;
-  const bool conv = window_prefix<LW, true>(A, W, sm, shot, &t_run, stg);
+  const bool conv = window_prefix<LW, true, false>(A, W, sm, shot, &t_run, stg);
   if (id >= nb) return;  // a CTA that only shared the pre-BP of its cluster
   if (conv) {
     if (id == 0) write_outputs(A, sm, shot, true, -1, 0, t_run, tr);
@@ -1657,7 +1792,7 @@ __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
   }
   const int n_short = A.W.n_short;
   const ShortG G = short_graph(sm, L, A.W, n_short);
-  const Slot B = make_slot(union_base(A, sm), L);
+  const Slot B = make_slot(union_base<false>(A, sm), L);
   const CtaGrp g{tid, (int)blockDim.x, sm + L.red};
   const size_t rb = path_result_bytes(A.sw_max);
   char* mine = A.path_res + ((size_t)shot * nb + id) * rb;
@@ -1825,9 +1960,14 @@ size_t trace_bytes_per_shot(int nb, int dmx, int ns_max) { return dev::trace_byt
 
 cudaError_t set_decode_smem(size_t bytes) {
   const int b = (int)bytes;
-  cudaError_t e = cudaFuncSetAttribute(dev::decode_shot_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  cudaError_t e =
+      cudaFuncSetAttribute(dev::decode_shot_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(dev::decode_shot_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    e = cudaFuncSetAttribute(dev::decode_shot_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(dev::decode_shot_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(dev::decode_shot_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(dev::decode_path_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   if (e == cudaSuccess)
@@ -1887,7 +2027,9 @@ cudaError_t launch_commit_batch(cudaStream_t st, const BatchMember* m, int n) {
 cudaError_t decode_occupancy(int mode, int threads, size_t smem, int* blocks) {
   if (mode == 1)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::decode_path_kernel<false>, threads, smem);
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::decode_shot_kernel<false>, threads, smem);
+  if (mode == 3)  // shot mode with the union region in global memory
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::decode_shot_kernel<false, true>, threads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, dev::decode_shot_kernel<false, false>, threads, smem);
 }
 
 cudaError_t path_cluster_occupancy(int threads, size_t smem, int cluster, int* clusters) {
@@ -1930,8 +2072,13 @@ cudaError_t launch_decode(int mode, int grid, int threads, size_t smem, cudaStre
     if (lw) return cudaLaunchKernelEx(&cfg, dev::decode_path_kernel<true>, A);
     return cudaLaunchKernelEx(&cfg, dev::decode_path_kernel<false>, A);
   } else {
-    if (lw) dev::decode_shot_kernel<true><<<grid, threads, smem, st>>>(A);
-    else dev::decode_shot_kernel<false><<<grid, threads, smem, st>>>(A);
+    if (uglob) {
+      if (lw) dev::decode_shot_kernel<true, true><<<grid, threads, smem, st>>>(A);
+      else dev::decode_shot_kernel<false, true><<<grid, threads, smem, st>>>(A);
+    } else {
+      if (lw) dev::decode_shot_kernel<true, false><<<grid, threads, smem, st>>>(A);
+      else dev::decode_shot_kernel<false, false><<<grid, threads, smem, st>>>(A);
+    }
   }
   return cudaGetLastError();
 }

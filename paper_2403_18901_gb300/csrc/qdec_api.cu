@@ -188,7 +188,7 @@ qd_status configure_layouts(qd_decoder* dec, bool hist, const char* who) {
       return QD_EUNSUPPORTED;
     }
     int bg = 0;
-    QD_CK(qd::decode_occupancy(0, 32 * kShotWarps, c.Lg.U, &bg));
+    QD_CK(qd::decode_occupancy(3, 32 * kShotWarps, c.Lg.U, &bg));
     c.grid_g = std::max(1, bg);
     c.L = lay(c.shot_warps, false);
     c.fits = c.L.total <= (unsigned)optin;
@@ -213,7 +213,8 @@ qd_status configure_layouts(qd_decoder* dec, bool hist, const char* who) {
     }
     smem_max = std::max<size_t>(smem_max, std::max(c.fits ? c.L.total : c.Lg.U, c.path_fits ? c.Lp.total : 0u));
     int blocks = 0;
-    QD_CK(qd::decode_occupancy(0, 32 * (c.fits ? c.shot_warps : kShotWarps), c.fits ? c.L.total : c.Lg.U, &blocks));
+    QD_CK(qd::decode_occupancy(c.fits ? 0 : 3, 32 * (c.fits ? c.shot_warps : kShotWarps), c.fits ? c.L.total : c.Lg.U,
+                               &blocks));
     c.grid_per_sm = std::max(1, blocks);
   }
   for (size_t w = 0; w < cf.size(); ++w) {

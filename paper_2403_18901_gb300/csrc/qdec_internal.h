@@ -52,6 +52,8 @@ bool build_window(const DemHost& d, int W, int F, int k, bool shorten, WindowHos
 
 size_t trace_bytes_per_shot(int nb, int dmx, int ns_max);
 cudaError_t set_decode_smem(size_t bytes);
+// CTAs per SM of the decode kernel: mode 0 shot mode, 1 path mode, 3 shot
+// mode with the union region in global memory.
 cudaError_t decode_occupancy(int mode, int threads, size_t smem, int* blocks);
 cudaError_t launch_decode(int mode, int grid, int threads, size_t smem, cudaStream_t st, const KParams& P,
                           const WinDev& W, const Layout& L, const uint32_t* det, int det_words, long long n,
