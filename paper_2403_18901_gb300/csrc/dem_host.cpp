@@ -393,8 +393,10 @@ bool build_window(const DemHost& d, int W, int F, int k, bool shorten, WindowHos
   }
   o.n_cols = (int)o.gcols.size();
   o.n_edges = (int)o.col_rows.size();
-  if (o.n_edges >= 65535 || o.n_rows >= 65535 || o.n_cols >= 65535) {
-    set_error("window larger than 16-bit indices");
+  // 16-bit edge ids; row and column ids below 2^15, as the decoder packs
+  // (index << 16) | label into one positive int for its tie-breaks
+  if (o.n_edges >= 65535 || o.n_rows >= 32768 || o.n_cols >= 32768) {
+    set_error("window larger than 16-bit edge / 15-bit node indices");
     return false;
   }
   o.row_ptr.assign(o.n_rows + 1, 0);

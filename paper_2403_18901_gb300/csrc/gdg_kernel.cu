@@ -344,8 +344,11 @@ struct ShortG {
   int wT, wE;
   int rpb;  // window rows per block (block of a column = its first row / rpb)
   const uint16_t* sel;    // short column -> window column
-  const uint16_t* cperm;  // checks by descending degree in the shortened matrix (ties by index)
-  const uint16_t* vperm;  // short columns by descending degree (ties by index)
+  // Checks and short columns are numbered by descending degree (ties by
+  // window row / rank); these map a label back to the window row and to the
+  // ranked column, whose order decides every tie.
+  const uint16_t* cperm;
+  const uint16_t* vperm;
 };
 
 struct Slot {
@@ -400,18 +403,19 @@ __device__ int peel(const ShortG& G, const Slot& B, const Grp& g) {
   int npeel = 0;
   for (int guard = 0; guard <= G.ns + 1; ++guard) {
     bool contra = false;
-    int cand = kNone;
+    int cand = kNone;  // (window row << 16) | label of the lowest degree-one check
     for (int j = g.rank; j < G.nr; j += g.size) {
       const int d = B.deg[j];
       if (d == 0) {
         if (bit_of(B.sp, j)) contra = true;
-      } else if (d == 1 && cand == kNone) {
-        cand = j;
+      } else if (d == 1) {
+        cand = min(cand, ((int)G.cperm[j] << 16) | j);
       }
     }
     if (g.any(contra)) return -1;
-    const int j = (int)g.min_u((unsigned)cand);
-    if (j == kNone) return npeel;
+    const int jc = (int)g.min_u((unsigned)cand);
+    if (jc == kNone) return npeel;
+    const int j = jc & 0xFFFF;
     int found = kNone;
     for (int q = G.rowptr[j] + g.rank; q < G.rowptr[j + 1]; q += g.size) {
       const int i = (int)(G.rowent[q] >> 16);
@@ -483,14 +487,15 @@ __device__ __forceinline__ uint32_t ranker_pair(const ShortG& G, const Slot& B, 
     hi = (float)min(nus, 127);
   } else {
     lo = (float)G.vdeg[k];
-    hi = (float)min(G.colrows[G.colptr[k]] / G.rpb, 255);
+    hi = (float)min(G.cperm[G.colrows[G.colptr[k]]] / G.rpb, 255);
   }
   return bf16x2_exact(lo, hi);
 }
 
-// Highest score over the candidates (ties to the lowest column), as
-// (-score, column) for the group's lexicographic argmin.  Each warp of the
-// group scores tiles of 16 consecutive columns; every lane of the group calls.
+// Highest score over the candidates (ties to the lowest ranked column), as
+// (-score, (ranked column << 16) | label) for the group's lexicographic
+// argmin.  Each warp of the group scores tiles of 16 consecutive labels;
+// every lane of the group calls.
 template <class Grp>
 __device__ void ranker_select(const KParams& P, const ShortG& G, const Slot& B, const Grp& g, float& nv, int& nk) {
   const int lane = g.rank & 31, wid = g.rank >> 5, nw = g.size >> 5;
@@ -524,14 +529,20 @@ __device__ void ranker_select(const KParams& P, const ShortG& G, const Slot& B, 
     }
     const float sc0 = __fadd_rn(__fadd_rn(__fadd_rn(q[0], q[1]), __fadd_rn(q[2], q[3])), b2);
     const float sc1 = __fadd_rn(__fadd_rn(__fadd_rn(p[0], p[1]), __fadd_rn(p[2], p[3])), b2);
-    // rows grow with the tile, so a strict '<' keeps the lowest column
-    if (c0 && -sc0 < nv) {
-      nv = -sc0;
-      nk = r0;
+    // ties to the lowest ranked column: (column << 16) | label
+    if (c0) {
+      const int pk = ((int)G.vperm[r0] << 16) | r0;
+      if (-sc0 < nv || (-sc0 == nv && pk < nk)) {
+        nv = -sc0;
+        nk = pk;
+      }
     }
-    if (c1 && -sc1 < nv) {
-      nv = -sc1;
-      nk = r1;
+    if (c1) {
+      const int pk = ((int)G.vperm[r1] << 16) | r1;
+      if (-sc1 < nv || (-sc1 == nv && pk < nk)) {
+        nv = -sc1;
+        nk = pk;
+      }
     }
   }
   g.argmin(nv, nk);
@@ -557,9 +568,9 @@ __device__ void dump_candidates(const KParams& P, const ShortG& G, const Slot& B
     r.x[4] = (float)(int8_t)(h4 >> 24) * 0.5f;
     r.x[5] = (float)min(nus, 127);
     r.x[6] = (float)G.vdeg[k];
-    r.x[7] = (float)min(G.colrows[G.colptr[k]] / G.rpb, 255);
+    r.x[7] = (float)min(G.cperm[G.colrows[G.colptr[k]]] / G.rpb, 255);
     r.shot = (int32_t)shot;
-    r.wcol = G.sel[k];
+    r.wcol = G.sel[G.vperm[k]];
     r.depth = (int16_t)D;
     r.path = 0;
     r.flags = (L <= 0.0f ? 1 : 0) | (k == gsel ? 2 : 0);
@@ -619,7 +630,7 @@ struct PathOut {
 template <bool LW, class Grp>
 __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int id, const Grp& g,
                          const PathOut& out, int dmx) {
-  const int nr = G.nr, ns = G.ns, rw = G.rw, R = g.rank, S = g.size;
+  const int nr = G.nr, ns = G.ns, R = g.rank, S = g.size;
   // one lane per check for a warp; small lane groups per check for a CTA
   const int tpc = Grp::kWarp ? 1 : lanes_per_check(S, nr), sub = R & (tpc - 1);
   const int nr_rounds = (nr + S / tpc - 1) / (S / tpc) * (S / tpc);
@@ -638,7 +649,11 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
     B.deg[j] = G.rowptr[j + 1] - G.rowptr[j];
     B.cns[j].pad = (uint32_t)G.rowptr[j] | ((uint32_t)G.rowptr[j + 1] << 16);
   }
-  for (int x = R; x < rw; x += S) B.sp[x] = G.sbits[x];
+  for (int base = 0; base < nr; base += S) {  // the window syndrome by check label
+    const int j = base + R;
+    const unsigned m = __ballot_sync(FULL, j < nr && bit_of(G.sbits, G.cperm[j]));
+    if ((R & 31) == 0 && base + R < nr) B.sp[(base + R) >> 5] = m;
+  }
   if (out.st)
     for (int q = R; q < dmx; q += S) out.st[q] = StepTrace{-2, -1, 0, 0, 0};
   g.sync();
@@ -659,13 +674,13 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
     PA = main_rules(D) ? P.pa_main : P.pa_other;  // read by this step's history flags
     for (int it = 1; it <= P.ips; ++it) {
       // ---- check-node update, Eq. (1), over active VNs; tpc lanes per check ----
-      // checks in descending static degree, so the lanes of a round loop alike.
+      // checks in label order (descending static degree): the lanes of a round loop alike.
       // Each check also takes the parity of its active VNs' hard decisions
       // (Eq. (4)) from the posteriors it reads: for it >= 2 this pass is the
       // convergence test H e = s of the previous iteration (Sec. II-A).
       bool unsat = false;
       for (int j0 = R / tpc; j0 < nr_rounds; j0 += S / tpc) {
-        const int j = G.cperm[j0 < nr ? j0 : nr - 1];
+        const int j = j0 < nr ? j0 : nr - 1;
         const int d = j0 < nr ? B.deg[j] : 0;
         if (tpc == 1 && d == 0) {  // no shuffle partner waits for this lane
           if (j0 < nr) unsat |= bit_of(B.sp, j) != 0u;
@@ -722,9 +737,8 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
       // ---- variable-node update, Eq. (2)-(3); history of Sec. IV-A ----
       const bool hist = it > P.ips - 4;
       const bool hist0 = it == P.ips - 3;
-      // variables in descending degree, so the lanes of a round loop alike
-      for (int k0 = R; k0 < ns; k0 += S) {
-        const int k = G.vperm[k0];
+      // variables in label order (descending degree): the lanes of a round loop alike
+      for (int k = R; k < ns; k += S) {
         if (B.status[k] != -1) continue;
         float p = G.llr[k];
         const int eb = G.colptr[k], ee = G.colptr[k + 1];
@@ -769,6 +783,8 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
     {
       // ---- SELECT-VN (Alg. 1) with AGG-DEC (Alg. 3) ----
       const float PBd = (D == 1) ? P.pb_d1 : (main_rules(D) ? P.pb_main : P.pb_other);
+      // bk, tk: (ranked column << 16) | label, so that ties go to the lowest
+      // ranked column (the oracle's index order) whatever the label order
       float bL = CUDART_INF_F, tL = CUDART_INF_F;
       int bk = kNone, tk = kNone, nagg = 0;
       for (int k = R; k < ns; k += S) {
@@ -788,19 +804,20 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
           }
         }
         if (P.rkq) continue;
-        if (L < bL) {
+        const int pk = ((int)G.vperm[k] << 16) | k;
+        if (L < bL || (L == bL && pk < bk)) {
           bL = L;
-          bk = k;
+          bk = pk;
         }
-        if ((fl & 1) && L < tL) {
+        if ((fl & 1) && (L < tL || (L == tL && pk < tk))) {
           tL = L;
-          tk = k;
+          tk = pk;
         }
       }
       if (P.rkq) {
         g.sync();  // the aggressive decisions are visible
         ranker_select(P, G, B, g, bL, bk);
-        if (bk != kNone) bL = B.acc[bk];  // f keeps the rule of Alg. 1: [L <= 0]
+        if (bk != kNone) bL = B.acc[bk & 0xFFFF];  // f keeps the rule of Alg. 1: [L <= 0]
       } else {
         g.argmin(bL, bk);
         g.argmin(tL, tk);
@@ -809,10 +826,10 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
       g.sync();
       int gsel, f;
       if (tk != kNone) {
-        gsel = tk;
+        gsel = tk & 0xFFFF;
         f = 1;
       } else if (bk != kNone) {
-        gsel = bk;
+        gsel = bk & 0xFFFF;
         f = bL <= 0.0f ? 1 : 0;
       } else {
         if (out.st && R == 0) out.st[D - 1] = StepTrace{-1, -1, 0, (int16_t)nagg, 0};
@@ -833,7 +850,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
       g.sync();
       const int np = peel(G, B, g);
       if (out.st && R == 0)
-        out.st[D - 1] = StepTrace{(int16_t)gsel, (int8_t)v, 0, (int16_t)nagg, (int16_t)(np < 0 ? -1 : np)};
+        out.st[D - 1] = StepTrace{(int16_t)G.vperm[gsel], (int8_t)v, 0, (int16_t)nagg, (int16_t)(np < 0 ? -1 : np)};
       if (np < 0) {
         status = np == -1 ? BR_CONTRADICTION : BR_INTERNAL;
         goto done;
@@ -848,18 +865,14 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
     }
   }
 done:
+  // the estimate by ranked column (bit vperm[k] for label k)
+  for (int x = R; x < (ns + 31) >> 5; x += S) out.ebits[x] = 0u;
   g.sync();
-  for (int base = 0; base < ns; base += S) {
-    const int k = base + R;
-    bool one = false;
-    if (k < ns) {
-      const int s8 = B.status[k];
-      one = s8 == 1 || (s8 == -1 && B.post[k] <= 0.0f);
-      if (out.fstat) out.fstat[k] = (int8_t)s8;
-    }
-    const unsigned m = __ballot_sync(FULL, one);
-    const int w0 = base + (R & ~31);
-    if ((R & 31) == 0 && w0 < ns) out.ebits[w0 >> 5] = m;
+  for (int k = R; k < ns; k += S) {
+    const int s8 = B.status[k];
+    const int kr = G.vperm[k];
+    if (s8 == 1 || (s8 == -1 && B.post[k] <= 0.0f)) atomicOr(&out.ebits[kr >> 5], 1u << (kr & 31));
+    if (out.fstat) out.fstat[kr] = (int8_t)s8;
   }
   visits = g.sum_ll(visits);
   if (R == 0) {
@@ -1528,23 +1541,61 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
   block_sort_u64(sortb, L.sortn);
   for (int k = tid; k < n_short; k += NT) sel[k] = (uint16_t)(sortb[k] & 0xFFFFu);
   __syncthreads();
-  // ---- shortened matrix in shared memory ----
+  // ---- shortened matrix in shared memory, numbered in processing order ----
+  // Columns and checks get labels by descending degree (ties by rank / row),
+  // so the lanes of a round loop alike and touch neighbouring words; vperm
+  // and cperm map a label back to the ranked column and the window row, which
+  // decide every tie.  A column's checks stay in ascending window row (the
+  // order of the sum of Eq. (2)).
   uint16_t* scp = (uint16_t*)(sm + L.s_colptr);
   uint16_t* scr = (uint16_t*)(sm + L.s_colrows);
   uint16_t* srp = (uint16_t*)(sm + L.s_rowptr);
   uint32_t* sre = (uint32_t*)(sm + L.s_rowent);
   float* sllr = (float*)(sm + L.s_llr);
   uint8_t* svd = (uint8_t*)(sm + L.s_vdeg);
+  uint16_t* sef = (uint16_t*)(sm + L.s_efull);
+  uint16_t* cperm = (uint16_t*)(sm + L.s_cperm);
+  uint16_t* vperm = (uint16_t*)(sm + L.s_vperm);
   int* rc = (int*)(sm + L.rowcnt);
   int* tmp = (int*)sortb;  // the sort buffer is free now
   for (int k = tid; k < n_short; k += NT) {
     const int c = sel[k];
-    const int d = W.col_ptr[c + 1] - W.col_ptr[c];
-    tmp[k] = d;
-    sllr[k] = W.llr[c];
-    svd[k] = (uint8_t)d;
+    tmp[k] = W.col_ptr[c + 1] - W.col_ptr[c];
   }
   for (int j = tid; j <= nr; j += NT) rc[j] = 0;
+  __syncthreads();
+  for (int k = tid; k < n_short; k += NT) {  // rows of the shortened matrix
+    const int c = sel[k];
+    for (int e = W.col_ptr[c]; e < W.col_ptr[c + 1]; ++e) atomicAdd(&rc[W.col_rows[e]], 1);
+  }
+  for (int k = tid; k < n_short; k += NT) {  // rank by counting; no sort needed at these sizes
+    const int dk = tmp[k];
+    int r = 0;
+    for (int i = 0; i < n_short; ++i) {
+      const int di = tmp[i];
+      r += (di > dk) || (di == dk && i < k);
+    }
+    vperm[r] = (uint16_t)k;
+  }
+  __syncthreads();
+  uint16_t* cinv = srp;  // window row -> label, until the row pointers are built
+  for (int j = tid; j < nr; j += NT) {
+    const int dj = rc[j];
+    int r = 0;
+    for (int i = 0; i < nr; ++i) {
+      const int di = rc[i];
+      r += (di > dj) || (di == dj && i < j);
+    }
+    cperm[r] = (uint16_t)j;
+    cinv[j] = (uint16_t)r;
+  }
+  for (int k = tid; k < n_short; k += NT) {
+    const int kr = vperm[k];
+    svd[k] = (uint8_t)tmp[kr];
+    sllr[k] = W.llr[sel[kr]];
+  }
+  __syncthreads();
+  for (int k = tid; k < n_short; k += NT) tmp[k] = svd[k];
   __syncthreads();
   if (warp == 0) {
     const int tot = warp_scan_excl(tmp, n_short, lane);
@@ -1552,17 +1603,18 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
   }
   __syncthreads();
   for (int k = tid; k <= n_short; k += NT) scp[k] = (uint16_t)tmp[k];
-  uint16_t* sef = (uint16_t*)(sm + L.s_efull);
   for (int k = tid; k < n_short; k += NT) {
-    const int c = sel[k];
+    const int c = sel[vperm[k]];
     int o = tmp[k];
     for (int e = W.col_ptr[c]; e < W.col_ptr[c + 1]; ++e, ++o) {
-      const int r = W.col_rows[e];
-      scr[o] = (uint16_t)r;
+      scr[o] = cinv[W.col_rows[e]];
       sef[o] = (uint16_t)e;  // the shortened edge keeps its full-window edge's weights
-      atomicAdd(&rc[r], 1);
     }
   }
+  for (int j = tid; j <= nr; j += NT) rc[j] = 0;
+  __syncthreads();
+  for (int k = tid; k < n_short; k += NT)
+    for (int e = scp[k]; e < scp[k + 1]; ++e) atomicAdd(&rc[scr[e]], 1);
   __syncthreads();
   if (warp == 0) {
     const int tot = warp_scan_excl(rc, nr, lane);
@@ -1576,28 +1628,6 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
       const int pos = atomicAdd(&rc[scr[e]], 1);
       sre[pos] = (uint32_t)e | ((uint32_t)k << 16);
     }
-  // processing order of the checks: descending degree, ties by index (rank
-  // by counting, no sort needed at these sizes)
-  uint16_t* cperm = (uint16_t*)(sm + L.s_cperm);
-  for (int j = tid; j < nr; j += NT) {
-    const int dj = srp[j + 1] - srp[j];
-    int r = 0;
-    for (int i = 0; i < nr; ++i) {
-      const int di = srp[i + 1] - srp[i];
-      r += (di > dj) || (di == dj && i < j);
-    }
-    cperm[r] = (uint16_t)j;
-  }
-  uint16_t* vperm = (uint16_t*)(sm + L.s_vperm);
-  for (int k = tid; k < n_short; k += NT) {
-    const int dk = svd[k];
-    int r = 0;
-    for (int i = 0; i < n_short; ++i) {
-      const int di = svd[i];
-      r += (di > dk) || (di == dk && i < k);
-    }
-    vperm[r] = (uint16_t)k;
-  }
   __syncthreads();
   return false;
 }
