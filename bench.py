@@ -33,6 +33,12 @@ import numpy as np  # noqa: E402
 CODE_KEY, ROUNDS, P_PHYS, K_GUESS = "144", 12, 0.003, 4
 METRIC = "[[144,12,12]] W=3 windows/s"
 OPS_PER_EDGE_ITER = 10  # FP32/ALU operations of Eq. (1)-(3) per edge and iteration
+# DRAM bytes (read + write) of one decode_shot_kernel launch of the default
+# workload (configured preset, 20000 shots per launch), from one ncu capture of
+# the current kernel (dram__bytes_read.sum + dram__bytes_write.sum; see
+# profiles/decode_shot_kernel_bb144_w3_p3e-3_configured.md).  Reported only for
+# that workload; per launch, like "achieved".
+TRAFFIC_PER_LAUNCH = {("configured", 20000): 2953216 + 0}
 
 
 def workload_name(preset_name):
@@ -709,7 +715,8 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * (2 * nwin + 1),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
-                         "frac": achieved / alu_peak, "traffic": None,
+                         "frac": achieved / alu_peak,
+                         "traffic": TRAFFIC_PER_LAUNCH.get((args.preset, B)),
                          "kernel": "decode_shot_kernel",
                          "work": f"{OPS_PER_EDGE_ITER} ops x {edge_iters} edge-iterations in "
                                  f"{nwin} launches",
