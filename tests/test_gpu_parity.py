@@ -312,6 +312,27 @@ def test_code_capacity_bit_exact(key, pd, ps, mode):
               capacity=(pd, ps))
 
 
+# a [[18,4]] bivariate-bicycle code (l = m = 3, A = 1 + y + y^2, B = 1 + y + x):
+# windows of 18 / 27 columns and 9 / 18 checks
+TINY18 = dict(name="[[18,4]]", n=18, k=4, l=3, m=3, A=[(0, 0), (0, 1), (0, 2)], B=[(0, 0), (0, 1), (1, 0)])
+
+
+@pytest.mark.parametrize("ps,mode", [(0.0, 1), (0.02, 2), (0.0, 2)])
+def test_tiny_windows_bit_exact(monkeypatch, ps, mode):
+    """Windows of fewer than 256 columns (the small network of the ranking
+    sort) and fewer checks than a warp round, in both launch shapes; path
+    mode runs 6 paths on two clusters of 4 CTAs, two of them idle."""
+    from paper_2403_18901_gb300.workloads import CAPACITY
+    monkeypatch.setitem(CODES, "tiny18", TINY18)
+    params = dict(CAPACITY, k_guess=2, side_max=4, d_max_main=12, d_max_other=8)
+    if mode == 2:
+        d = qdec.Dem(TINY18, 0.05, 0, capacity=(0.05, ps))
+        info = qdec.Decoder(d, params, max_shots=4).launch_info(0)
+        assert info["path_cluster"] == 4 and info["path_ctas_per_shot"] == 8
+    _pipeline("tiny18", 0, 0.05, params, n=200 if mode == 1 else 40, seed=18_004, trace_windows=(0,), mode=mode,
+              capacity=(0.05, ps))
+
+
 def test_bb72_2000_shots_bit_exact():
     """[[72,12,6]], 6 rounds, p = 0.003, 2000 seeded shots (seed 72003):
     corrections of every window, committed syndromes, predictions and failures."""
