@@ -206,6 +206,17 @@ __host__ __device__ inline int lanes_per_check(int threads, int n_checks) {
   return t;
 }
 
+// Lanes per check of a decision path run by a whole CTA: the most (<= 8) that
+// keep the check pass within two rounds of threads / lanes checks.  Checks
+// come in descending degree, so the first round holds the heavy ones, whose
+// edges the extra lanes split (measured on [[144]] (3,1) windows, 216 checks,
+// 512 threads: 1.18 / 1.02 / 1.19 ms per window with 2 / 4 / 8 lanes).
+__host__ __device__ inline int path_lanes_per_check(int threads, int n_checks) {
+  int t = 1;
+  while (t < 8 && 2 * (threads / (2 * t)) >= n_checks) t <<= 1;
+  return t;
+}
+
 // lexicographic (value, index) minimum over the warp
 __device__ __forceinline__ void warp_argmin(float& v, int& k) {
 #pragma unroll
@@ -624,6 +635,72 @@ struct PathOut {
   long long shot;
 };
 
+// Check-node update of Eq. (1) over the active VNs of one decision path, TPC
+// lanes per check (a template parameter, so that the loops and the group
+// reduction are unrolled for it); checks in label order (descending static
+// degree): the lanes of a round loop alike.  Each check also takes the parity
+// of its active VNs' hard decisions (Eq. (4)) from the posteriors it reads:
+// for it >= 2 this pass is the convergence test H e = s of the previous
+// iteration (Sec. II-A).  Returns whether this lane saw an unsatisfied check.
+template <bool LW, int TPC>
+__device__ __forceinline__ bool check_pass(const KParams& P, const ShortG& G, const Slot& B, int R, int S, bool first,
+                                           int tw, long long& visits) {
+  const int nr = G.nr, sub = R & (TPC - 1);
+  const int nr_rounds = (nr + S / TPC - 1) / (S / TPC) * (S / TPC);
+  bool unsat = false;
+  for (int j0 = R / TPC; j0 < nr_rounds; j0 += S / TPC) {
+    const int j = j0 < nr ? j0 : nr - 1;
+    const int d = j0 < nr ? B.deg[j] : 0;
+    if (TPC == 1 && d == 0) {  // no shuffle partner waits for this lane
+      if (j0 < nr) unsat |= bit_of(B.sp, j) != 0u;
+      continue;
+    }
+    const CNState oc = B.cns[j];
+    float m1 = CUDART_INF_F, m2 = CUDART_INF_F;
+    int am = 0xFFFF;
+    uint32_t neg = 0, hp = 0;
+    // one row entry; the (min1, min2) pair and so every message do not
+    // depend on the order in which a check sees its inputs
+    auto take = [&](uint32_t ent, float pv, uint32_t sg) {
+      if (pv != pv) return;  // stale message of a decimated VN
+      hp ^= pv <= 0.0f;
+      const int e = (int)(ent & 0xFFFFu);
+      ++visits;
+      // the previous iteration's multiplier, only when there was one (tw >= 1)
+      const float wprev = (LW && !first) ? edge_weight(G.wts, G.wT, G.wE, P.alpha, tw, G.efull[e]) : P.alpha;
+      const float v = first ? pv : clipf(__fsub_rn(pv, c2v<LW>(wprev, P.clip, oc, e, sg)), P.clip);
+      const float a = fabsf(v);
+      if (a < m1) {
+        m2 = m1;
+        m1 = a;
+        am = e;
+      } else if (a < m2) {
+        m2 = a;
+      }
+      const uint32_t sgn = v < 0.0f;
+      neg ^= sgn;
+      B.sign[e] = (uint8_t)sgn;
+    };
+    const int qe = d ? (int)(oc.pad >> 16) : 0;
+    for (int q = (d ? (int)(oc.pad & 0xFFFFu) : 0) + 2 * sub; q < qe; q += 2 * TPC) {
+      const bool two = q + 1 < qe;
+      const uint32_t e0 = G.rowent[q], e1 = two ? G.rowent[q + 1] : e0;
+      const float p0 = B.post[e0 >> 16], p1 = B.post[e1 >> 16];
+      const uint32_t s0 = B.sign[e0 & 0xFFFFu], s1 = B.sign[e1 & 0xFFFFu];
+      take(e0, p0, s0);
+      if (two) take(e1, p1, s1);
+    }
+    if (TPC > 1) {
+      group_min2(m1, m2, am, neg, TPC);
+      for (int off = TPC >> 1; off; off >>= 1) hp ^= __shfl_xor_sync(FULL, hp, off);
+    }
+    if (sub == 0 && j0 < nr) unsat |= (hp ^ bit_of(B.sp, j)) != 0u;
+    if (sub == 0 && d > 0)
+      B.cns[j] = cn_store<LW>(P.alpha, P.clip, m1, m2, am, neg ^ bit_of(B.sp, j), d == 1, oc.pad);
+  }
+  return unsat;
+}
+
 // One decision path of Alg. 2 on the shortened window, run by group g.
 // LW: learned per-edge weights instead of alpha (compiled separately so the
 // plain decoder carries no weight lookups).
@@ -632,8 +709,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
                          const PathOut& out, int dmx) {
   const int nr = G.nr, ns = G.ns, R = g.rank, S = g.size;
   // one lane per check for a warp; small lane groups per check for a CTA
-  const int tpc = Grp::kWarp ? 1 : lanes_per_check(S, nr), sub = R & (tpc - 1);
-  const int nr_rounds = (nr + S / tpc - 1) / (S / tpc) * (S / tpc);
+  const int tpc = Grp::kWarp ? 1 : path_lanes_per_check(S, nr);
   // Fig. 2: main branch (id 0), tree branches, side branches (split > 0),
   // which keep the main-branch thresholds up to and including their split
   const int split = path_split(P, id);
@@ -673,61 +749,15 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
     depth = D;
     PA = main_rules(D) ? P.pa_main : P.pa_other;  // read by this step's history flags
     for (int it = 1; it <= P.ips; ++it) {
-      // ---- check-node update, Eq. (1), over active VNs; tpc lanes per check ----
-      // checks in label order (descending static degree): the lanes of a round loop alike.
-      // Each check also takes the parity of its active VNs' hard decisions
-      // (Eq. (4)) from the posteriors it reads: for it >= 2 this pass is the
-      // convergence test H e = s of the previous iteration (Sec. II-A).
-      bool unsat = false;
-      for (int j0 = R / tpc; j0 < nr_rounds; j0 += S / tpc) {
-        const int j = j0 < nr ? j0 : nr - 1;
-        const int d = j0 < nr ? B.deg[j] : 0;
-        if (tpc == 1 && d == 0) {  // no shuffle partner waits for this lane
-          if (j0 < nr) unsat |= bit_of(B.sp, j) != 0u;
-          continue;
-        }
-        const CNState oc = B.cns[j];
-        float m1 = CUDART_INF_F, m2 = CUDART_INF_F;
-        int am = 0xFFFF;
-        uint32_t neg = 0, hp = 0;
-        // one row entry; the (min1, min2) pair and so every message do not
-        // depend on the order in which a check sees its inputs
-        auto take = [&](uint32_t ent, float pv, uint32_t sg) {
-          if (pv != pv) return;  // stale message of a decimated VN
-          hp ^= pv <= 0.0f;
-          const int e = (int)(ent & 0xFFFFu);
-          ++visits;
-          // the previous iteration's multiplier, only when there was one (tw >= 1)
-          const float wprev = (LW && !first) ? edge_weight(G.wts, G.wT, G.wE, P.alpha, tw, G.efull[e]) : P.alpha;
-          const float v = first ? pv : clipf(__fsub_rn(pv, c2v<LW>(wprev, P.clip, oc, e, sg)), P.clip);
-          const float a = fabsf(v);
-          if (a < m1) {
-            m2 = m1;
-            m1 = a;
-            am = e;
-          } else if (a < m2) {
-            m2 = a;
-          }
-          const uint32_t sgn = v < 0.0f;
-          neg ^= sgn;
-          B.sign[e] = (uint8_t)sgn;
-        };
-        const int qe = d ? (int)(oc.pad >> 16) : 0;
-        for (int q = (d ? (int)(oc.pad & 0xFFFFu) : 0) + 2 * sub; q < qe; q += 2 * tpc) {
-          const bool two = q + 1 < qe;
-          const uint32_t e0 = G.rowent[q], e1 = two ? G.rowent[q + 1] : e0;
-          const float p0 = B.post[e0 >> 16], p1 = B.post[e1 >> 16];
-          const uint32_t s0 = B.sign[e0 & 0xFFFFu], s1 = B.sign[e1 & 0xFFFFu];
-          take(e0, p0, s0);
-          if (two) take(e1, p1, s1);
-        }
-        if (tpc > 1) {
-          group_min2(m1, m2, am, neg, tpc);
-          for (int off = tpc >> 1; off; off >>= 1) hp ^= __shfl_xor_sync(FULL, hp, off);
-        }
-        if (sub == 0 && j0 < nr) unsat |= (hp ^ bit_of(B.sp, j)) != 0u;
-        if (sub == 0 && d > 0)
-          B.cns[j] = cn_store<LW>(P.alpha, P.clip, m1, m2, am, neg ^ bit_of(B.sp, j), d == 1, oc.pad);
+      // ---- check-node update, Eq. (1), and the previous iteration's H e = s ----
+      bool unsat;
+      if constexpr (Grp::kWarp) {
+        unsat = check_pass<LW, 1>(P, G, B, R, S, first, tw, visits);
+      } else {
+        if (tpc == 8) unsat = check_pass<LW, 8>(P, G, B, R, S, first, tw, visits);
+        else if (tpc == 4) unsat = check_pass<LW, 4>(P, G, B, R, S, first, tw, visits);
+        else if (tpc == 2) unsat = check_pass<LW, 2>(P, G, B, R, S, first, tw, visits);
+        else unsat = check_pass<LW, 1>(P, G, B, R, S, first, tw, visits);
       }
       if (!g.any(unsat) && it >= 2) {  // the previous iteration's decisions satisfy H e = s
         status = BR_CONVERGED;
