@@ -161,9 +161,12 @@ qd_status qd_sample_shots(const qd_dem* dem, uint64_t seed, uint64_t shot_offset
 
 /*
  * Prepare the (W,F) window matrices (Eq. (8)) and the GPU launch plan for
- * batches of up to max_shots shots.  Allocates all device scratch.  Errors:
- * QD_EINVAL for bad parameters, QD_EUNSUPPORTED when iters_per_step < 4,
- * k_guess > 5, or a window too large for shared memory.
+ * batches of up to max_shots shots.  Allocates all device scratch (windows
+ * whose pre-BP scratch or path slots exceed shared memory get a region in
+ * global memory).  Errors: QD_EINVAL for bad parameters or a window with
+ * 2^15 or more rows or columns (or 65535 edges); QD_EUNSUPPORTED when
+ * iters_per_step < 4, k_guess > 5, or a window whose persistent part alone
+ * exceeds shared memory.
  */
 qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* params, int64_t max_shots,
                             qd_decoder** out);
