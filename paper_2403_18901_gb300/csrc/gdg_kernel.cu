@@ -1175,6 +1175,9 @@ __device__ __forceinline__ uint32_t cl_ld_u8(unsigned a) {
   asm volatile("ld.shared::cluster.u8 %0, [%1];" : "=h"(v) : "r"(a));
   return v;
 }
+__device__ __forceinline__ void cl_st_f32(unsigned a, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
 __device__ __forceinline__ void cl_st_u32(unsigned a, uint32_t v) {
   asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
@@ -1189,17 +1192,17 @@ __device__ __forceinline__ CNState cl_ld_cns(unsigned a) {
 // a2 split over the CTAs of a cluster (path mode, one cluster per shot): CTA
 // r owns the r-th slice of the checks and of the variables, runs the check
 // pass of Eq. (1) for its checks and the variable pass of Eq. (2)-(3) for its
-// variables, and reads the inputs it does not own (posteriors in the check
-// pass; check states and signs in the variable pass) from their owners'
-// shared memory.  Two cluster barriers per iteration separate the passes, so
-// every value read was written in the pass before.  The arithmetic of every
-// message and posterior is that of the single-CTA loop.  At the end every
-// CTA holds the whole posterior and ranking key.  A remote load costs a round
-// trip of ~1200 cycles (a cluster barrier ~470), so each pass makes one: a
-// check's inputs and a variable's messages are requested together, and the
-// per-CTA "unsatisfied" flags are pushed to every CTA before the barrier
-// rather than read remotely after it.  Returns t as the loop leaves it; conv
-// and t_conv as in the caller.
+// variables.  A remote load costs a round trip of ~1200 cycles (a cluster
+// barrier ~470), so values travel the cheap way: each CTA pushes its
+// posteriors (and ranking keys) and its "unsatisfied" flag into every CTA's
+// shared memory before the barrier that ends the pass, and the check pass
+// reads them locally; the variable pass requests a variable's check states
+// and signs from their owners in one round trip.  Two cluster barriers per
+// iteration separate the passes, so every value read was written in the pass
+// before, and after the last one no CTA touches another's shared memory.
+// The arithmetic of every message and posterior is that of the single-CTA
+// loop; at the end every CTA holds the whole posterior and key.  Returns t as
+// the loop leaves it; conv and t_conv as in the caller.
 template <bool LW>
 __device__ int prebp_cluster(const DecodeArgs& A, const WinDev& W, const WinDev& Wg, char* sm, char* U,
                              const uint32_t* sbits, bool& conv, int& t_conv) {
@@ -1215,9 +1218,9 @@ __device__ int prebp_cluster(const DecodeArgs& A, const WinDev& W, const WinDev&
   // flags[8 * parity + c]: CTA c found an unsatisfied check (in the reduction
   // scratch of the path phase, idle until the pre-BP ends)
   int* flags = (int*)(sm + L.red);
-  // slices: owner(x) = floor(x / slice) = umulhi(x, ceil(2^32 / slice)), exact for x, slice < 2^16
+  // slices; the owner of check j is floor(j / sc) = umulhi(j, ceil(2^32 / sc)), exact for j, sc < 2^16
   const int sc = (nr + (int)C - 1) / (int)C, sv = (nc + (int)C - 1) / (int)C;
-  const unsigned mc = (unsigned)((0x100000000ull + sc - 1) / sc), mv = (unsigned)((0x100000000ull + sv - 1) / sv);
+  const unsigned mc = (unsigned)((0x100000000ull + sc - 1) / sc);
   const int jb = min(nr, (int)r * sc), je = min(nr, jb + sc);
   const int ib = min(nc, (int)r * sv), ie = min(nc, ib + sv);
   const int tpc = lanes_per_check(NT, max(1, je - jb)), sub = tid & (tpc - 1);
@@ -1246,7 +1249,7 @@ __device__ int prebp_cluster(const DecodeArgs& A, const WinDev& W, const WinDev&
           pv[u] = 0.0f;
           sg[u] = 0u;
           if (q + u < end) {
-            pv[u] = (t == 1) ? Wg.llr[i] : cl_ld_f32(cl_map(&post[i], __umulhi(i, mv)));
+            pv[u] = (t == 1) ? Wg.llr[i] : post[i];
             sg[u] = sign[e];
           }
         }
@@ -1312,6 +1315,8 @@ __device__ int prebp_cluster(const DecodeArgs& A, const WinDev& W, const WinDev&
           }
       }
       post[i] = p;
+      for (unsigned c = 0; c < C; ++c)  // every CTA reads the whole posterior in its check pass
+        if (c != r) cl_st_f32(cl_map(&post[i], c), p);
       if (kacc) {
         float kv;
         if (t == tk0) {
@@ -1327,34 +1332,15 @@ __device__ int prebp_cluster(const DecodeArgs& A, const WinDev& W, const WinDev&
           kv = __fadd_rn(key[i], p);
         }
         key[i] = kv;
+        for (unsigned c = 0; c < C; ++c)
+          if (c != r) cl_st_f32(cl_map(&key[i], c), kv);
       }
     }
-    cl_sync();  // posteriors of pass t
+    cl_sync();  // posteriors (and keys) of pass t, in every CTA
   }
-  // the whole posterior and key in every CTA, then no CTA reuses its shared
-  // memory while another may still read it
-  for (int i0 = tid; i0 < nc; i0 += 4 * NT) {  // four round trips in flight
-    float pv[4], kv[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u * NT;
-      const unsigned o = i < nc ? __umulhi((unsigned)i, mv) : r;
-      pv[u] = kv[u] = 0.0f;
-      if (o != r) {
-        pv[u] = cl_ld_f32(cl_map(&post[i], o));
-        kv[u] = cl_ld_f32(cl_map(&key[i], o));
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u * NT;
-      if (i < nc && __umulhi((unsigned)i, mv) != r) {
-        post[i] = pv[u];
-        key[i] = kv[u];
-      }
-    }
-  }
-  cl_sync();
+  // every CTA holds the whole posterior and key: the last variable pass
+  // pushed them before the barrier that ended the loop, and no CTA touches
+  // another's shared memory after it
   return t;
 }
 
