@@ -710,8 +710,8 @@ def main():
             "latency_ms": {"p50": p50, "p99": p99, "windows": n_lat,
                            "mode": "1 shot per window step (decode + commit, one CUDA graph); path mode: "
                                    "one 512-thread CTA per decision path, the shot's "
-                                   f"{ldec.launch_info(1)['path_ctas_per_shot']} CTAs in clusters of "
-                                   f"{ldec.launch_info(1)['path_cluster']} that split the pre-BP"},
+                                   f"{ldec.launch_info(0)['path_ctas_per_shot']} CTAs in clusters of "
+                                   f"{ldec.launch_info(0)['path_cluster']} that split the pre-BP"},
             "paper_context": {"worst_case_ms_per_window": 3.0,
                               "hardware": "Intel i9-13900K, multi-threaded"},
             "e2e": {"value": B * nwin / e2e_s, "unit": "windows/s", "h2d_bytes_per_step": h2d,
