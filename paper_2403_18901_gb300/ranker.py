@@ -14,7 +14,6 @@ MMAs inside the decode kernel.
 Every numerical step runs in libqdec; torch provides device memory and
 streams.
 """
-import numpy as np
 import torch
 
 from . import qdec

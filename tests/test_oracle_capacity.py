@@ -16,7 +16,6 @@ noise": [H_X | I] with a virtual column per check).
 import math
 
 import numpy as np
-import pytest
 
 from gf2 import rank
 from oracle import oracle as O
