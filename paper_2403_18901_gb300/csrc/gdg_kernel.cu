@@ -3,26 +3,32 @@
 // decode, per shot:
 //   a1  window syndrome: bits [row0, row0 + n_rows) of the shot's detectors
 //   a2  pre-BP: n_pre flooding min-sum iterations on the full window
-//       (Eq. (1)-(4)), whole CTA; check node j by one warp, variable node i
-//       by one thread; early stop when H e = s (Sec. II-A)
+//       (Eq. (1)-(4)); a check node by one lane (shot mode) or a lane group
+//       (path mode), a variable node by one thread; early stop when H e = s
+//       (Sec. II-A), tested inside the next check pass
 //   a3  ranking key ((h0+h1)+h2)+h3 of the last four posteriors, bitonic sort
 //       of (key, column) ascending, first 2w' columns kept (Sec. III); the
-//       shortened matrix is rebuilt in shared memory
-//   a4-a7 GDG decision paths (Alg. 2 on the 2^k tree): BP steps of
-//       iters_per_step iterations, SELECT-VN (Alg. 1) with aggressive
-//       decimation (Alg. 3), guess value by the path id, peeling
+//       shortened matrix is rebuilt in shared memory with its checks and
+//       columns numbered in processing order (descending degree)
+//   a4-a7 GDG decision paths (Alg. 2 on the 2^k tree and the side branches of
+//       Fig. 2): BP steps of iters_per_step iterations, SELECT-VN (Alg. 1)
+//       with aggressive decimation (Alg. 3), guess value by the path id,
+//       peeling
 //   a8  minimum path metric Eq. (5) over converged paths, ties to the lowest id
 //
 // Two launch shapes run the same path code:
-//   shot mode (throughput): persistent CTAs of 8 warps take shots from a work
-//     counter; after the CTA-wide pre-BP the warps take decision paths from a
-//     shared-memory queue, path 0 (the longest, D_max 25) first, one warp per
+//   shot mode (throughput): persistent CTAs of up to 8 warps take shots from
+//     a work counter; after the CTA-wide pre-BP the warps take decision paths
+//     from a shared-memory queue, path 0 (the longest) first, one warp per
 //     path;
-//   path mode (latency, small batches): one CTA per (shot, path); every CTA
-//     repeats the cheap pre-BP and ranking, runs its one path with all its
-//     threads, stores the result in global scratch, and the last CTA of the
-//     shot to arrive (atomic counter, no waiting) picks the winner.
-// Every wait is a CTA or warp barrier; nothing spins.
+//   path mode (latency, small batches): one CTA per (shot, path); the path
+//     CTAs of a shot form a thread-block cluster that splits the pre-BP over
+//     distributed shared memory, each CTA then ranks, shortens and runs its
+//     one path with all its threads, stores the result in global scratch,
+//     and the last CTA of the shot to arrive (atomic counter, no waiting)
+//     picks the winner.
+// Every wait is a CTA, warp or cluster barrier, except the bulk-copy
+// mbarrier, whose wait is bounded.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
