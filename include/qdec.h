@@ -455,7 +455,9 @@ qd_status qd_adam_step(float* w, const float* g, float* m1, float* m2, int64_t n
  * 0 automatic (default): path mode for batches that leave most SMs idle,
  * otherwise shot mode; 1 shot mode: persistent CTAs, one warp per decision
  * path; 2 path mode: one CTA per (shot, decision path) for the lowest
- * latency, at most 64 shots per call (larger batches fall back to shot mode);
+ * latency, the path CTAs of a shot launched as a thread-block cluster (up to
+ * 8 CTAs, padded with idle CTAs to whole clusters) that splits the shot's
+ * pre-BP, at most 64 shots per call (larger batches fall back to shot mode);
  * 3 shot mode with every CTA's pre-BP scratch and path states in global
  * memory (L2 / HBM) instead of shared memory -- the shape a window too large
  * for shared memory always uses (chosen at decoder creation, which allocates
