@@ -11,6 +11,7 @@
 // explicit form performs, so every value is bit-identical to it.  All FP32
 // operations are __fadd_rn / __fsub_rn / __fmul_rn (never contracted).
 #pragma once
+#include <cstddef>
 #include <cstdint>
 
 namespace qd {
