@@ -2109,6 +2109,8 @@ cudaError_t launch_decode(int mode, int grid, int threads, size_t smem, cudaStre
                           uglob, ubytes,   cps};
   const bool lw = W.wts != nullptr;
   if (mode == 1) {  // one cluster of `cluster` CTAs shares each shot's pre-BP
+    // every path needs its CTA, and a cluster never spans two shots
+    if (cluster < 1 || cps < P.nb || cps % cluster || grid % cps) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute at[1];
     cfg.gridDim = dim3((unsigned)grid);
