@@ -720,7 +720,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
   // which keep the main-branch thresholds up to and including their split
   const int split = path_split(P, id);
   const int d_reinit = path_reinit(P, id, split);
-  const int dmax = id == 0 ? P.dmax_main : (split ? split + (P.dmax_other - P.k) : P.dmax_other);
+  const int dmax = path_dmax(P, id, split);
   auto main_rules = [&](int D) { return id == 0 || (split && D <= split); };
   float PA = main_rules(1) ? P.pa_main : P.pa_other;
   for (int k = R; k < ns; k += S) {

@@ -63,8 +63,18 @@ __host__ __device__ inline int path_reinit(const KParams& P, int id, int split) 
   return (id >= 1 && (id & 1) && P.k >= 1) ? P.k : 0;
 }
 
+// D_max of path `id` with side-branch split `split` (Fig. 2): the main
+// branch's own; a side branch runs as many steps past its split as a tree
+// branch runs past depth k.
+__host__ __device__ inline int path_dmax(const KParams& P, int id, int split) {
+  return id == 0 ? P.dmax_main : (split ? split + (P.dmax_other - P.k) : P.dmax_other);
+}
+
 // Shot-mode queue order: the main branch, side branches from the deepest
-// split down, then the tree branches (longest paths first).
+// split down, then the tree branches -- the longest paths first when the main
+// branch's D_max is the largest (the circuit-level presets; the code-capacity
+// tree's deepest side branches outlast its main branch).  The order only
+// schedules the paths; every result is kept by path id.
 __host__ __device__ inline int path_at(const KParams& P, int pos) {
   const int nside = P.nb - (1 << P.k);
   if (pos == 0) return 0;

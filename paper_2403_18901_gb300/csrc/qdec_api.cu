@@ -400,8 +400,8 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
   k.side_max = p->side_max;
   k.reinit = p->reinit_on_split != 0;
   k.nb = (1 << p->k_guess) + (p->side_max > p->k_guess ? p->side_max - p->k_guess : 0);
-  dec->dmx = std::max(p->d_max_main, p->d_max_other);
-  if (p->side_max > 0) dec->dmx = std::max(dec->dmx, p->side_max + p->d_max_other - p->k_guess);
+  dec->dmx = 0;  // the deepest path, by the kernels' own rule (trace sizing)
+  for (int id = 0; id < k.nb; ++id) dec->dmx = std::max(dec->dmx, qd::path_dmax(k, id, qd::path_split(k, id)));
 
   int dev = 0, optin = 0;
   QD_CK(cudaGetDevice(&dev));

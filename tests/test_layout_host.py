@@ -1,8 +1,9 @@
-"""Host check of the decoder's shared-memory layout: make_layout (the one
-definition shared by the host plan and the kernels) gives 16-byte aligned,
-non-overlapping regions that fit, for the windows of every code and window
-shape the tests and the bench decode (tests/layout_check.cpp states the
-invariants)."""
+"""Host checks of definitions the kernels share with the host, built with g++
+from gdg_kernel.cuh: the shared-memory layout (make_layout gives 16-byte
+aligned, non-overlapping regions that fit, for the windows of every code and
+window shape the tests and the bench decode; tests/layout_check.cpp states
+the invariants) and the decision-path schedule (path_at, path_split,
+path_reinit, path_dmax against the oracle's tree; tests/tree_check.cpp)."""
 import os
 import shutil
 import subprocess
@@ -60,3 +61,57 @@ def test_layouts_are_aligned_disjoint_and_fit(checker, key, rounds, W, F, capaci
                     args = [str(x) for x in (*dims, nb, nslots, stage, ranker)]
                     r = subprocess.run([checker] + args, capture_output=True, text=True)
                     assert r.returncode == 0 and r.stdout.strip() == "ok", (args, r.stdout)
+
+
+# ---- the decision-path schedule (path_split, path_reinit, path_at, path_dmax) ----
+
+@pytest.fixture(scope="module")
+def tree_checker(tmp_path_factory):
+    cxx = shutil.which("g++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    exe = str(tmp_path_factory.mktemp("tree") / "tree_check")
+    subprocess.run([cxx, "-std=c++17", "-O1", "-Wall", "-o", exe, os.path.join(HERE, "tree_check.cpp")],
+                   check=True, capture_output=True)
+    return exe
+
+
+def _oracle_paths(params):
+    import ctypes as C
+    P = O.make_params(params, None, None)
+    return O.lib().qdo_n_paths(C.byref(P)), O.lib().qdo_path_dmax_all(C.byref(P))
+
+
+TREES = [("configured", dict(k_guess=k)) for k in range(1, 6)] + [
+    ("paper", dict(k_guess=3)), ("paper", dict(k_guess=4)), ("paper", dict(k_guess=4, reinit_on_split=1)),
+    ("paper", dict(k_guess=5, d_max_main=40, d_max_other=25, side_max=20, n_pre=16)),
+    ("configured", dict(k_guess=4, reinit_on_split=1)), ("capacity", dict())]
+
+
+@pytest.mark.parametrize("pname,over", TREES)
+def test_path_schedule_matches_the_oracle_tree(tree_checker, pname, over):
+    """The kernels' queue visits every path once, main branch first; path
+    counts and the deepest D_max equal the oracle's; splits and message
+    restarts follow the Fig. 2 reading (id 1 splits at depth k, ids 2^k..
+    at k + 1 .. side_max; restarts at a side branch's split and at depth k
+    for odd tree ids)."""
+    from paper_2403_18901_gb300.workloads import CAPACITY, preset
+    params = dict(CAPACITY, **over) if pname == "capacity" else preset(pname, **over)
+    nb, dmax_all = _oracle_paths(params)
+    k, side, reinit = params["k_guess"], params["side_max"], int(params["reinit_on_split"])
+    args = [str(x) for x in (k, side, reinit, nb, params["d_max_main"], params["d_max_other"])]
+    r = subprocess.run([tree_checker] + args, capture_output=True, text=True, check=True)
+    rows = [tuple(int(v) for v in line.split()) for line in r.stdout.strip().splitlines()]
+    ids = [row[1] for row in rows]
+    assert sorted(ids) == list(range(nb)) and ids[0] == 0
+    assert max(row[4] for row in rows) == dmax_all
+    nt = 1 << k
+    for _, pid, split, rst, dmax in rows:
+        if pid >= nt:
+            assert split == k + 1 + (pid - nt) and split <= side
+        else:
+            assert split == (k if (side > 0 and pid == 1) else 0)
+        want_rst = (split if split else (k if pid % 2 == 1 else 0)) if reinit else 0
+        assert rst == want_rst
+        assert dmax == (params["d_max_main"] if pid == 0 else
+                        (split + params["d_max_other"] - k if split else params["d_max_other"]))
