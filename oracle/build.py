@@ -21,11 +21,17 @@ def build(force: bool = False) -> str:
             return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", "-Wall", "-Wno-unused-function", "-o", tmp] + srcs + ["-lm"]
-    subprocess.run(cmd, check=True)
+    compile_lib(HERE, tmp)
     os.replace(tmp, LIB)
     return LIB
+
+
+def compile_lib(src_dir: str, out: str) -> None:
+    """gcc the oracle sources found in src_dir into the shared library out."""
+    srcs = [os.path.join(src_dir, s) for s in SOURCES]
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-Wall", "-Wno-unused-function", "-o", out] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
 
 
 if __name__ == "__main__":

@@ -454,6 +454,47 @@ static int select_vn(const graph_t* g, state_t* s, const qdo_params* P, int D, i
   return gsel;
 }
 
+/* Test access to Alg. 3 for one VN: its four-iteration history h (oldest
+ * first), depth D, main-branch flag and unsatisfied-neighbour count. */
+int qdo_agg_dec(const qdo_params* P, const float* h, int D, int main_branch, int n_unsat) {
+  float L = ((h[0] + h[1]) + h[2]) + h[3];
+  return agg_dec(P, h, L, D, main_branch, n_unsat);
+}
+
+/* Test access to one call of Alg. 1 (with Alg. 3 outside the low-error mode)
+ * on an explicit graph and path state: hist [4][nc] oldest first, whose
+ * newest row is also the current posterior deciding e_i (Eq. (4)); status
+ * [nc] (-1 active, else the decimated value) and synd [nr] = the current s'
+ * are updated with the aggressive decisions.  Returns g (-1: no candidate)
+ * and writes f and the number of aggressive decisions. */
+int qdo_select_vn(const qdo_params* P, int nr, int nc, const int* col_ptr, const int* col_rows,
+                  const float* hist, int8_t* status, uint8_t* synd, int D, int main_branch,
+                  int* f_out, int* n_agg) {
+  float* llr = calloc(nc > 0 ? nc : 1, sizeof(float));
+  graph_t g;
+  graph_init(&g, nr, nc, col_ptr, col_rows, llr);
+  free(llr);
+  state_t s;
+  state_alloc(&s, &g);
+  for (int i = 0; i < nc; ++i) {
+    for (int k = 0; k < 4; ++k) s.hist[k][i] = hist[(size_t)k * nc + i];
+    s.post[i] = hist[(size_t)3 * nc + i];
+    s.status[i] = status[i];
+  }
+  for (int j = 0; j < nr; ++j) {
+    s.sp[j] = synd[j];
+    s.deg[j] = 0;
+    for (int q = g.row_ptr[j]; q < g.row_ptr[j + 1]; ++q)
+      if (s.status[g.edge_col[g.row_edges[q]]] == -1) s.deg[j]++;
+  }
+  int gsel = select_vn(&g, &s, P, D, main_branch, 0, f_out, n_agg);
+  memcpy(status, s.status, nc);
+  memcpy(synd, s.sp, nr);
+  state_free(&s);
+  graph_free(&g);
+  return gsel;
+}
+
 /* Eq. (5) accumulated in double from the FP32 priors. */
 static double path_metric(const graph_t* g, const state_t* s) {
   double pm = 0.0;

@@ -96,8 +96,48 @@ def lib():
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.qdo_run_shots.argtypes = [C.c_void_p, P(QdoParams), C.c_void_p, C.c_void_p,
                                     C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        declare_select(L)
         _lib = L
     return _lib
+
+
+def declare_select(L):
+    """Argument types of the SELECT-VN / AGG-DEC test-access calls of an
+    oracle library handle (also used on rebuilt copies of the oracle)."""
+    L.qdo_agg_dec.argtypes = [C.POINTER(QdoParams), C.c_void_p, C.c_int, C.c_int, C.c_int]
+    L.qdo_select_vn.argtypes = [C.POINTER(QdoParams), C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                C.c_void_p, C.c_void_p]
+    return L
+
+
+def agg_dec(params, h, D, main_branch, n_unsat, lib_=None):
+    """Alg. 3 on one VN's four-iteration history h (oldest first): 1, 0 or -1."""
+    q = make_params(params)
+    hv = np.ascontiguousarray(h, np.float32)
+    assert hv.size == 4
+    return (lib_ or lib()).qdo_agg_dec(C.byref(q), _ptr(hv), int(D), int(main_branch), int(n_unsat))
+
+
+def select_vn(params, H, hist, status, synd, D, main_branch, lib_=None):
+    """One SELECT-VN call (Alg. 1, with Alg. 3 outside the low-error mode) on
+    the dense matrix H [nr][nc] with history hist [4][nc] (oldest first; the
+    newest row is the current posterior), status [nc] (-1 active) and current
+    syndrome synd [nr].  Returns (g, f, n_agg, status after, synd after)."""
+    H = np.asarray(H, np.uint8)
+    nr, nc = H.shape
+    cols = [np.nonzero(H[:, i])[0] for i in range(nc)]
+    ptr = np.cumsum([0] + [len(c) for c in cols]).astype(np.int32)
+    rows = (np.concatenate(cols) if nc else np.zeros(0)).astype(np.int32)
+    hv = np.ascontiguousarray(hist, np.float32).reshape(4, nc)
+    st = np.ascontiguousarray(status, np.int8).copy()
+    sp = np.ascontiguousarray(synd, np.uint8).copy()
+    f = C.c_int(-7)
+    nagg = C.c_int(-7)
+    q = make_params(params)
+    g = (lib_ or lib()).qdo_select_vn(C.byref(q), nr, nc, _ptr(ptr), _ptr(rows), _ptr(hv), _ptr(st),
+                                      _ptr(sp), int(D), int(main_branch), C.byref(f), C.byref(nagg))
+    return g, f.value, nagg.value, st, sp
 
 
 def _ptr(a):

@@ -161,6 +161,17 @@ int qdo_run_shots(const qdo_dem* d, const qdo_params* P, const uint32_t* det_bit
                   uint32_t* obs_pred, uint32_t* win_corr_words /* may be NULL */,
                   int corr_words_per_window);
 
+/* Test access to Alg. 3 (one VN: history h[4] oldest first, depth D, main
+ * branch flag, unsatisfied-neighbour count): returns 1, 0 or -1. */
+int qdo_agg_dec(const qdo_params* P, const float* h, int D, int main_branch, int n_unsat);
+/* Test access to one SELECT-VN call (Alg. 1, with Alg. 3 outside the
+ * low-error mode) on an explicit graph and path state: hist [4][nc] oldest
+ * first (the newest row is the current posterior); status [nc] and synd [nr]
+ * (s') are updated with the aggressive decisions.  Returns g or -1. */
+int qdo_select_vn(const qdo_params* P, int nr, int nc, const int* col_ptr, const int* col_rows,
+                  const float* hist, int8_t* status, uint8_t* synd, int D, int main_branch,
+                  int* f_out, int* n_agg);
+
 /* Number of decision paths (2^k tree + side branches) and the largest D_max. */
 int qdo_n_paths(const qdo_params* P);
 int qdo_path_dmax_all(const qdo_params* P);
