@@ -257,7 +257,7 @@ qd_status qd_decode_shots_host(qd_decoder* dec, const uint32_t* det_bits, const 
  * synchronisation cudaFree implies) would stall the stream, or a host
  * framework that owns all device memory and forbids the runtime allocator.
  * The paper has no counterpart; this is a packaging of qd_decode_windows
- * followed by qd_commit_and_slide.
+ * followed by qd_commit_and_slide, with the same results bit for bit.
  *
  * The window corrections and the work counter, which qd_decode_windows keeps
  * in caller or decoder buffers, live in one fixed array of
@@ -266,9 +266,15 @@ qd_status qd_decode_shots_host(qd_decoder* dec, const uint32_t* det_bits, const 
  * + 256 <= QD_STATIC_SCRATCH_BYTES (30839 shots for [[144,12,12]] with
  * (3,1) windows, 68 correction words per shot); larger batches return QD_EINVAL with the limit in the
  * message.
- *   det_bits     device [n_shots][det_words], updated in place (Eq. (10))
- *   obs_pred     device [n_shots], updated in place
- *   residue_fail device [n_shots], updated in place (Eq. (11))
+ *   det_bits     device [n_shots][det_words], updated in place as by
+ *                qd_commit_and_slide
+ *   obs_pred     device [n_shots], updated in place as by qd_commit_and_slide
+ *   residue_fail device [n_shots], updated in place as by qd_commit_and_slide
+ * The launch shape follows qd_decoder_set_launch exactly as qd_decode_windows
+ * does (path mode for small batches in mode 0 or on request in mode 2, within
+ * the same limits; global-memory path state in mode 3 or for windows too large
+ * for shared memory), using the buffers the decoder allocated at creation;
+ * the work counters add to the decoder's, read by qd_decoder_counters.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
  * capture.  All calls share the array and it keeps the previous call's

@@ -738,7 +738,7 @@ qd_status qd_decoder_reset_counters(qd_decoder* dec, qd_stream_t stream) {
 // QD_STATIC_SCRATCH_BYTES until the process exits.
 namespace {
 constexpr size_t kStaticScratchBytes = QD_STATIC_SCRATCH_BYTES;
-constexpr size_t kStaticHeader = 256;  // work counter + statistics, before the corrections
+constexpr size_t kStaticHeader = 256;  // the work counter, then padding to the corrections' alignment
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 std::mutex g_static_mu;
@@ -780,23 +780,36 @@ extern "C" qd_status qd_decode_commit_static(qd_decoder* dec, int k, uint32_t* d
   void* base = nullptr;
   if (qd_status st = static_scratch_address(&base)) return st;
   int* work = (int*)base;
-  long long* stats = (long long*)((char*)base + 64);
   uint32_t* corr = (uint32_t*)((char*)base + kStaticHeader);
   const WinGpu& g = dec->wins[k];
   cudaStream_t st = (cudaStream_t)stream;
-  // the array keeps the previous call's contents: the counters must restart at 0
-  QD_CK(cudaMemsetAsync(base, 0, kStaticHeader, st));
   const int dw = (dec->dem->h.n_det + 31) / 32;
   if (g.h.n_cols > 0) {
-    // the global union regions, when used, were allocated with the decoder
+    // the launch shape qd_decode_windows would take; every buffer it needs
+    // besides the corrections and the work counter was allocated with the
+    // decoder (path results and arrival counters, global union regions), and
+    // the work counters go to the decoder's own (qd_decoder_counters)
     const bool global = !g.fits || dec->launch_mode == 3;
-    const qd::Layout& L = global ? g.Lg : g.L;
-    const long long grid =
-        std::min<long long>(n_shots, (long long)dec->sm_count * (global ? g.grid_g : g.grid_per_sm));
-    QD_CK(qd::launch_decode(0, (int)grid, 32 * (global ? kShotWarps : g.shot_warps), global ? L.U : L.total, st,
-                            dec->kp, g.dv, L, det_bits, dw, n_shots, corr, dec->corr_words, nullptr, nullptr, 0,
-                            dec->dmx, dec->ns_max, work, stats, nullptr, nullptr, dec->sw_max,
-                            global ? dec->d_uscratch : nullptr, global ? L.total - L.U : 0));
+    bool path_mode = dec->launch_mode == 2;
+    if (dec->launch_mode == 0) path_mode = n_shots * 4 <= dec->sm_count;
+    if (path_mode && (n_shots > std::min<long long>(dec->max_shots, kPathModeMaxShots) || !g.path_fits || global))
+      path_mode = false;
+    if (path_mode) {
+      const int cps = (dec->kp.nb + g.pcl - 1) / g.pcl * g.pcl;
+      QD_CK(qd::launch_decode(1, (int)(n_shots * cps), kPathThreads, g.Lp.total, st, dec->kp, g.dv, g.Lp, det_bits,
+                              dw, n_shots, corr, dec->corr_words, nullptr, nullptr, 0, dec->dmx, dec->ns_max, nullptr,
+                              dec->d_counters, dec->d_path_res, dec->d_arrive, dec->sw_max, nullptr, 0, cps, g.pcl));
+    } else {
+      // the array keeps the previous call's contents: the work counter restarts at 0
+      QD_CK(cudaMemsetAsync(work, 0, sizeof(int), st));
+      const qd::Layout& L = global ? g.Lg : g.L;
+      const long long grid =
+          std::min<long long>(n_shots, (long long)dec->sm_count * (global ? g.grid_g : g.grid_per_sm));
+      QD_CK(qd::launch_decode(0, (int)grid, 32 * (global ? kShotWarps : g.shot_warps), global ? L.U : L.total, st,
+                              dec->kp, g.dv, L, det_bits, dw, n_shots, corr, dec->corr_words, nullptr, nullptr, 0,
+                              dec->dmx, dec->ns_max, work, dec->d_counters, nullptr, nullptr, dec->sw_max,
+                              global ? dec->d_uscratch : nullptr, global ? L.total - L.U : 0));
+    }
   }
   const int w = dec->dem->h.w;
   QD_CK(qd::launch_commit(st, g.h.n_commit, g.d_ccptr, g.d_ccdet, g.d_ccobs, dec->corr_words, corr, n_shots,

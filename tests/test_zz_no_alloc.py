@@ -45,20 +45,58 @@ def _run(dec, det0, n, use_static):
     return det.cpu().numpy(), pred.cpu().numpy(), resid.cpu().numpy()
 
 
-@pytest.mark.parametrize("key,R,k,n", [("144", 12, 4, 600), ("72", 6, 3, 513)])
-def test_static_scratch_matches_two_call_path(key, R, k, n):
+# (code, rounds, k, shots, launch mode): 0 = automatic (throughput shape at
+# these batch sizes), 2 = one CTA per decision path, 3 = path state in global
+# memory (the decoder's own union regions)
+CASES = [("144", 12, 4, 600, 0), ("72", 6, 3, 513, 0), ("144", 12, 4, 24, 2), ("72", 6, 3, 300, 3)]
+
+
+@pytest.mark.parametrize("key,R,k,n,mode", CASES)
+def test_static_scratch_matches_two_call_path(key, R, k, n, mode):
     dem = qdec.Dem(CODES[key], 0.003, R)
     dec = qdec.Decoder(dem, preset("configured", k_guess=k), max_shots=n)
+    dec.set_launch(mode)
     for seed in (11, 12):  # two calls in a row on different inputs
         det0, _ = dem.sample(seed=seed, shot_offset=0, n_shots=n)
+        dec.reset_counters()
         ref = _run(dec, det0, n, use_static=False)
+        c_ref = dec.counters()
+        dec.reset_counters()
         got = _run(dec, det0, n, use_static=True)
+        c_got = dec.counters()
         for a, b in zip(ref, got):
             assert (a == b).all()
+        # the same work, counted in the decoder's counters by both paths
+        assert list(c_ref) == list(c_got) and c_got[1] > 0 and c_got[4] == 0
     # and the same input twice through the static path
     again = _run(dec, det0, n, use_static=True)
     for a, b in zip(got, again):
         assert (a == b).all()
+
+
+def test_static_scratch_allocates_nothing():
+    dem = qdec.Dem(CODES["72"], 0.003, 6)
+    n = 256
+    dec = qdec.Decoder(dem, preset("configured", k_guess=3), max_shots=n)
+    det0, _ = dem.sample(seed=21, shot_offset=0, n_shots=n)
+    det = det0.clone()
+    pred = torch.zeros(n, dtype=torch.int32, device="cuda")
+    resid = torch.zeros(n, dtype=torch.int32, device="cuda")
+    # warm-up: the array's address is looked up once, and every kernel of the
+    # loop below (the copy included) is loaded before memory is measured
+    det.copy_(det0)
+    for k in range(dec.n_windows):
+        dec.decode_commit_static(k, det, n, pred, resid)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        det.copy_(det0)
+        for k in range(dec.n_windows):
+            dec.decode_commit_static(k, det, n, pred, resid)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0 and torch.cuda.memory_allocated() == alloc0
 
 
 def test_static_scratch_rejects_oversized_batches():
