@@ -86,6 +86,11 @@ typedef struct {
                          /* branches at D_split, odd tree ids at D = k) restarts  */
                          /* its messages there, mu = Lambda (the appendix's       */
                          /* multi-thread snapshots); 0: continuous messages.      */
+  int iters_first;       /* BP iterations of the first decimation step (D = 1);   */
+                         /* 0: iters_per_step.  With n_pre = 0 and shorten = 0    */
+                         /* this is the reading in which the initial BP run is    */
+                         /* GDG's own first step on the whole window; >= 4 on     */
+                         /* the GPU when set.                                     */
 } qd_gdg_params;
 
 typedef struct qd_dem qd_dem;

@@ -572,7 +572,10 @@ static void run_branch(const graph_t* g, const uint8_t* synd, const qdo_params* 
   }
   for (int D = 1; D <= dmax; ++D) {
     out->depth = D;
-    for (int it = 0; it < P->iters_per_step; ++it) {
+    /* READING: iters_first > 0 gives the first step its own length (the
+     * initial BP run as GDG's first step, without pre-BP or shortening) */
+    const int n_it = (D == 1 && P->iters_first > 0) ? P->iters_first : P->iters_per_step;
+    for (int it = 0; it < n_it; ++it) {
       bp_iteration(g, s, P->alpha, P->clip, ++tw);
       out->iters++;
       if (converged(g, s)) {

@@ -48,6 +48,7 @@ typedef struct {
                          /* at D_split = k .. side_max (0: the 2^k tree only) */
   int reinit_on_split;   /* 1: a path restarts its messages where it splits    */
                          /* off another (appendix, multi-thread snapshots)     */
+  int iters_first;       /* BP iterations of step D = 1 (0: iters_per_step)    */
   /* Learned weighted min-sum (no counterpart in the paper; alpha of Eq. (1)
    * replaced by w[t][e]): wts[k] is window k's array [wT][n_edges] over the
    * full-window edges (CSC order), or NULL for plain alpha.  Iteration t

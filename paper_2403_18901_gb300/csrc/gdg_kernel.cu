@@ -754,7 +754,8 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
   for (int D = 1; D <= dmax; ++D) {
     depth = D;
     PA = main_rules(D) ? P.pa_main : P.pa_other;  // read by this step's history flags
-    for (int it = 1; it <= P.ips; ++it) {
+    const int ips = (D == 1 && P.ips1 > 0) ? P.ips1 : P.ips;  // the first step may have its own length
+    for (int it = 1; it <= ips; ++it) {
       // ---- check-node update, Eq. (1), and the previous iteration's H e = s ----
       bool unsat;
       if constexpr (Grp::kWarp) {
@@ -771,8 +772,8 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
         goto done;
       }
       // ---- variable-node update, Eq. (2)-(3); history of Sec. IV-A ----
-      const bool hist = it > P.ips - 4;
-      const bool hist0 = it == P.ips - 3;
+      const bool hist = it > ips - 4;
+      const bool hist0 = it == ips - 3;
       // variables in label order (descending degree): the lanes of a round loop alike
       for (int k = R; k < ns; k += S) {
         if (B.status[k] != -1) continue;
@@ -792,7 +793,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
         if (e < ee) p = __fadd_rn(p, msg(e));
         B.post[k] = p;
         if (hist) {
-          if (P.rkq || P.dump) B.hq[4 * k + (it - (P.ips - 3))] = qhist(p);
+          if (P.rkq || P.dump) B.hq[4 * k + (it - (ips - 3))] = qhist(p);
           const uint8_t f = (uint8_t)((p <= 0.0f) | ((p < PA) << 1) | ((p > P.pc) << 2) | ((p > P.pd) << 3));
           if (hist0) {
             B.acc[k] = p;

@@ -24,6 +24,7 @@ struct KParams {
   int nb;        // decision paths: 2^k tree + side branches
   int side_max;  // side branches split off the main branch at D_split = k .. side_max (0: none)
   int reinit;    // 1: a path continuing from another's snapshot restarts its messages there
+  int ips1;      // BP iterations of the first decimation step (0: ips)
   // learned decimation ranker (NULL: the argmin of Alg. 1): rkq = the
   // grid-rounded W1[64][8], b1[64], W2[64], b2; rkb[t][lane] = the BF16 pair
   // (W1[8t + lane/4][2 (lane%4)], W1[8t + lane/4][2 (lane%4) + 1]), the B

@@ -361,10 +361,11 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
   QD_REQ(p->n_pre >= 0 && p->iters_per_step >= 1 && p->d_max_main >= 1 && p->d_max_other >= 1,
          "qd_decoder_create: bad iteration counts");
   QD_REQ(p->alpha > 0.0f && p->clip > 0.0f, "qd_decoder_create: alpha and clip must be positive");
-  if (p->iters_per_step < 4) {
-    set_error("qd_decoder_create: iters_per_step < 4 is not implemented on the GPU");
+  if (p->iters_per_step < 4 || (p->iters_first != 0 && p->iters_first < 4)) {
+    set_error("qd_decoder_create: iters_per_step or iters_first < 4 is not implemented on the GPU");
     return QD_EUNSUPPORTED;
   }
+  QD_REQ(p->iters_first >= 0, "qd_decoder_create: iters_first < 0");
   QD_REQ(p->side_max == 0 || (p->side_max >= p->k_guess && p->side_max <= 32),
          "qd_decoder_create: side_max must be 0 or in [k_guess, 32]");
   QD_REQ(p->d_max_other >= p->k_guess, "qd_decoder_create: d_max_other < k_guess");
@@ -390,6 +391,7 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
   k.pd = p->pd;
   k.n_pre = p->n_pre;
   k.ips = p->iters_per_step;
+  k.ips1 = p->iters_first;
   k.dmax_main = p->d_max_main;
   k.dmax_other = p->d_max_other;
   k.k = p->k_guess;

@@ -391,3 +391,14 @@ def test_window_too_large_for_shared_memory_bit_exact():
     union region through global memory on its own."""
     params = preset("configured", k_guess=2, p=0.002, W=6, F=1, d_max_main=12)
     _pipeline("288", 6, 0.002, params, n=8, seed=288_006, trace_windows=(0,), mode=1)
+
+
+@pytest.mark.parametrize("key,R,n,mode,tw", [("72", 6, 60, 1, (0, 2)), ("144", 12, 16, 1, (1,)),
+                                             ("144", 12, 8, 2, (0,))])
+def test_initial_bp_as_first_step_bit_exact(key, R, n, mode, tw):
+    """The second reading of "100 initial BP iterations": no pre-BP, no
+    shortening, GDG on the whole window with a first step of 100 iterations.
+    The [[144]] whole-window path states do not fit shared memory in the
+    throughput shape, so they run in global memory."""
+    params = preset("configured", k_guess=4 if key == "144" else 3, p=0.003, n_pre=0, shorten=0, iters_first=100)
+    _pipeline(key, R, 0.003, params, n=n, seed=int(key) * 1000 + 7, trace_windows=tw, mode=mode)
