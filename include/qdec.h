@@ -483,12 +483,29 @@ qd_status qd_decoder_set_launch(qd_decoder* dec, int mode);
 qd_status qd_decoder_launch_info(const qd_decoder* dec, int k, int out[8]);
 
 /* Counters summed over every decode since the last reset: out[0] pre-BP
- * edge-iterations, out[1] GDG edge-iterations, out[2] windows whose pre-BP
- * converged, out[3] windows that ran GDG, out[4] bulk (TMA) staging copies
- * whose bounded wait ran out (then copied with plain loads; expected 0).
- * Synchronous. */
+ * edge-iterations, out[1] GDG edge-iterations of every decision path run
+ * from the root as Alg. 2 defines it (a path resumed from a shared prefix,
+ * see qd_decoder_set_fork, counts the prefix as its own), out[2] windows
+ * whose pre-BP converged, out[3] windows that ran GDG, out[4] bulk (TMA)
+ * staging copies whose bounded wait ran out (then copied with plain loads;
+ * expected 0).  Synchronous. */
 qd_status qd_decoder_counters(qd_decoder* dec, long long out[5]);
+/* The first n (1..8) counters: out[0..4] as qd_decoder_counters, out[5] GDG
+ * edge-iterations the GPU executed (out[1] minus the shared prefixes it did
+ * not recompute), out[6..7] 0.  Synchronous. */
+qd_status qd_decoder_counters_ex(qd_decoder* dec, long long* out, int n);
 qd_status qd_decoder_reset_counters(qd_decoder* dec, qd_stream_t stream);
+
+/* Shared path prefixes in shot mode (on by default; no counterpart in the
+ * paper, whose threads snapshot the main branch's status only): decision
+ * paths that made the same decisions at depths 1..D-1 -- the same guess
+ * values, the same Alg. 3 thresholds and message restarts -- hold the same
+ * state after the BP of step D, so the first path to get there leaves a
+ * snapshot (in a pool the decoder allocated with its layouts) and paths
+ * queued later resume from it instead of recomputing the prefix.  Results,
+ * traces and out[1] of the counters are those of every path run from the
+ * root; on = 0 runs every path from the root. */
+qd_status qd_decoder_set_fork(qd_decoder* dec, int on);
 
 #ifdef __cplusplus
 }

@@ -637,9 +637,29 @@ struct PathOut {
   BranchTrace* btr;
   StepTrace* st;
   int8_t* fstat;
-  long long* visits;  // accumulates active edge visits
+  long long* visits;  // accumulates active edge visits, the path's shared prefix included
+  long long* exec;    // accumulates the active edge visits this launch executed (nullable)
   long long shot;
 };
+
+// Shot mode's shared path prefixes.  Paths that made the same decisions at
+// depths 1..D-1 are in the same state after the BP of step D (that BP does
+// not depend on the path: both P_A flags of Alg. 3 are kept), so a path can
+// resume there from a snapshot another path left instead of recomputing the
+// prefix from the root.  A snapshot is a 32-byte header (depth, iterations,
+// iterations since the messages were initialised, the `first` flag, the
+// producing path, the prefix's edge visits) and a copy of the slot.
+struct ForkCtx {
+  const char* src;       // snapshot to resume from (nullptr: from the root)
+  const int16_t* chain;  // this path's snapshot node by depth (index D - 1), -1: none; nullptr: no snapshots
+  int* flags;            // per node: 0 free, 1 being written, 2 ready
+  char* pool;            // this CTA's snapshots, `stride` bytes apart
+  unsigned stride;
+  char* slot;            // this warp's slot and its size
+  unsigned slot_bytes;
+  const StepTrace* st0;  // the shot's step records (path p at st0 + p * dmx), or nullptr
+};
+constexpr unsigned kSnapHeader = kSnapHeaderBytes;
 
 // Check-node update of Eq. (1) over the active VNs of one decision path, TPC
 // lanes per check (a template parameter, so that the loops and the group
@@ -712,7 +732,7 @@ __device__ __forceinline__ bool check_pass(const KParams& P, const ShortG& G, co
 // plain decoder carries no weight lookups).
 template <bool LW, class Grp>
 __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int id, const Grp& g,
-                         const PathOut& out, int dmx) {
+                         const PathOut& out, int dmx, const ForkCtx& F) {
   const int nr = G.nr, ns = G.ns, R = g.rank, S = g.size;
   // one lane per check for a warp; small lane groups per check for a CTA
   const int tpc = Grp::kWarp ? 1 : path_lanes_per_check(S, nr);
@@ -722,38 +742,65 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
   const int d_reinit = path_reinit(P, id, split);
   const int dmax = path_dmax(P, id, split);
   auto main_rules = [&](int D) { return id == 0 || (split && D <= split); };
-  float PA = main_rules(1) ? P.pa_main : P.pa_other;
-  for (int k = R; k < ns; k += S) {
-    B.status[k] = -1;
-    B.post[k] = G.llr[k];  // t = 0: mu_{i->j} = Lambda_i (Sec. II-A)
-  }
-  for (int j = R; j < nr; j += S) {
-    B.deg[j] = G.rowptr[j + 1] - G.rowptr[j];
-    B.cns[j].pad = (uint32_t)G.rowptr[j] | ((uint32_t)G.rowptr[j + 1] << 16);
-  }
-  for (int base = 0; base < nr; base += S) {  // the window syndrome by check label
-    const int j = base + R;
-    const unsigned m = __ballot_sync(FULL, j < nr && bit_of(G.sbits, G.cperm[j]));
-    if ((R & 31) == 0 && base + R < nr) B.sp[(base + R) >> 5] = m;
-  }
-  if (out.st)
-    for (int q = R; q < dmx; q += S) out.st[q] = StepTrace{-2, -1, 0, 0, 0};
-  g.sync();
   int status = BR_MAXDEPTH, depth = 0, iters = 0;
   int tw = 0;  // iterations since the messages were (re)initialised (learned weights)
-  long long visits = 0;
+  long long visits = 0, inherited = 0;  // executed here / the resumed prefix's (lane 0)
   double pm = CUDART_INF;
   bool first = true;
-  if (P.peel_init) {
-    const int np = peel(G, B, g);
-    if (np < 0) {
-      status = np == -1 ? BR_CONTRADICTION : BR_INTERNAL;
-      goto done;
+  int D0 = 1;  // first depth of this run: resumed runs start at its SELECT-VN
+  if (F.src) {
+    // resume from a snapshot taken after the BP of step D0 by a path with the
+    // same decisions at depths 1..D0-1
+    const int* h = (const int*)F.src;
+    D0 = __ldcg(h);
+    iters = __ldcg(h + 1);
+    tw = __ldcg(h + 2);
+    first = __ldcg(h + 3) != 0;
+    const int producer = __ldcg(h + 4);
+    if (R == 0) inherited = __ldcg((const long long*)(F.src + 24));
+    const uint4* s4 = (const uint4*)(F.src + kSnapHeader);
+    uint4* d4 = (uint4*)F.slot;
+    for (unsigned x = R; x < F.slot_bytes / 16u; x += S) d4[x] = __ldcg(s4 + x);
+    if (out.st) {  // the decision records of the shared prefix are the producer's
+      const StepTrace* ps = F.st0 + (size_t)producer * dmx;
+      for (int q = R; q < dmx; q += S) {
+        StepTrace r{-2, -1, 0, 0, 0};
+        if (q < D0 - 1) {
+          const uint2 v = __ldcg((const uint2*)(ps + q));
+          memcpy(&r, &v, sizeof(r));
+        }
+        out.st[q] = r;
+      }
+    }
+    g.sync();
+  } else {
+    for (int k = R; k < ns; k += S) {
+      B.status[k] = -1;
+      B.post[k] = G.llr[k];  // t = 0: mu_{i->j} = Lambda_i (Sec. II-A)
+    }
+    for (int j = R; j < nr; j += S) {
+      B.deg[j] = G.rowptr[j + 1] - G.rowptr[j];
+      B.cns[j].pad = (uint32_t)G.rowptr[j] | ((uint32_t)G.rowptr[j + 1] << 16);
+    }
+    for (int base = 0; base < nr; base += S) {  // the window syndrome by check label
+      const int j = base + R;
+      const unsigned m = __ballot_sync(FULL, j < nr && bit_of(G.sbits, G.cperm[j]));
+      if ((R & 31) == 0 && base + R < nr) B.sp[(base + R) >> 5] = m;
+    }
+    if (out.st)
+      for (int q = R; q < dmx; q += S) out.st[q] = StepTrace{-2, -1, 0, 0, 0};
+    g.sync();
+    if (P.peel_init) {
+      const int np = peel(G, B, g);
+      if (np < 0) {
+        status = np == -1 ? BR_CONTRADICTION : BR_INTERNAL;
+        goto done;
+      }
     }
   }
-  for (int D = 1; D <= dmax; ++D) {
+  for (int D = D0; D <= dmax; ++D) {
     depth = D;
-    PA = main_rules(D) ? P.pa_main : P.pa_other;  // read by this step's history flags
+    if (!(F.src && D == D0)) {  // (a resumed run's snapshot holds its first step's BP)
     const int ips = (D == 1 && P.ips1 > 0) ? P.ips1 : P.ips;  // the first step may have its own length
     for (int it = 1; it <= ips; ++it) {
       // ---- check-node update, Eq. (1), and the previous iteration's H e = s ----
@@ -794,7 +841,10 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
         B.post[k] = p;
         if (hist) {
           if (P.rkq || P.dump) B.hq[4 * k + (it - (ips - 3))] = qhist(p);
-          const uint8_t f = (uint8_t)((p <= 0.0f) | ((p < PA) << 1) | ((p > P.pc) << 2) | ((p > P.pd) << 3));
+          // both P_A tests of Alg. 3 (main branch: bit 1, other branches: bit 4),
+          // so that the step's BP does not depend on the path
+          const uint8_t f = (uint8_t)((p <= 0.0f) | ((p < P.pa_main) << 1) | ((p > P.pc) << 2) | ((p > P.pd) << 3) |
+                                      ((p < P.pa_other) << 4));
           if (hist0) {
             B.acc[k] = p;
             B.hfl[k] = f;
@@ -816,10 +866,38 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
       pm = path_metric(G, B, g);
       goto done;
     }
+    // a snapshot here for paths queued later that share the decisions so far
+    // (the first path to get here writes it)
+    if (F.chain && F.chain[D - 1] >= 0) {
+      const int n = F.chain[D - 1];
+      int won = 0;
+      if (R == 0) won = atomicCAS(&F.flags[n], 0, 1) == 0;
+      if (g.any(won != 0)) {
+        const long long vs = g.sum_ll(visits + inherited);
+        char* dst = F.pool + (size_t)n * F.stride;
+        if (R == 0) {
+          int* h = (int*)dst;
+          __stcg(h, D);
+          __stcg(h + 1, iters);
+          __stcg(h + 2, tw);
+          __stcg(h + 3, first ? 1 : 0);
+          __stcg(h + 4, id);
+          __stcg((long long*)(dst + 24), vs);
+        }
+        const uint4* s4 = (const uint4*)F.slot;
+        uint4* d4 = (uint4*)(dst + kSnapHeader);
+        for (unsigned x = R; x < F.slot_bytes / 16u; x += S) __stcg(d4 + x, s4[x]);
+        __threadfence();  // the snapshot and this path's decision records before the flag
+        g.sync();
+        if (R == 0) atomicExch(&F.flags[n], 2);
+      }
+    }
+    }
     if (D == dmax) break;  // no decimation after the last BP step
     {
       // ---- SELECT-VN (Alg. 1) with AGG-DEC (Alg. 3) ----
       const float PBd = (D == 1) ? P.pb_d1 : (main_rules(D) ? P.pb_main : P.pb_other);
+      const uint8_t pa_bit = main_rules(D) ? 2 : 16;
       // bk, tk: (ranked column << 16) | label, so that ties go to the lowest
       // ranked column (the oracle's index order) whatever the label order
       float bL = CUDART_INF_F, tL = CUDART_INF_F;
@@ -832,7 +910,7 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
           int nus = 0;
           for (int e = G.colptr[k]; e < G.colptr[k + 1]; ++e) nus += bit_of(B.unsat, G.colrows[e]);
           int bdec = -1;
-          if ((fl & 2) && L < PBd) bdec = 1;
+          if ((fl & pa_bit) && L < PBd) bdec = 1;
           else if (((fl & 4) && D <= P.pc_max_depth) || ((fl & 8) && nus >= P.n_unsat_min)) bdec = 0;
           if (bdec >= 0) {
             decimate_atomic(G, B, k, bdec);
@@ -916,7 +994,8 @@ done:
     *out.status = status;
     *out.pm = status == BR_CONVERGED ? pm : CUDART_INF;
     if (out.btr) *out.btr = BranchTrace{status, depth, iters, 0, status == BR_CONVERGED ? pm : CUDART_INF};
-    atomicAdd((unsigned long long*)out.visits, (unsigned long long)visits);
+    atomicAdd((unsigned long long*)out.visits, (unsigned long long)(visits + inherited));
+    if (out.exec) atomicAdd((unsigned long long*)out.exec, (unsigned long long)visits);
   }
   g.sync();
 }
@@ -962,6 +1041,10 @@ struct DecodeArgs {
   // path mode: CTAs per shot (the paths, then idle CTAs up to a whole number
   // of clusters, which only help with the pre-BP)
   int cps;
+  // executed GDG edge visits (nullable; counters[1] counts every path's
+  // whole run, resumed prefixes included)
+  long long* exec;
+  ForkDev F;  // shot mode: snapshots of shared path prefixes
 };
 
 // UG (a template parameter, so that shared-memory kernels keep shared-memory
@@ -1673,6 +1756,7 @@ __device__ __forceinline__ PathOut trace_out(const DecodeArgs& A, char* tr, int 
     o.fstat = (int8_t*)(tr + trace_off_fs(A.P.nb, A.dmx)) + (size_t)id * A.ns_max;
   }
   o.visits = &A.counters[1];
+  o.exec = A.exec;
   o.shot = shot;
   return o;
 }
@@ -1723,19 +1807,46 @@ __device__ void shot_body(const DecodeArgs& A, long long shot, char* sm, Stager&
     // warps beyond the layout's path slots (batched launches) sit out the paths
     if (warp < L.nslots) {
       const ShortG G = short_graph(sm, L, A.W, n_short);
-      const Slot B = make_slot(union_base<UG>(A, sm) + (size_t)warp * L.b_size, L);
+      char* slot = union_base<UG>(A, sm) + (size_t)warp * L.b_size;
+      const Slot B = make_slot(slot, L);
       const WarpGrp g{lane};
+      // snapshots of shared prefixes, when planned and this CTA has a pool
+      const bool fork = A.F.pool && A.F.n_nodes > 0 && (int)blockIdx.x < A.F.pool_ctas;
+      ForkCtx F{};
+      F.flags = (int*)(sm + L.red);
+      F.pool = fork ? A.F.pool + (size_t)blockIdx.x * A.F.cta_bytes : nullptr;
+      F.stride = kSnapHeader + L.b_size;
+      F.slot = slot;
+      F.slot_bytes = L.b_size;
+      F.st0 = tr ? (const StepTrace*)(tr + trace_off_st(A.P.nb)) : nullptr;
       while (true) {
-        int id = 0;
-        if (lane == 0) id = atomicAdd(&misc[2], 1);
-        id = __shfl_sync(FULL, id, 0);
-        if (id >= A.P.nb) break;
-        id = path_at(A.P, id);
+        int pos = 0;
+        if (lane == 0) pos = atomicAdd(&misc[2], 1);
+        pos = __shfl_sync(FULL, pos, 0);
+        if (pos >= A.P.nb) break;
+        const int id = fork ? (int)A.F.order[pos] : path_at(A.P, pos);
         PathOut o = trace_out(A, tr, id, shot);
         o.status = &res_status[id];
         o.pm = &res_pm[id];
         o.ebits = res_e + (size_t)id * L.sw;
-        run_path<LW>(A.P, G, B, id, g, o, A.dmx);
+        F.chain = fork ? A.F.chain + (size_t)id * A.dmx : nullptr;
+        F.src = nullptr;
+        if (fork) {  // the deepest ready snapshot on this path's chain
+          int node = -1;
+          if (lane == 0) {
+            const int dm = path_dmax(A.P, id, path_split(A.P, id));
+            for (int D = dm; D >= 1 && node < 0; --D) {
+              const int n = F.chain[D - 1];
+              if (n >= 0 && *(volatile int*)&F.flags[n] == 2) node = n;
+            }
+          }
+          node = __shfl_sync(FULL, node, 0);
+          if (node >= 0) {
+            __threadfence();  // the snapshot's contents after its flag
+            F.src = F.pool + (size_t)node * F.stride;
+          }
+        }
+        run_path<LW>(A.P, G, B, id, g, o, A.dmx, F);
       }
     }
     __syncthreads();
@@ -1771,6 +1882,7 @@ __global__ void __launch_bounds__(256, 2) decode_shot_kernel(DecodeArgs A) {
       misc[0] = atomicAdd(A.work, 1);
       misc[2] = 0;  // decision-path queue, path 0 first
     }
+    if (threadIdx.x < kMaxForkNodes) ((int*)(sm + A.L.red))[threadIdx.x] = 0;  // no snapshot yet
     __syncthreads();
     const long long shot = misc[0];
     if (shot >= A.n_shots) break;
@@ -1853,7 +1965,7 @@ __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
   o.status = (int*)mine;
   o.pm = (double*)(mine + 8);
   o.ebits = (uint32_t*)(mine + 16);
-  run_path<LW>(A.P, G, B, id, g, o, A.dmx);
+  run_path<LW>(A.P, G, B, id, g, o, A.dmx, ForkCtx{});
   // publish, then count arrivals; the last CTA of the shot reduces
   __threadfence();
   __syncthreads();
@@ -2051,7 +2163,8 @@ cudaError_t launch_decode_batch(cudaStream_t st, int grid, int threads, size_t s
     B.seg_end[i] = end;
     B.seg[i] = dev::DecodeArgs{*x.P,   *x.W,   *x.L,     x.det,      x.det_words, x.n,      x.corr,
                                x.corr_words, nullptr, nullptr, 0,     x.dmx,    x.ns_max, nullptr,
-                               x.counters, nullptr, nullptr, x.sw_max, nullptr, 0};
+                               x.counters, nullptr, nullptr, x.sw_max, nullptr, 0, 1,
+                               x.counters ? x.counters + 5 : nullptr, ForkDev{}};
     lw = lw || x.W->wts != nullptr;
   }
   if (lw) dev::decode_batch_kernel<true><<<grid, threads, smem, st>>>(B);
@@ -2104,10 +2217,12 @@ cudaError_t launch_decode(int mode, int grid, int threads, size_t smem, cudaStre
                           const WinDev& W, const Layout& L, const uint32_t* det, int det_words, long long n,
                           uint32_t* corr, int corr_words, int32_t* status, char* trace, size_t tr_bytes, int dmx,
                           int ns_max, int* work, long long* counters, char* path_res, int* arrive, int sw_max,
-                          char* uglob, size_t ubytes, int cps, int cluster) {
+                          char* uglob, size_t ubytes, int cps, int cluster, const ForkDev* fork) {
+  // counters[5]: the GDG edge visits the launch executed (counters[1] adds
+  // the resumed prefixes every path counts as its own)
   const dev::DecodeArgs A{P,     W,        L,     det,      det_words, n,     corr,     corr_words, status,
                           trace, tr_bytes, dmx,   ns_max,   work,      counters, path_res, arrive,     sw_max,
-                          uglob, ubytes,   cps};
+                          uglob, ubytes,   cps,   counters ? counters + 5 : nullptr, fork ? *fork : ForkDev{}};
   const bool lw = W.wts != nullptr;
   if (mode == 1) {  // one cluster of `cluster` CTAs shares each shot's pre-BP
     // every path needs its CTA, and a cluster never spans two shots

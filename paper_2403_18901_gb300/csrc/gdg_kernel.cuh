@@ -96,6 +96,22 @@ struct WinDev {
   const uint16_t* vperm;  // pre-BP processing order of the columns (descending degree)
 };
 
+// Shot mode's plan for resuming decision paths from snapshots of shared
+// prefixes (see ForkCtx in gdg_kernel.cu): the queue order, and for every path
+// p and depth D the snapshot node of p after the BP of step D
+// (chain[p * dmx + D - 1], -1: none).  Snapshots of CTA b live at
+// pool + b * cta_bytes, nodes `stride` bytes apart; pool = nullptr: no
+// snapshots, the path-queue order of path_at.
+constexpr int kMaxForkNodes = 64;  // node flags live in the shot-mode CTA's 512-byte reduction area
+constexpr unsigned kSnapHeaderBytes = 32;  // a snapshot's header, before the copy of the slot
+struct ForkDev {
+  const int16_t* order;
+  const int16_t* chain;
+  char* pool;
+  size_t cta_bytes;
+  int n_nodes, pool_ctas;
+};
+
 // A window's Tanner graph for the learned weighted min-sum (training kernels).
 struct WmsGraph {
   int nr, nc, ne, rw, T, ckpt;

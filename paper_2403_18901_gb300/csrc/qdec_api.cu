@@ -60,6 +60,7 @@ namespace {
 constexpr int kShotWarps = 8;
 constexpr int kPathThreads = 512;
 constexpr long long kPathModeMaxShots = 64;
+constexpr int kCounters = 8;
 
 struct WinGpu {
   qd::WindowHost h;
@@ -80,6 +81,10 @@ struct WinGpu {
   int grid_g = 1;
   bool fits = true, path_fits = true;
   int pcl = 1;  // path mode: CTAs per cluster sharing a shot's pre-BP
+  // shot mode's snapshot plan (qd::ForkDev): queue order [nb], then the
+  // node chain [nb][dmx]; fork_nodes = 0: none
+  int16_t* d_fork = nullptr;
+  int fork_nodes = 0;
 };
 
 template <class T>
@@ -119,8 +124,13 @@ struct qd_decoder {
   bool hist_on = false;  // layouts hold the quantised history (ranker or dump)
   void* d_ranker = nullptr;  // grid-rounded parameters (644 floats), then the 256 B fragments
   int* d_work = nullptr;
-  long long* d_counters = nullptr;
+  long long* d_counters = nullptr;  // kCounters entries (qd_decoder_counters_ex)
   uint32_t* d_corr = nullptr;
+  // shot mode's snapshots of shared path prefixes: one pool per resident CTA
+  char* d_snap = nullptr;
+  size_t snap_cta_bytes = 0;
+  int snap_ctas = 0;
+  bool fork_on = true;
   uint32_t *d_det = nullptr, *d_obs = nullptr, *d_pred = nullptr, *d_fail = nullptr, *d_resid = nullptr;
   long long* d_nfail = nullptr;
 };
@@ -144,6 +154,81 @@ qd_status ensure_uscratch(qd_decoder* dec, bool all) {
   QD_CK(cudaMalloc(&dec->d_uscratch, need));
   dec->uscratch_bytes = need;
   return QD_OK;
+}
+
+// Shot mode's plan for sharing path prefixes (qd::ForkDev).  The decision of
+// path p at depth d is summarised as (contrary value at d, main-branch
+// thresholds of Alg. 3 at d (when Alg. 3 is on), message restart after d);
+// two paths with equal summaries at depths 1..D-1 hold the same state after
+// the BP of step D.  The queue order runs `wave` paths at once first, each
+// sharing as little as possible with those before it, then takes the paths
+// that share the deepest prefix with a path before them; node = the deepest
+// state such a later path shares with an earlier one.
+struct ForkPlan {
+  std::vector<int16_t> order, chain;
+  int n_nodes = 0;
+};
+
+ForkPlan fork_plan(const qd::KParams& P, int dmx, int wave) {
+  const int nb = P.nb;
+  auto dmax = [&](int p) { return qd::path_dmax(P, p, qd::path_split(P, p)); };
+  auto sig = [&](int p, int d) {
+    const int split = qd::path_split(P, p);
+    const int contrary = split ? (d == split ? 1 : 0) : (d <= P.k ? (p >> (P.k - d)) & 1 : 0);
+    const int mainr = P.low_err ? 0 : ((p == 0 || (split && d <= split)) ? 1 : 0);
+    const int re = qd::path_reinit(P, p, split) == d ? 1 : 0;
+    return contrary | (mainr << 1) | (re << 2);
+  };
+  // deepest D with equal summaries below it that both paths reach
+  auto shared = [&](int p, int q) {
+    const int m = std::min(dmax(p), dmax(q));
+    int D = 1;
+    while (D < m && sig(p, D) == sig(q, D)) ++D;
+    return D;
+  };
+  ForkPlan F;
+  std::vector<int> order;
+  std::vector<char> used(nb, 0);
+  std::vector<int> share(nb, 0);  // deepest prefix shared with a path before it in the order
+  for (int pos = 0; pos < nb; ++pos) {
+    int best = -1, bkey = 0, bs = 0;
+    for (int q = 0; q < nb; ++q) {
+      if (used[q]) continue;
+      int s = 0;
+      for (int p : order) s = std::max(s, shared(p, q));
+      const int key = pos < wave ? -s : s;
+      if (best < 0 || key > bkey || (key == bkey && dmax(q) > dmax(best))) {
+        best = q;
+        bkey = key;
+        bs = s;
+      }
+    }
+    used[best] = 1;
+    share[best] = pos < wave ? 0 : bs;
+    order.push_back(best);
+  }
+  // nodes: (depth, summaries below it) of every later path's shared prefix
+  std::vector<std::vector<int>> keys;
+  auto key_of = [&](int p, int D) {
+    std::vector<int> k{D};
+    for (int d = 1; d < D; ++d) k.push_back(sig(p, d));
+    return k;
+  };
+  for (int q = 0; q < nb; ++q)
+    if (share[q] >= 1) {
+      const std::vector<int> k = key_of(q, share[q]);
+      if (std::find(keys.begin(), keys.end(), k) == keys.end()) keys.push_back(k);
+    }
+  if (keys.empty() || (int)keys.size() > qd::kMaxForkNodes) return F;
+  F.n_nodes = (int)keys.size();
+  F.order.assign(order.begin(), order.end());
+  F.chain.assign((size_t)nb * dmx, (int16_t)-1);
+  for (int p = 0; p < nb; ++p)
+    for (int D = 1; D <= dmax(p) && D <= dmx; ++D) {
+      const auto it = std::find(keys.begin(), keys.end(), key_of(p, D));
+      if (it != keys.end()) F.chain[(size_t)p * dmx + D - 1] = (int16_t)(it - keys.begin());
+    }
+  return F;
 }
 
 qd_status configure_layouts(qd_decoder* dec, bool hist, const char* who) {
@@ -230,6 +315,32 @@ qd_status configure_layouts(qd_decoder* dec, bool hist, const char* who) {
     g.grid_per_sm = cf[w].grid_per_sm;
   }
   QD_CK_ST(ensure_uscratch(dec, dec->launch_mode == 3));
+  // shot mode's snapshot plans (one per window: the first wave is its slot
+  // count) and one snapshot pool per resident CTA
+  size_t cta_bytes = 0;
+  int ctas = 0;
+  for (WinGpu& g : dec->wins) {
+    const ForkPlan F = fork_plan(dec->kp, dec->dmx, std::max(1, g.L.nslots));
+    g.fork_nodes = F.n_nodes;
+    if (!F.n_nodes) continue;
+    std::vector<int16_t> v(F.order);
+    v.insert(v.end(), F.chain.begin(), F.chain.end());
+    if (!g.d_fork) QD_CK(cudaMalloc(&g.d_fork, sizeof(int16_t) * (size_t)dec->kp.nb * (1 + dec->dmx)));
+    QD_CK(cudaMemcpy(g.d_fork, v.data(), sizeof(int16_t) * v.size(), cudaMemcpyHostToDevice));
+    cta_bytes = std::max(cta_bytes, (size_t)F.n_nodes * (qd::kSnapHeaderBytes + g.L.b_size));
+    ctas = std::max(ctas, dec->sm_count * std::max(g.grid_per_sm, g.grid_g));
+  }
+  if (cta_bytes > dec->snap_cta_bytes || ctas > dec->snap_ctas) {
+    const size_t cb = std::max(cta_bytes, dec->snap_cta_bytes);
+    const int nc = std::max(ctas, dec->snap_ctas);
+    cudaFree(dec->d_snap);
+    dec->d_snap = nullptr;
+    dec->snap_cta_bytes = 0;
+    dec->snap_ctas = 0;
+    QD_CK(cudaMalloc(&dec->d_snap, cb * nc));
+    dec->snap_cta_bytes = cb;
+    dec->snap_ctas = nc;
+  }
   dec->smem_max = smem_max;
   dec->hist_on = hist;
   return QD_OK;
@@ -335,7 +446,9 @@ qd_status qd_decoder_destroy(qd_decoder* dec) {
     cudaFree(w.d_ccdet);
     cudaFree(w.d_ccobs);
     cudaFree(w.d_wthr);
+    cudaFree(w.d_fork);
   }
+  cudaFree(dec->d_snap);
   cudaFree(dec->d_work);
   cudaFree(dec->d_uscratch);
   cudaFree(dec->d_ranker);
@@ -470,8 +583,8 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
   QD_CK(cudaMalloc(&dec->d_path_res, qd::path_result_bytes(dec->sw_max) * k.nb * pm_shots));
   QD_CK(cudaMalloc(&dec->d_arrive, sizeof(int) * pm_shots));
   QD_CK(cudaMemset(dec->d_arrive, 0, sizeof(int) * pm_shots));
-  QD_CK(cudaMalloc(&dec->d_counters, sizeof(long long) * 5));
-  QD_CK(cudaMemset(dec->d_counters, 0, sizeof(long long) * 5));
+  QD_CK(cudaMalloc(&dec->d_counters, sizeof(long long) * kCounters));
+  QD_CK(cudaMemset(dec->d_counters, 0, sizeof(long long) * kCounters));
   const int dw = (dem->h.n_det + 31) / 32;
   QD_CK(cudaMalloc(&dec->d_corr, sizeof(uint32_t) * (size_t)max_shots * dec->corr_words));
   QD_CK(cudaMalloc(&dec->d_det, sizeof(uint32_t) * (size_t)max_shots * dw));
@@ -518,6 +631,26 @@ qd_status qd_window_info(const qd_decoder* dec, int k, qd_window_info_t* o, int*
   return QD_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// shot mode's snapshot plan of window g (pool = nullptr: none, or turned off)
+qd::ForkDev fork_dev(const qd_decoder* dec, const WinGpu& g) {
+  qd::ForkDev F{};
+  // the candidate dump records path 0's every step, so path 0 runs from the root
+  if (!dec->fork_on || !g.fork_nodes || !dec->d_snap || dec->kp.dump) return F;
+  F.order = g.d_fork;
+  F.chain = g.d_fork + dec->kp.nb;
+  F.pool = dec->d_snap;
+  F.cta_bytes = dec->snap_cta_bytes;
+  F.n_nodes = g.fork_nodes;
+  F.pool_ctas = dec->snap_ctas;
+  return F;
+}
+}  // namespace
+
+extern "C" {
+
 qd_status qd_decode_windows(qd_decoder* dec, int k, const uint32_t* det_bits, int64_t n_shots,
                             uint32_t* win_correction, int32_t* status, void* trace, qd_stream_t stream) {
   QD_REQ(dec && det_bits && win_correction, "qd_decode_windows: null argument");
@@ -540,13 +673,14 @@ qd_status qd_decode_windows(qd_decoder* dec, int k, const uint32_t* det_bits, in
   if (dec->launch_mode == 0) path_mode = n_shots * 4 <= dec->sm_count;
   if (path_mode && (n_shots > std::min<long long>(dec->max_shots, kPathModeMaxShots) || !g.path_fits || global))
     path_mode = false;
+  const qd::ForkDev fk = fork_dev(dec, g);
   if (global) {
     QD_CK(cudaMemsetAsync(dec->d_work + k, 0, sizeof(int), st));
     const long long grid = std::min<long long>(n_shots, (long long)dec->sm_count * g.grid_g);
     QD_CK(qd::launch_decode(0, (int)grid, 32 * kShotWarps, g.Lg.U, st, dec->kp, g.dv, g.Lg, det_bits, dw, n_shots,
                             win_correction, dec->corr_words, status, (char*)trace, dec->trace_bytes, dec->dmx,
                             dec->ns_max, dec->d_work + k, dec->d_counters, nullptr, nullptr, dec->sw_max,
-                            dec->d_uscratch, g.Lg.total - g.Lg.U));
+                            dec->d_uscratch, g.Lg.total - g.Lg.U, 1, 1, &fk));
     return QD_OK;
   }
   if (path_mode) {
@@ -561,7 +695,8 @@ qd_status qd_decode_windows(qd_decoder* dec, int k, const uint32_t* det_bits, in
   const long long grid = std::min<long long>(n_shots, (long long)dec->sm_count * g.grid_per_sm);
   QD_CK(qd::launch_decode(0, (int)grid, 32 * g.shot_warps, g.L.total, st, dec->kp, g.dv, g.L, det_bits, dw,
                           n_shots, win_correction, dec->corr_words, status, (char*)trace, dec->trace_bytes,
-                          dec->dmx, dec->ns_max, dec->d_work + k, dec->d_counters, nullptr, nullptr, dec->sw_max));
+                          dec->dmx, dec->ns_max, dec->d_work + k, dec->d_counters, nullptr, nullptr, dec->sw_max,
+                          nullptr, 0, 1, 1, &fk));
   return QD_OK;
 }
 
@@ -722,9 +857,22 @@ qd_status qd_decoder_counters(qd_decoder* dec, long long out[5]) {
   return QD_OK;
 }
 
+qd_status qd_decoder_counters_ex(qd_decoder* dec, long long* out, int n) {
+  QD_REQ(dec && out, "null argument");
+  QD_REQ(n >= 1 && n <= kCounters, "qd_decoder_counters_ex: n outside [1, 8]");
+  QD_CK(cudaMemcpy(out, dec->d_counters, sizeof(long long) * n, cudaMemcpyDeviceToHost));
+  return QD_OK;
+}
+
+qd_status qd_decoder_set_fork(qd_decoder* dec, int on) {
+  QD_REQ(dec, "null argument");
+  dec->fork_on = on != 0;
+  return QD_OK;
+}
+
 qd_status qd_decoder_reset_counters(qd_decoder* dec, qd_stream_t stream) {
   QD_REQ(dec, "null argument");
-  QD_CK(cudaMemsetAsync(dec->d_counters, 0, sizeof(long long) * 5, (cudaStream_t)stream));
+  QD_CK(cudaMemsetAsync(dec->d_counters, 0, sizeof(long long) * kCounters, (cudaStream_t)stream));
   return QD_OK;
 }
 
@@ -804,13 +952,14 @@ extern "C" qd_status qd_decode_commit_static(qd_decoder* dec, int k, uint32_t* d
     } else {
       // the array keeps the previous call's contents: the work counter restarts at 0
       QD_CK(cudaMemsetAsync(work, 0, sizeof(int), st));
+      const qd::ForkDev fk = fork_dev(dec, g);
       const qd::Layout& L = global ? g.Lg : g.L;
       const long long grid =
           std::min<long long>(n_shots, (long long)dec->sm_count * (global ? g.grid_g : g.grid_per_sm));
       QD_CK(qd::launch_decode(0, (int)grid, 32 * (global ? kShotWarps : g.shot_warps), global ? L.U : L.total, st,
                               dec->kp, g.dv, L, det_bits, dw, n_shots, corr, dec->corr_words, nullptr, nullptr, 0,
                               dec->dmx, dec->ns_max, work, dec->d_counters, nullptr, nullptr, dec->sw_max,
-                              global ? dec->d_uscratch : nullptr, global ? L.total - L.U : 0));
+                              global ? dec->d_uscratch : nullptr, global ? L.total - L.U : 0, 1, 1, &fk));
     }
   }
   const int w = dec->dem->h.w;

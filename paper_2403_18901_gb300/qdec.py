@@ -99,6 +99,8 @@ _SIGS = {
     "qd_adam_step": (_I, [_VP, _VP, _VP, _VP, _I64, C.c_float, C.c_float, C.c_float, C.c_float, _I,
                           _VP]),
     "qd_decoder_counters": (_I, [_VP, _VP]),
+    "qd_decoder_counters_ex": (_I, [_VP, _VP, C.c_int]),
+    "qd_decoder_set_fork": (_I, [_VP, C.c_int]),
     "qd_decoder_reset_counters": (_I, [_VP, _VP]),
 }
 
@@ -322,6 +324,17 @@ class Decoder:
         out = np.zeros(5, np.int64)
         _check(lib().qd_decoder_counters(self.h, _ptr(out)))
         return out
+
+    def counters_ex(self, n=8):
+        """counters() then [5] the GDG edge-iterations actually executed (shared
+        path prefixes computed once), [6..7] reserved."""
+        out = np.zeros(n, np.int64)
+        _check(lib().qd_decoder_counters_ex(self.h, _ptr(out), int(n)))
+        return out
+
+    def set_fork(self, on):
+        """Shot mode: resume decision paths from snapshots of shared prefixes (default on)."""
+        _check(lib().qd_decoder_set_fork(self.h, int(bool(on))))
 
     def reset_counters(self, stream=None):
         _check(lib().qd_decoder_reset_counters(self.h, _stream(stream)))

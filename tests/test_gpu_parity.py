@@ -402,3 +402,40 @@ def test_initial_bp_as_first_step_bit_exact(key, R, n, mode, tw):
     throughput shape, so they run in global memory."""
     params = preset("configured", k_guess=4 if key == "144" else 3, p=0.003, n_pre=0, shorten=0, iters_first=100)
     _pipeline(key, R, 0.003, params, n=n, seed=int(key) * 1000 + 7, trace_windows=tw, mode=mode)
+
+
+@pytest.mark.parametrize("pname,p,n", [("configured", 0.003, 400), ("configured", 0.002, 300), ("paper", 0.004, 300)])
+def test_shared_prefixes_change_nothing(pname, p, n):
+    """Shot mode resumes decision paths from snapshots of the prefixes they
+    share with paths queued before them.  Every output -- corrections,
+    statuses, the whole per-shot trace (every path's status, depth,
+    iterations, metric, step log and final statuses) -- and the per-path work
+    count equal those of every path run from the root; only the executed
+    work drops."""
+    d = qdec.Dem(CODES["144"], p, 12)
+    runs = []
+    for fork in (True, False):
+        dec = qdec.Decoder(d, preset(pname, k_guess=4, p=p), max_shots=n)
+        dec.set_launch(1)
+        dec.set_fork(fork)
+        det, _ = d.sample(seed=144_777, shot_offset=0, n_shots=n)
+        corr = torch.zeros((n, dec.corr_words), dtype=torch.int32, device="cuda")
+        status = torch.zeros(n, dtype=torch.int32, device="cuda")
+        pred = torch.zeros(n, dtype=torch.int32, device="cuda")
+        resid = torch.zeros(n, dtype=torch.int32, device="cuda")
+        out = []
+        for k in range(dec.n_windows):
+            tr = torch.zeros((n, dec.trace_bytes), dtype=torch.uint8, device="cuda")
+            dec.decode_window(k, det, n, corr, status, tr)
+            out.append((corr.cpu().numpy().copy(), status.cpu().numpy().copy(), tr.cpu().numpy()))
+            dec.commit(k, corr, n, det, pred, resid)
+        torch.cuda.synchronize()
+        runs.append((out, det.cpu().numpy(), pred.cpu().numpy(), resid.cpu().numpy(), dec.counters_ex()))
+    (a, da, pa, ra, ca), (b, db, pb, rb, cb) = runs
+    for k, (x, y) in enumerate(zip(a, b)):
+        for u, v in zip(x, y):
+            assert (u == v).all(), f"window {k} differs"
+    assert (da == db).all() and (pa == pb).all() and (ra == rb).all()
+    assert list(ca[:5]) == list(cb[:5]) and ca[4] == 0
+    assert cb[5] == cb[1]  # from the root: executed = counted
+    assert ca[5] < ca[1], "no decision path resumed from a shared prefix"
