@@ -33,12 +33,13 @@ import numpy as np  # noqa: E402
 CODE_KEY, ROUNDS, P_PHYS, K_GUESS = "144", 12, 0.003, 4
 METRIC = "[[144,12,12]] W=3 windows/s"
 OPS_PER_EDGE_ITER = 10  # FP32/ALU operations of Eq. (1)-(3) per edge and iteration
+BYTES_PER_EDGE_ITER = 16  # explicit-message shared-memory bytes per edge and iteration (4 B x 2 read + 2 written)
 # DRAM bytes (read + write) of one decode_shot_kernel launch of the default
 # workload (configured preset, 20000 shots per launch), from one ncu capture of
 # the current kernel (dram__bytes_read.sum + dram__bytes_write.sum; see
 # profiles/decode_shot_kernel_bb144_w3_p3e-3_configured.md).  Reported only for
 # that workload; per launch, like "achieved".
-TRAFFIC_PER_LAUNCH = {("configured", 20000): 2953216 + 0}
+TRAFFIC_PER_LAUNCH = {}
 
 
 def workload_name(preset_name):
@@ -54,11 +55,13 @@ def parse():
     ap.add_argument("--impl", default="gdg", choices=["gdg", "reference"])
     ap.add_argument("--shots", type=int, default=20000, help="shots per step per GPU")
     ap.add_argument("--preset", default="configured", choices=["configured", "paper"])
-    ap.add_argument("--latency-shots", type=int, default=100)
+    ap.add_argument("--latency-shots", type=int, default=1000,
+                    help="shots of the latency measurements (x windows per shot >= 1e4 windows)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--seed", type=int, default=144_003)
-    ap.add_argument("--train-steps", type=int, default=60,
-                    help="Adam steps per window type for the learned weights (0: skip)")
+    ap.add_argument("--train-steps", type=int, default=245,
+                    help="Adam steps per window type for the learned weights (0: skip); "
+                         "245 x 4096 = 1.0e6 samples per window type")
     ap.add_argument("--train-batch", type=int, default=4096)
     ap.add_argument("--ranker-steps", type=int, default=300,
                     help="Adam steps of the decimation ranker (0: skip)")
@@ -72,6 +75,13 @@ def parse():
                     help="shots per code of the batched uneven workload (0: skip)")
     ap.add_argument("--ranker-shots", type=int, default=4096,
                     help="window samples per collection round for the ranker (4 rounds)")
+    ap.add_argument("--r288-shots", type=int, default=50000,
+                    help="[[288,12,18]] shots of the ranker-vs-Alg. 1 measurement (0: skip)")
+    ap.add_argument("--r288-latency-shots", type=int, default=200)
+    ap.add_argument("--reading-shots", type=int, default=2000,
+                    help="shots of the second reading of the configured pre-BP (0: skip the readings section)")
+    ap.add_argument("--shape-shots", type=int, default=5000,
+                    help="shots of each other window shape of Sec. IV-C (0: skip)")
     return ap.parse_args()
 
 
@@ -86,6 +96,38 @@ def wilson(k, n, z=1.96):
 
 def per_round(P, R=ROUNDS):
     return 1.0 - (1.0 - P) ** (1.0 / R)
+
+
+def ler_entry(f, n, R=ROUNDS):
+    lo, hi = wilson(f, n)
+    return {"failures": int(f), "shots": int(n), "p_L": per_round(f / n, R) if n else None,
+            "wilson95": [per_round(lo, R), per_round(hi, R)]}
+
+
+def decode_pass(torch, dec, dem, seed, n_total, batch, offset=0):
+    """Whole sliding-window passes over n_total fresh shots in batches (one
+    warm-up batch first); returns (GPU seconds of the decode passes,
+    failures, failures of Eq. (11) alone, GDG windows)."""
+    pred = torch.empty(batch, dtype=torch.int32, device="cuda")
+    fail = torch.empty(batch, dtype=torch.int32, device="cuda")
+    nf = torch.zeros(1, dtype=torch.int64, device="cuda")
+    det, obs = dem.sample(seed, offset, min(batch, n_total))
+    dec.decode_all(det, obs, det.shape[0], pred, fail, nf)  # warm-up
+    nf.zero_()
+    dec.reset_counters()
+    t, done, resid_only = 0.0, 0, 0
+    while done < n_total:
+        n = min(batch, n_total - done)
+        det, obs = dem.sample(seed, offset + done, n)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dec.decode_all(det, obs, n, pred, fail, nf)
+        e1.record()
+        torch.cuda.synchronize()
+        t += e0.elapsed_time(e1) / 1000.0
+        resid_only += int((fail[:n] == 1).sum().item())
+        done += n
+    return t, int(nf.item()), resid_only, int(dec.counters()[3])
 
 
 def dist_env():
@@ -335,7 +377,7 @@ def paper_tree(args, torch, qdec, CODES, preset, latency_fn):
     pi = np.zeros(2, np.int32)
     qdec._check(qdec.lib().qd_decoder_path_info(dec.h, qdec._ptr(pi)))
     ldec = qdec.Decoder(dem, params, max_shots=1)
-    p50, p99, nl = latency_fn(ldec, det[:max(1, args.latency_shots)].clone())
+    lat = latency_fn(ldec, det[:max(1, args.latency_shots)].clone())
     # the appendix's snapshot variant: paths restart their messages where they split
     rdec = qdec.Decoder(dem, dict(params, reinit_on_split=1), max_shots=n)
     work.copy_(det)
@@ -354,7 +396,7 @@ def paper_tree(args, torch, qdec, CODES, preset, latency_fn):
             "reinit_on_split": reinit,
             "shots": n, "value": n * dec.n_windows / t, "unit": "windows/s", "seconds": t,
             "gdg_windows_frac": float(c[3]) / (n * dec.n_windows),
-            "latency_ms": {"p50": p50, "p99": p99, "windows": nl},
+            "latency_ms": lat,
             "failures_eq11_only": resid_only,
             "ler_per_round": {"failures": f, "shots": n, "p_L": per_round(f / n),
                               "wilson95": [per_round(lo), per_round(hi)]}}
@@ -428,6 +470,85 @@ def code_capacity(args, torch, qdec, CODES):
         if ps > 0:
             r["lower_bound_terms_864_2592"] = 864 * ps * ps + 2592 * pd * ps * ps
         out.append(r)
+    return out
+
+
+def ranker_288(args, torch, qdec, CODES, preset, latency_fn):
+    """[[288,12,18]], 18 rounds, (3,1) windows, p = 0.002 (low-error mode),
+    k = 4, D_max 40 on the main path and 20 steps after the last guess
+    (Sec. IV-C for N = 288): a decimation ranker trained on the decoder's own
+    interior-window records against Alg. 1's argmin, on the same fresh shots."""
+    from paper_2403_18901_gb300 import ranker as rk
+    p, R = 0.002, 18
+    params = preset("configured", k_guess=K_GUESS, p=p, d_max_main=40, d_max_other=K_GUESS + 20)
+    dem = qdec.Dem(CODES["288"], p, R)
+    n = args.r288_shots
+    B = min(n, args.shots)
+    dec = qdec.Decoder(dem, params, max_shots=max(B, args.ranker_shots))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rparams, rinfo = rk.train(dec, 1, steps=max(args.ranker_steps, 1), shots_per_round=args.ranker_shots, rounds=4,
+                              cap=1 << 24, batch=65536, lr=1e-2, seed=2_403_189_02)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    rhost = rparams.cpu().numpy()
+    out = {"workload": "[[288,12,18]] BB memory, 18 rounds, (3,1) windows, p=0.002, GDG 2^4 paths, low-error mode, "
+                       "D_max 40 / 24",
+           "shots": n, "windows_per_shot": dec.n_windows,
+           "train": dict(rinfo, steps=max(args.ranker_steps, 1), window=1, rounds=4,
+                         shots_per_round=args.ranker_shots, seconds=train_s)}
+    ldec = qdec.Decoder(dem, params, max_shots=1)
+    lsrc, _ = dem.sample(args.seed + 2880, 0, max(1, args.r288_latency_shots))
+    for name, rp in (("plain", None), ("ranker", rhost)):
+        dec.set_ranker(rp)
+        t, f, f11, gdg = decode_pass(torch, dec, dem, args.seed + 288, n, B)
+        ldec.set_ranker(rp)
+        out[name] = {"windows_per_s": n * dec.n_windows / t, "seconds": t, "gdg_windows_frac": gdg / (n * dec.n_windows),
+                     "ler_per_round": ler_entry(f, n, R), "failures_eq11_only": f11,
+                     "latency_ms": latency_fn(ldec, lsrc)}
+    dec.set_ranker(None)
+    return out
+
+
+def readings(args, torch, qdec, CODES, preset):
+    """The configured preset (alpha = 0.625, 100 initial BP iterations, steps
+    of 10) on the headline workload under two changes: the second reading of
+    "100 initial BP iterations" (no pre-BP and no shortening; GDG's first
+    step runs 100 iterations on the whole window), and alpha = 1.0 (the
+    paper's) with the preset otherwise unchanged."""
+    dem = qdec.Dem(CODES[CODE_KEY], P_PHYS, ROUNDS)
+    out = {}
+    for name, over, n in (("initial_bp_as_first_step", dict(n_pre=0, shorten=0, iters_first=100), args.reading_shots),
+                          ("alpha_1.0", dict(alpha=1.0), args.shots)):
+        params = preset("configured", k_guess=K_GUESS, p=P_PHYS, **over)
+        B = min(n, args.shots)
+        dec = qdec.Decoder(dem, params, max_shots=B)
+        t, f, f11, gdg = decode_pass(torch, dec, dem, args.seed + 5, n, B)
+        out[name] = {"change": over, "shots": n, "windows_per_s": n * dec.n_windows / t,
+                     "gdg_windows_frac": gdg / (n * dec.n_windows), "ler_per_round": ler_entry(f, n),
+                     "failures_eq11_only": f11}
+    return out
+
+
+def window_shapes(args, torch, qdec, CODES, preset):
+    """The other window shapes of Sec. IV-C with the paper's decoder: (5,2)
+    windows for [[144,12,12]] (12 rounds, p = 0.003, the Fig. 2 tree) and (4,1)
+    windows for [[288,12,18]] (18 rounds, p = 0.002, its own tree: D_max 40,
+    depth-5 tree, side branches to D_split 20, 16 pre-BP iterations)."""
+    out = []
+    n = args.shape_shots
+    for key, R, p, params in (
+            ("144", 12, 0.003, preset("paper", 4, p=0.003, W=5, F=2)),
+            ("288", 18, 0.002, preset("paper", 5, p=0.002, d_max_main=40, d_max_other=25, side_max=20, n_pre=16,
+                                      W=4, F=1))):
+        dem = qdec.Dem(CODES[key], p, R)
+        B = min(n, args.shots)
+        dec = qdec.Decoder(dem, params, max_shots=B)
+        t, f, f11, gdg = decode_pass(torch, dec, dem, args.seed + 17, n, B)
+        out.append({"code": CODES[key]["name"], "rounds": R, "p": p, "W": params["W"], "F": params["F"],
+                    "shots": n, "windows_per_shot": dec.n_windows, "windows_per_s": n * dec.n_windows / t,
+                    "gdg_windows_frac": gdg / (n * dec.n_windows), "ler_per_round": ler_entry(f, n, R),
+                    "failures_eq11_only": f11})
     return out
 
 
@@ -527,14 +648,17 @@ def main():
         kern_ms.append((e0, e1))
     torch.cuda.synchronize()
     kern_ms = [a.elapsed_time(b) for a, b in kern_ms]
-    kc = dec.counters()
-    edge_iters = int(kc[0] + kc[1])
+    kc = dec.counters_ex()
+    edge_iters = int(kc[0] + kc[1])  # every decision path counted from the root (Alg. 2)
+    edge_exec = int(kc[0] + kc[5])   # what the GPU ran (shared path prefixes once)
     kern_s = sum(kern_ms) / 1000.0
     peaks, peak_kind = measured_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     alu_peak = n_sm * 128 * sm_mhz * 1e6 / 1e12  # T op/s, one FP32 op per lane per clock
     achieved = OPS_PER_EDGE_ITER * edge_iters / kern_s / 1e12
+    smem_peak = n_sm * 128 * sm_mhz * 1e6 / 1e9  # GB/s, 32 banks x 4 B per clock per SM
+    smem_achieved = BYTES_PER_EDGE_ITER * edge_iters / kern_s / 1e9
 
     # ---- learned weighted min-sum: train on the GPU, then time the same shots ----
     learned = None
@@ -622,7 +746,7 @@ def main():
         def latency(ld, src=None):
             src = lsrc if src is None else src
             nwin = ld.n_windows
-            ldet = torch.empty((1, dw), dtype=torch.int32, device="cuda")
+            ldet = torch.empty((1, ld.dem.det_words), dtype=torch.int32, device="cuda")
             lcorr = torch.empty((1, ld.corr_words), dtype=torch.int32, device="cuda")
             lpred = torch.zeros(1, dtype=torch.int32, device="cuda")
             lres = torch.zeros(1, dtype=torch.int32, device="cuda")
@@ -651,16 +775,17 @@ def main():
                     lat.append((a, b2))
             torch.cuda.synchronize()
             lat_ms = sorted(a.elapsed_time(b2) for a, b2 in lat)
-            return (lat_ms[len(lat_ms) // 2], lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))],
-                    len(lat_ms))
+            return {"p50": lat_ms[len(lat_ms) // 2], "p99": lat_ms[min(len(lat_ms) - 1, int(0.99 * len(lat_ms)))],
+                    "max": lat_ms[-1], "windows": len(lat_ms)}
 
-        p50, p99, n_lat = latency(ldec)
+        lat_plain = latency(ldec)
         n_shots_total = B * args.steps * world
         if learned is not None:
             for k, w in wts.items():
                 ldec.set_weights(k, w)
-            lp50, lp99, _ = latency(ldec)
-            learned["latency_ms"] = {"p50": lp50, "p99": lp99}
+            learned["latency_ms"] = latency(ldec)
+            for k in wts:
+                ldec.set_weights(k, None)
             fl_tot = fail_l if world == 1 else None
             lo, hi = wilson(failures, n_shots_total)
             llo, lhi = wilson(fail_l, B * args.steps)
@@ -675,9 +800,8 @@ def main():
 
         if ranked is not None:
             ldec.set_ranker(rhost)
-            rp50, rp99, _ = latency(ldec)
+            ranked["latency_ms"] = latency(ldec)
             ldec.set_ranker(None)
-            ranked["latency_ms"] = {"p50": rp50, "p99": rp99}
             lo, hi = wilson(failures, n_shots_total)
             rlo, rhi = wilson(ranked["failures"], B * args.steps)
             ranked["ler_per_round"] = {
@@ -693,9 +817,30 @@ def main():
         paper = None
         if args.paper_shots > 0:
             paper = paper_tree(args, torch, qdec, CODES, preset, latency)
+        r288 = ranker_288(args, torch, qdec, CODES, preset, latency) if args.r288_shots > 0 else None
+        rdg = readings(args, torch, qdec, CODES, preset) if args.reading_shots > 0 else None
+        shapes = window_shapes(args, torch, qdec, CODES, preset) if args.shape_shots > 0 else None
+
+        # the metric's own numbers first: plain vs learned GDG on the headline
+        # workload (windows/s, per-window latency, LER per round), and the
+        # [[288,12,18]] ranker workload
+        def hl(v, lat, ler):
+            return {"windows_per_s": v, "latency_ms": {k: lat[k] for k in ("p50", "p99", "max", "windows")},
+                    "ler_per_round": ler}
+        headline = {"workload": workload_name(args.preset),
+                    "plain": hl(value, lat_plain, ler_entry(failures, n_shots_total))}
+        if learned is not None:
+            headline["learned_weights"] = hl(learned["value"], learned["latency_ms"],
+                                             learned["ler_per_round"]["learned"])
+        if ranked is not None:
+            headline["learned_ranker"] = hl(ranked["value"], ranked["latency_ms"], ranked["ler_per_round"]["ranker"])
+        if r288 is not None:
+            headline["bb288_p002"] = {k: hl(r288[k]["windows_per_s"], r288[k]["latency_ms"], r288[k]["ler_per_round"])
+                                      for k in ("plain", "ranker")}
 
         cpu_rate, cores, cpu_shots, cpu_s = cpu_oracle_rate(params, args.cpu_seconds, args.seed)
         line = {
+            "headline": headline,
             "metric": METRIC, "value": value, "unit": "windows/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * tot_s / args.steps, "higher_is_better": True,
@@ -707,11 +852,11 @@ def main():
                        "cuda_graph": "latency mode replays one captured graph per window"},
             "shots_per_s": B * args.steps * world / tot_s,
             "logical_failures": failures, "shots_decoded": B * args.steps * world,
-            "latency_ms": {"p50": p50, "p99": p99, "windows": n_lat,
-                           "mode": "1 shot per window step (decode + commit, one CUDA graph); path mode: "
-                                   "one 512-thread CTA per decision path, the shot's "
-                                   f"{ldec.launch_info(0)['path_ctas_per_shot']} CTAs in clusters of "
-                                   f"{ldec.launch_info(0)['path_cluster']} that split the pre-BP"},
+            "latency_ms": dict(lat_plain,
+                               mode="1 shot per window step (decode + commit, one CUDA graph); path mode: "
+                                    "one 512-thread CTA per decision path, the shot's "
+                                    f"{ldec.launch_info(0)['path_ctas_per_shot']} CTAs in clusters of "
+                                    f"{ldec.launch_info(0)['path_cluster']} that split the pre-BP"),
             "paper_context": {"worst_case_ms_per_window": 3.0,
                               "hardware": "Intel i9-13900K, multi-threaded"},
             "e2e": {"value": B * nwin / e2e_s, "unit": "windows/s", "h2d_bytes_per_step": h2d,
@@ -724,7 +869,14 @@ def main():
                          "work": f"{OPS_PER_EDGE_ITER} ops x {edge_iters} edge-iterations in "
                                  f"{nwin} launches",
                          "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz "
-                                       f"({peak_kind} sm_max_mhz)"},
+                                       f"({peak_kind} sm_max_mhz)",
+                         "smem": {"achieved": smem_achieved, "peak": smem_peak, "unit": "GB/s",
+                                  "frac": smem_achieved / smem_peak,
+                                  "basis": f"{BYTES_PER_EDGE_ITER} B per counted edge-iteration (two FP32 messages "
+                                           f"read and written) against {n_sm} SMs x 128 B/clk x {sm_mhz:.0f} MHz "
+                                           f"({peak_kind} sm_max_mhz); the kernel keeps compressed check state "
+                                           f"and moves fewer bytes than this count"},
+                         "edge_iterations_executed": edge_exec},
             "launch": dec.launch_info(1),
             "edge_iterations_per_window": edge_iters / (B * nwin),
             "gdg_windows_frac": float(kc[3]) / (B * nwin),
@@ -740,6 +892,9 @@ def main():
             "paper_tree": paper,
             "code_capacity": capacity,
             "ler_sweep_144": sweep,
+            "ranker_288": r288,
+            "readings": rdg,
+            "window_shapes": shapes,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -7,7 +7,9 @@ Alg. 1; no counterpart in the paper).
 * The candidate records the decode kernel writes equal the oracle's.
 * Window-local samples: the detector placement and fault bits agree with
   the window matrix and with qd_wms_sample.
-* The training kernel's gradient matches the FP64 reference.
+* The training kernel's gradient matches the FP64 reference; on grid-rounded
+  parameters it runs on the tensor cores and its scores equal the oracle's
+  bit for bit.
 * A ranker trained on the decoder's own records gives fewer logical
   failures than Alg. 1 on the same held-out memory shots.
 """
@@ -58,6 +60,20 @@ def test_ranker_decode_bit_exact(key, R, k_guess, mode, seed, coarse):
     n = 96 if key == "72" else 48
     _pipeline(key, R, 0.004, params, n, seed, trace_windows=(0, 1, 2), mode=mode,
               ranker=_random_ranker(seed, coarse))
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_ranker_bb288_bit_exact(mode):
+    """[[288,12,18]] with (3,1) windows and the decoder of p = 0.002
+    (low-error mode; D_max 40 on the main path, 20 steps after the last
+    guess), the ranker choosing the decimated VN in both launch shapes, on
+    shots at p = 0.003 (so that most windows run GDG): corrections, decision
+    logs and final statuses equal the oracle's."""
+    from test_gpu_parity import _pipeline
+    params = preset("configured", k_guess=4, p=0.002, d_max_main=40, d_max_other=24)
+    assert params["low_error_mode"]
+    _pipeline("288", 3, 0.003, params, 24 if mode == 1 else 8, 288_21, trace_windows=(0, 1), mode=mode,
+              ranker=_random_ranker(288))
 
 
 def test_ranker_low_error_mode_bit_exact():
@@ -162,11 +178,12 @@ def test_training_gradient_matches_fp64():
         sc, _ = rk.evaluate(pt, rt, None, quantize=quant)
         s64 = ranker_ref.forward(p, recs["x"], quant=quant)
         assert np.allclose(sc.cpu().numpy(), s64, rtol=1e-5, atol=1e-4)
-    # quantised scores equal the oracle's exactly-rounded FP32 scores up to
-    # the training kernel's own (unordered) layer-2 sums
+    # the tensor-core training kernel scores grid-rounded parameters exactly
+    # as the oracle (and the decoder) do: exact layer 1, layer 2 in the same
+    # fixed FP32 order
     sc, _ = rk.evaluate(pt, rt, None, quantize=True)
     so = O.ranker_score(p, recs["x"])
-    assert np.allclose(sc.cpu().numpy(), so, rtol=1e-5, atol=1e-4)
+    assert (sc.cpu().numpy() == so).all()
 
 
 def test_trained_ranker_lowers_logical_failures():
