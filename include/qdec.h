@@ -91,6 +91,14 @@ typedef struct {
                          /* this is the reading in which the initial BP run is    */
                          /* GDG's own first step on the whole window; >= 4 on     */
                          /* the GPU when set.                                     */
+  int merge_h1;          /* Sec. III: the window's H_1 columns (those reaching    */
+                         /* past its last block) merged toward an identity:       */
+                         /* 0 off; 1 columns with equal restrictions to the       */
+                         /* window merged (probabilities XOR-combined; the        */
+                         /* window's parity-check problem unchanged); 2 replaced  */
+                         /* by one column per last-block detector with the XOR    */
+                         /* of the H_1 columns holding it.  Not in the last       */
+                         /* window, and only with W > F (never committed).        */
 } qd_gdg_params;
 
 typedef struct qd_dem qd_dem;
@@ -496,16 +504,21 @@ qd_status qd_decoder_counters(qd_decoder* dec, long long out[5]);
 qd_status qd_decoder_counters_ex(qd_decoder* dec, long long* out, int n);
 qd_status qd_decoder_reset_counters(qd_decoder* dec, qd_stream_t stream);
 
-/* Shared path prefixes in shot mode (on by default; no counterpart in the
- * paper, whose threads snapshot the main branch's status only): decision
- * paths that made the same decisions at depths 1..D-1 -- the same guess
- * values, the same Alg. 3 thresholds and message restarts -- hold the same
- * state after the BP of step D, so the first path to get there leaves a
- * snapshot (in a pool the decoder allocated with its layouts) and paths
- * queued later resume from it instead of recomputing the prefix.  Results,
- * traces and out[1] of the counters are those of every path run from the
- * root; on = 0 runs every path from the root. */
-qd_status qd_decoder_set_fork(qd_decoder* dec, int on);
+/* Shot mode's decision-path scheduling (no counterpart in the paper, whose
+ * threads snapshot the main branch's status only), for windows with more
+ * paths than the CTA has warps.  mode 1: decision paths that made the same
+ * decisions at depths 1..D-1 -- the same guess values, the same Alg. 3
+ * thresholds and message restarts -- hold the same state after the BP of
+ * step D, so the first path to get there leaves a snapshot (in a pool the
+ * decoder allocated with its layouts) and paths queued later resume from it
+ * instead of recomputing the prefix.  mode 2 (the default) adds preemption:
+ * at every step boundary a warp whose path has fewer steps left than a
+ * waiting path parks its path (a snapshot of the same kind) and takes the
+ * other, longest remaining work first, so that no warp idles at the end of a
+ * shot while paths wait.  mode 0: every path from the root, one after
+ * another in a fixed order.  Results, traces and out[1] of the counters are
+ * the same in every mode. */
+qd_status qd_decoder_set_fork(qd_decoder* dec, int mode);
 
 #ifdef __cplusplus
 }

@@ -698,7 +698,131 @@ typedef struct {
   float* llr;
 } window_t;
 
-static void window_build(const qdo_dem* d, int W, int F, int k, window_t* wd) {
+const double* qdo__col_p(const qdo_dem* d);
+static void window_free(window_t* wd);
+
+typedef struct { double p; int col; } pcol_t;
+static int cmp_pcol(const void* a, const void* b) {
+  const pcol_t* x = a;
+  const pcol_t* y = b;
+  if (x->p < y->p) return -1;
+  if (x->p > y->p) return 1;
+  return x->col < y->col ? -1 : (x->col > y->col);
+}
+
+/* XOR-probability of independent mechanisms (Sec. II-B merging), folded in
+ * ascending (probability, DEM column), as the DEM's own merge does. */
+static double xor_fold(pcol_t* v, int n) {
+  qsort(v, n, sizeof(pcol_t), cmp_pcol);
+  double pm = 0.0;
+  for (int i = 0; i < n; ++i) pm = pm * (1.0 - v[i].p) + v[i].p * (1.0 - pm);
+  return pm;
+}
+
+/*
+ * Sec. III: the columns of H_1 -- the window columns that extend past the
+ * window's last block, restricted to it -- are merged to an identity matrix
+ * with recalculated priors.  READING (two variants, off by default; only for
+ * windows that are not the last and commit fewer blocks than they hold, so
+ * that no merged column is ever committed):
+ *   merge = 1: exact merges only -- H_1 columns whose restrictions to the
+ *     window are equal become one column at the first one's place, its
+ *     probability the XOR of theirs; the window's parity-check problem is
+ *     unchanged (the restrictions of weight one become the identity);
+ *   merge = 2: the identity itself -- every H_1 column is removed, and one
+ *     column per detector t of the last block is appended (t ascending),
+ *     flipping t alone with probability the XOR of the H_1 columns whose
+ *     restriction contains t (detector flips taken as independent).
+ */
+static void window_merge_h1(const qdo_dem* d, int merge, window_t* wd) {
+  const int w = qdo__w(d), hi = (wd->r0 + wd->nb) * w, lo_last = (wd->r0 + wd->nb - 1) * w;
+  const int* cptr = qdo__col_ptr(d);
+  const int* cdet = qdo__col_dets(d);
+  const double* cp = qdo__col_p(d);
+  int nc = wd->nc;
+  int* ext = calloc(nc > 0 ? nc : 1, sizeof(int));
+  for (int c = 0; c < nc; ++c) {
+    int g = wd->gcols[c];
+    for (int e = cptr[g]; e < cptr[g + 1]; ++e)
+      if (cdet[e] >= hi) ext[c] = 1;
+  }
+  int* gc = malloc(sizeof(int) * (nc + w + 1));
+  int* cpn = malloc(sizeof(int) * (nc + w + 2));
+  int* crn = malloc(sizeof(int) * (wd->ne + w + 1));
+  uint8_t* com = malloc(nc + w + 1);
+  float* ll = malloc(sizeof(float) * (nc + w + 1));
+  pcol_t* grp = malloc(sizeof(pcol_t) * (nc + 1));
+  int m = 0, ne = 0;
+  cpn[0] = 0;
+  for (int c = 0; c < nc; ++c) {
+    if (ext[c] && merge == 2) continue;
+    if (ext[c] && merge == 1) {
+      /* the first column of its restriction class keeps the class */
+      int first = 1;
+      for (int c2 = 0; c2 < c && first; ++c2)
+        if (ext[c2] && wd->col_ptr[c2 + 1] - wd->col_ptr[c2] == wd->col_ptr[c + 1] - wd->col_ptr[c] &&
+            memcmp(wd->col_rows + wd->col_ptr[c2], wd->col_rows + wd->col_ptr[c],
+                   sizeof(int) * (wd->col_ptr[c + 1] - wd->col_ptr[c])) == 0)
+          first = 0;
+      if (!first) continue;
+      int n = 0;
+      for (int c2 = c; c2 < nc; ++c2)
+        if (ext[c2] && wd->col_ptr[c2 + 1] - wd->col_ptr[c2] == wd->col_ptr[c + 1] - wd->col_ptr[c] &&
+            memcmp(wd->col_rows + wd->col_ptr[c2], wd->col_rows + wd->col_ptr[c],
+                   sizeof(int) * (wd->col_ptr[c + 1] - wd->col_ptr[c])) == 0) {
+          grp[n].p = cp[wd->gcols[c2]];
+          grp[n].col = wd->gcols[c2];
+          ++n;
+        }
+      double pm = xor_fold(grp, n);
+      ll[m] = (float)log((1.0 - pm) / pm);
+    } else {
+      ll[m] = wd->llr[c];
+    }
+    gc[m] = wd->gcols[c];
+    com[m] = wd->commit[c];
+    for (int e = wd->col_ptr[c]; e < wd->col_ptr[c + 1]; ++e) crn[ne++] = wd->col_rows[e];
+    cpn[++m] = ne;
+  }
+  if (merge == 2)
+    for (int t = 0; t < w; ++t) {
+      const int row = lo_last + t - wd->r0 * w;
+      int n = 0, rep = -1;
+      for (int c = 0; c < nc; ++c) {
+        if (!ext[c]) continue;
+        for (int e = wd->col_ptr[c]; e < wd->col_ptr[c + 1]; ++e)
+          if (wd->col_rows[e] == row) {
+            grp[n].p = cp[wd->gcols[c]];
+            grp[n].col = wd->gcols[c];
+            if (rep < 0) rep = wd->gcols[c];
+            ++n;
+          }
+      }
+      if (!n) continue;
+      double pm = xor_fold(grp, n);
+      gc[m] = rep;
+      com[m] = 0;
+      ll[m] = (float)log((1.0 - pm) / pm);
+      crn[ne++] = row;
+      cpn[++m] = ne;
+    }
+  free(grp);
+  free(ext);
+  free(wd->gcols);
+  free(wd->col_ptr);
+  free(wd->col_rows);
+  free(wd->commit);
+  free(wd->llr);
+  wd->gcols = gc;
+  wd->col_ptr = cpn;
+  wd->col_rows = crn;
+  wd->commit = com;
+  wd->llr = ll;
+  wd->nc = m;
+  wd->ne = ne;
+}
+
+static void window_build(const qdo_dem* d, int W, int F, int k, int merge, window_t* wd) {
   int info[7];
   qdo_window_info(d, W, F, k, info);
   wd->k = k;
@@ -716,6 +840,31 @@ static void window_build(const qdo_dem* d, int W, int F, int k, window_t* wd) {
   qdo_window_graph(d, W, F, k, wd->gcols, wd->col_ptr, wd->col_rows, wd->commit);
   const float* L = qdo__col_llr(d);
   for (int c = 0; c < wd->nc; ++c) wd->llr[c] = L[wd->gcols[c]];
+  if (merge && !wd->last && W > F) window_merge_h1(d, merge, wd);
+}
+
+int qdo_window_build(const qdo_dem* d, int W, int F, int k, int merge, int* info, int* gcols, int* col_ptr,
+                     int* col_rows, uint8_t* commit, float* llr) {
+  window_t wd;
+  window_build(d, W, F, k, merge, &wd);
+  int ncom = 0;
+  for (int c = 0; c < wd.nc; ++c) ncom += wd.commit[c];
+  info[0] = wd.r0;
+  info[1] = wd.nb;
+  info[2] = wd.nr;
+  info[3] = wd.nc;
+  info[4] = wd.ne;
+  info[5] = ncom;
+  info[6] = wd.last;
+  if (gcols) {
+    memcpy(gcols, wd.gcols, sizeof(int) * wd.nc);
+    memcpy(col_ptr, wd.col_ptr, sizeof(int) * (wd.nc + 1));
+    memcpy(col_rows, wd.col_rows, sizeof(int) * wd.ne);
+    memcpy(commit, wd.commit, wd.nc);
+    memcpy(llr, wd.llr, sizeof(float) * wd.nc);
+  }
+  window_free(&wd);
+  return 0;
 }
 
 static void window_free(window_t* wd) {
@@ -833,7 +982,7 @@ int qdo_decode_window(const qdo_dem* d, const qdo_params* P, int k, const uint8_
                       uint8_t* corr, int* info, int* short_cols, qdo_branch_summary* br,
                       qdo_step_record* steps, int8_t* final_status) {
   window_t wd;
-  window_build(d, P->W, P->F, k, &wd);
+  window_build(d, P->W, P->F, k, P->merge_h1, &wd);
   int rc = decode_window_impl(&wd, P, synd, corr, info, short_cols, br, steps, final_status);
   window_free(&wd);
   return rc;
@@ -859,7 +1008,7 @@ int qdo_run_shots(const qdo_dem* d, const qdo_params* P, const uint32_t* det_bit
   window_t* wins = malloc(sizeof(window_t) * nwin);
   int maxr = 0, maxc = 0;
   for (int k = 0; k < nwin; ++k) {
-    window_build(d, W, F, k, &wins[k]);
+    window_build(d, W, F, k, P->merge_h1, &wins[k]);
     if (wins[k].nr > maxr) maxr = wins[k].nr;
     if (wins[k].nc > maxc) maxc = wins[k].nc;
   }

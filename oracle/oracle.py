@@ -41,7 +41,7 @@ class QdoParams(C.Structure):
                 ("pa_other", C.c_float), ("pb_main", C.c_float), ("pb_other", C.c_float),
                 ("pb_d1", C.c_float), ("pc", C.c_float), ("pd", C.c_float),
                 ("pc_max_depth", C.c_int), ("n_unsat_min", C.c_int), ("side_max", C.c_int),
-                ("reinit_on_split", C.c_int), ("iters_first", C.c_int),
+                ("reinit_on_split", C.c_int), ("iters_first", C.c_int), ("merge_h1", C.c_int),
                 ("wts", C.POINTER(C.c_void_p)), ("wT", C.c_int), ("ranker", C.c_void_p),
                 ("dump", C.c_void_p), ("dump_n", C.c_void_p), ("dump_cap", C.c_int)]
 
@@ -96,6 +96,7 @@ def lib():
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.qdo_run_shots.argtypes = [C.c_void_p, P(QdoParams), C.c_void_p, C.c_void_p,
                                     C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        L.qdo_window_build.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int] + [C.c_void_p] * 6
         declare_select(L)
         _lib = L
     return _lib
@@ -323,18 +324,20 @@ class OracleDEM:
     def n_windows(self, W, F):
         return lib().qdo_n_windows(self.h, W, F)
 
-    def window(self, W, F, k):
+    def window(self, W, F, k, merge=0):
+        """Window k as GDG decodes it (merge: the H_1 merge of Sec. III, 0 none)."""
         info = np.zeros(7, np.int32)
-        lib().qdo_window_info(self.h, W, F, k, _ptr(info))
+        lib().qdo_window_build(self.h, W, F, k, merge, _ptr(info), None, None, None, None, None)
         r0, nb, nr, nc, ne, ncom, last = (int(x) for x in info)
         gcols = np.zeros(nc, np.int32)
         cp = np.zeros(nc + 1, np.int32)
         cr = np.zeros(max(ne, 1), np.int32)
         com = np.zeros(nc, np.uint8)
-        lib().qdo_window_graph(self.h, W, F, k, _ptr(gcols), _ptr(cp), _ptr(cr), _ptr(com))
+        llr = np.zeros(nc, np.float32)
+        lib().qdo_window_build(self.h, W, F, k, merge, _ptr(info), _ptr(gcols), _ptr(cp), _ptr(cr), _ptr(com),
+                               _ptr(llr))
         return dict(r0=r0, n_blocks=nb, n_rows=nr, n_cols=nc, n_edges=ne, n_commit=ncom,
-                    last=bool(last), gcols=gcols, col_ptr=cp, col_rows=cr[:ne], commit=com,
-                    llr=self.col_llr[gcols])
+                    last=bool(last), gcols=gcols, col_ptr=cp, col_rows=cr[:ne], commit=com, llr=llr)
 
     # ---- sampling ----
     def sample(self, seed, shot_offset, n_shots):
@@ -348,7 +351,7 @@ class OracleDEM:
         """dump: None or a RANK_REC array that receives path 0's candidate
         records (the returned info carries 'n_dump', the number produced)."""
         W, F = params["W"], params["F"]
-        win = self.window(W, F, k)
+        win = self.window(W, F, k, params.get("merge_h1", 0))
         synd = np.ascontiguousarray(synd, np.uint8)
         corr = np.zeros(win["n_cols"], np.uint8)
         info = np.zeros(4, np.int32)

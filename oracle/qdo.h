@@ -49,6 +49,8 @@ typedef struct {
   int reinit_on_split;   /* 1: a path restarts its messages where it splits    */
                          /* off another (appendix, multi-thread snapshots)     */
   int iters_first;       /* BP iterations of step D = 1 (0: iters_per_step)    */
+  int merge_h1;          /* Sec. III H_1 merge: 0 off, 1 equal restrictions,   */
+                         /* 2 identity with XOR priors (see gdg.c)             */
   /* Learned weighted min-sum (no counterpart in the paper; alpha of Eq. (1)
    * replaced by w[t][e]): wts[k] is window k's array [wT][n_edges] over the
    * full-window edges (CSC order), or NULL for plain alpha.  Iteration t
@@ -131,6 +133,11 @@ int qdo_n_windows(const qdo_dem* d, int W, int F);
 int qdo_window_info(const qdo_dem* d, int W, int F, int k, int* out);
 int qdo_window_graph(const qdo_dem* d, int W, int F, int k, int* gcols, int* col_ptr,
                      int* col_rows, uint8_t* commit);
+/* The window as GDG decodes it, after the H_1 merge `merge` (Sec. III; 0:
+ * none): info as qdo_window_info; with gcols != NULL also the columns (DEM
+ * column, or a merged class's first member), CSC, commit flags and priors. */
+int qdo_window_build(const qdo_dem* d, int W, int F, int k, int merge, int* info, int* gcols, int* col_ptr,
+                     int* col_rows, uint8_t* commit, float* llr);
 
 /* ---- sampling (Philox4x32-10, Salmon et al. SC'11) ---- */
 void qdo_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

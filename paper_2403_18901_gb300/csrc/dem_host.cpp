@@ -31,6 +31,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <set>
 
 #include "qdec_internal.h"
 
@@ -360,7 +362,84 @@ int n_windows(const DemHost& d, int W, int F) {
     if (r + W >= B) return k + 1;
 }
 
-bool build_window(const DemHost& d, int W, int F, int k, bool shorten, WindowHost& o) {
+namespace {
+// Probability that an odd number of the independent mechanisms fire, folded
+// in ascending (probability, column) order as the DEM's columns are.
+double odd_probability(std::vector<std::pair<double, int>> v) {
+  std::sort(v.begin(), v.end());
+  double pm = 0.0;
+  for (const auto& x : v) pm = pm * (1.0 - x.first) + x.first * (1.0 - pm);
+  return pm;
+}
+}  // namespace
+
+// The H_1 merge of Sec. III on window o (not the last window, W > F, so the
+// merged columns are never committed).  H_1 = the window columns that reach
+// past its last block, seen on the window's rows (all in the last block).
+// merge = 1: the H_1 columns of each equal restriction become one column at
+// the first one's place, with the odd-count probability of the class;
+// merge = 2: all H_1 columns are replaced by one column per detector t of
+// the last block (t ascending), probability the odd count of the H_1 columns
+// whose restriction holds t.
+static void merge_h1(const DemHost& d, int merge, int r1, WindowHost& o) {
+  const int hi = r1 * d.w, last0 = (r1 - 1) * d.w - o.row0;
+  std::vector<char> ext(o.n_cols, 0);
+  for (int c = 0; c < o.n_cols; ++c) {
+    const int g = o.gcols[c];
+    ext[c] = d.col_dets[d.col_ptr[g + 1] - 1] >= hi;  // detectors ascend: the last one decides
+  }
+  auto rows_of = [&](int c) {
+    return std::vector<uint16_t>(o.col_rows.begin() + o.col_ptr[c], o.col_rows.begin() + o.col_ptr[c + 1]);
+  };
+  std::vector<int> gcols;
+  std::vector<uint16_t> cptr{0}, crows;
+  std::vector<float> llr;
+  std::map<std::vector<uint16_t>, std::vector<std::pair<double, int>>> cls;  // restriction -> members
+  if (merge == 1)
+    for (int c = 0; c < o.n_cols; ++c)
+      if (ext[c]) cls[rows_of(c)].push_back({d.col_p[o.gcols[c]], o.gcols[c]});
+  std::set<std::vector<uint16_t>> seen;
+  for (int c = 0; c < o.n_cols; ++c) {
+    float l = o.llr[c];
+    if (ext[c]) {
+      if (merge == 2) continue;
+      const std::vector<uint16_t> r = rows_of(c);
+      if (!seen.insert(r).second) continue;  // folded into its class's first column
+      const double pm = odd_probability(cls[r]);
+      l = (float)std::log((1.0 - pm) / pm);
+    }
+    gcols.push_back(o.gcols[c]);
+    const std::vector<uint16_t> r = rows_of(c);
+    crows.insert(crows.end(), r.begin(), r.end());
+    cptr.push_back((uint16_t)crows.size());
+    llr.push_back(l);
+  }
+  if (merge == 2)
+    for (int t = 0; t < d.w; ++t) {
+      std::vector<std::pair<double, int>> members;
+      int rep = -1;
+      for (int c = 0; c < o.n_cols; ++c) {
+        if (!ext[c]) continue;
+        for (int e = o.col_ptr[c]; e < o.col_ptr[c + 1]; ++e)
+          if (o.col_rows[e] == last0 + t) {
+            members.push_back({d.col_p[o.gcols[c]], o.gcols[c]});
+            if (rep < 0) rep = o.gcols[c];
+          }
+      }
+      if (members.empty()) continue;
+      const double pm = odd_probability(members);
+      gcols.push_back(rep);
+      crows.push_back((uint16_t)(last0 + t));
+      cptr.push_back((uint16_t)crows.size());
+      llr.push_back((float)std::log((1.0 - pm) / pm));
+    }
+  o.gcols = gcols;
+  o.col_ptr = cptr;
+  o.col_rows = crows;
+  o.llr = llr;
+}
+
+bool build_window(const DemHost& d, int W, int F, int k, bool shorten, WindowHost& o, int merge) {
   const int B = d.R + 1, w = d.w;
   o = WindowHost();
   o.k = k;
@@ -391,6 +470,12 @@ bool build_window(const DemHost& d, int W, int F, int k, bool shorten, WindowHos
     o.col_ptr.push_back((uint16_t)o.col_rows.size());
     o.llr.push_back(d.col_llr[c]);
   }
+  if (merge && !o.last && W > F) merge_h1(d, merge, r1, o);
+  for (float l : o.llr)
+    if (!(l > std::ldexp(1.0f, -15) && l < 16.0f)) {
+      set_error("window prior LLR outside (2^-15, 16); Eq. (5) would not be exact");
+      return false;
+    }
   o.n_cols = (int)o.gcols.size();
   o.n_edges = (int)o.col_rows.size();
   // 16-bit edge ids; row and column ids below 2^15, as the decoder packs

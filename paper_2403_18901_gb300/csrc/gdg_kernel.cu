@@ -649,17 +649,52 @@ struct PathOut {
 // prefix from the root.  A snapshot is a 32-byte header (depth, iterations,
 // iterations since the messages were initialised, the `first` flag, the
 // producing path, the prefix's edge visits) and a copy of the slot.
+//
+// Preemption (sched): the paths of a shot outnumber the warps, and the main
+// branch is the longest, so a fixed assignment leaves warps idle at the end
+// of the shot.  At every step boundary a warp compares the steps its path
+// has left with those of the waiting paths -- parked paths, and queued paths
+// whose planned snapshot is ready -- and when one has more than one step
+// more, it parks its own path (a snapshot of the same form in the path's own
+// buffer) and switches to it: longest remaining work first.  Path states
+// (sched words): 0 queued, 1 running, 2 | D << 8 parked after the BP of
+// step D, 3 done.
 struct ForkCtx {
   const char* src;       // snapshot to resume from (nullptr: from the root)
   const int16_t* chain;  // this path's snapshot node by depth (index D - 1), -1: none; nullptr: no snapshots
   int* flags;            // per node: 0 free, 1 being written, 2 ready
-  char* pool;            // this CTA's snapshots, `stride` bytes apart
+  char* pool;            // this CTA's snapshots, `stride` bytes apart: nodes, then one per path
   unsigned stride;
   char* slot;            // this warp's slot and its size
   unsigned slot_bytes;
   const StepTrace* st0;  // the shot's step records (path p at st0 + p * dmx), or nullptr
+  unsigned* sched;       // per path state word (nullptr: no preemption)
+  const int16_t* fnode;  // per path: its planned snapshot node (-1: none) and that node's depth
+  const int16_t* fdep;
+  int n_nodes;
 };
 constexpr unsigned kSnapHeader = kSnapHeaderBytes;
+enum { PS_QUEUED = 0, PS_RUNNING = 1, PS_PARKED = 2, PS_DONE = 3 };
+
+// Snapshot of a path's state after the BP of step D (all lanes of the group).
+template <class Grp>
+__device__ void write_snapshot(char* dst, const ForkCtx& F, const Grp& g, int D, int iters, int tw, bool first,
+                               int producer, long long vs) {
+  if (g.rank == 0) {
+    int* h = (int*)dst;
+    __stcg(h, D);
+    __stcg(h + 1, iters);
+    __stcg(h + 2, tw);
+    __stcg(h + 3, first ? 1 : 0);
+    __stcg(h + 4, producer);
+    __stcg((long long*)(dst + 24), vs);
+  }
+  const uint4* s4 = (const uint4*)F.slot;
+  uint4* d4 = (uint4*)(dst + kSnapHeader);
+  for (unsigned x = g.rank; x < F.slot_bytes / 16u; x += g.size) __stcg(d4 + x, s4[x]);
+  __threadfence();  // the snapshot and this path's decision records before its flag
+  g.sync();
+}
 
 // Check-node update of Eq. (1) over the active VNs of one decision path, TPC
 // lanes per check (a template parameter, so that the loops and the group
@@ -730,9 +765,11 @@ __device__ __forceinline__ bool check_pass(const KParams& P, const ShortG& G, co
 // One decision path of Alg. 2 on the shortened window, run by group g.
 // LW: learned per-edge weights instead of alpha (compiled separately so the
 // plain decoder carries no weight lookups).
+// Returns -1 when the path is finished, or (preemption) the path this group
+// switches to after parking this one; *claimed is the state word it took.
 template <bool LW, class Grp>
-__device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int id, const Grp& g,
-                         const PathOut& out, int dmx, const ForkCtx& F) {
+__device__ int run_path(const KParams& P, const ShortG& G, const Slot& B, int id, const Grp& g,
+                        const PathOut& out, int dmx, const ForkCtx& F, unsigned* claimed = nullptr) {
   const int nr = G.nr, ns = G.ns, R = g.rank, S = g.size;
   // one lane per check for a warp; small lane groups per check for a CTA
   const int tpc = Grp::kWarp ? 1 : path_lanes_per_check(S, nr);
@@ -761,7 +798,8 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
     const uint4* s4 = (const uint4*)(F.src + kSnapHeader);
     uint4* d4 = (uint4*)F.slot;
     for (unsigned x = R; x < F.slot_bytes / 16u; x += S) d4[x] = __ldcg(s4 + x);
-    if (out.st) {  // the decision records of the shared prefix are the producer's
+    // a path resumed from its own parking snapshot keeps its records
+    if (out.st && producer != id) {  // the decision records of the shared prefix are the producer's
       const StepTrace* ps = F.st0 + (size_t)producer * dmx;
       for (int q = R; q < dmx; q += S) {
         StepTrace r{-2, -1, 0, 0, 0};
@@ -873,25 +911,49 @@ __device__ void run_path(const KParams& P, const ShortG& G, const Slot& B, int i
       int won = 0;
       if (R == 0) won = atomicCAS(&F.flags[n], 0, 1) == 0;
       if (g.any(won != 0)) {
-        const long long vs = g.sum_ll(visits + inherited);
-        char* dst = F.pool + (size_t)n * F.stride;
-        if (R == 0) {
-          int* h = (int*)dst;
-          __stcg(h, D);
-          __stcg(h + 1, iters);
-          __stcg(h + 2, tw);
-          __stcg(h + 3, first ? 1 : 0);
-          __stcg(h + 4, id);
-          __stcg((long long*)(dst + 24), vs);
-        }
-        const uint4* s4 = (const uint4*)F.slot;
-        uint4* d4 = (uint4*)(dst + kSnapHeader);
-        for (unsigned x = R; x < F.slot_bytes / 16u; x += S) __stcg(d4 + x, s4[x]);
-        __threadfence();  // the snapshot and this path's decision records before the flag
-        g.sync();
+        write_snapshot(F.pool + (size_t)n * F.stride, F, g, D, iters, tw, first, id, g.sum_ll(visits + inherited));
         if (R == 0) atomicExch(&F.flags[n], 2);
       }
     }
+    }
+    // preemption point: switch to a waiting path with more steps left (not
+    // right where this run resumed)
+    if (F.sched && D < dmax && !(F.src && D == D0)) {
+      int c = -1;
+      unsigned cw = 0;
+      if (R == 0) {
+        int best = dmax - D + 2;  // more than one step more than this path's dmax - D + 1
+        for (int p = 0; p < P.nb; ++p) {
+          const unsigned w = *(volatile unsigned*)&F.sched[p];
+          int at = 0;
+          if ((w & 3u) == PS_PARKED) at = (int)(w >> 8);
+          else if (w == PS_QUEUED && F.fnode[p] >= 0 && *(volatile int*)&F.flags[F.fnode[p]] == 2) at = F.fdep[p];
+          if (!at) continue;
+          const int rem = path_dmax(P, p, path_split(P, p)) - at + 1;
+          if (rem > best) {
+            best = rem;
+            c = p;
+            cw = w;
+          }
+        }
+        if (c >= 0 && atomicCAS(&F.sched[c], cw, (unsigned)PS_RUNNING) != cw) c = -1;
+      }
+      const unsigned cu = g.min_u(R == 0 && c >= 0 ? (unsigned)c : 0xFFFFFFFFu);  // lane 0's choice
+      c = cu == 0xFFFFFFFFu ? -1 : (int)cu;
+      if (c >= 0) {
+        const unsigned cw0 = g.min_u(R == 0 ? cw : 0xFFFFFFFFu);
+        if (claimed) *claimed = cw0;
+        // park: this path resumes from its own snapshot after the BP of step D
+        const long long own = g.sum_ll(visits);
+        write_snapshot(F.pool + (size_t)(F.n_nodes + id) * F.stride, F, g, D, iters, tw, first, id,
+                       g.sum_ll(visits + inherited));
+        if (R == 0) {
+          atomicExch(&F.sched[id], (unsigned)PS_PARKED | ((unsigned)D << 8));
+          if (out.exec) atomicAdd((unsigned long long*)out.exec, (unsigned long long)own);
+        }
+        g.sync();
+        return c;
+      }
     }
     if (D == dmax) break;  // no decimation after the last BP step
     {
@@ -996,8 +1058,10 @@ done:
     if (out.btr) *out.btr = BranchTrace{status, depth, iters, 0, status == BR_CONVERGED ? pm : CUDART_INF};
     atomicAdd((unsigned long long*)out.visits, (unsigned long long)(visits + inherited));
     if (out.exec) atomicAdd((unsigned long long*)out.exec, (unsigned long long)visits);
+    if (F.sched) atomicExch(&F.sched[id], (unsigned)PS_DONE);
   }
   g.sync();
+  return -1;
 }
 
 // Trace layout of one shot: int32 head[4]; BranchTrace[nb]; StepTrace[nb][dmx];
@@ -1811,27 +1875,82 @@ __device__ void shot_body(const DecodeArgs& A, long long shot, char* sm, Stager&
       const Slot B = make_slot(slot, L);
       const WarpGrp g{lane};
       // snapshots of shared prefixes, when planned and this CTA has a pool
-      const bool fork = A.F.pool && A.F.n_nodes > 0 && (int)blockIdx.x < A.F.pool_ctas;
+      // shared prefixes and preemption, when planned and this CTA has a pool
+      const bool fork = A.F.pool && (int)blockIdx.x < A.F.pool_ctas;
+      const int nb = A.P.nb;
       ForkCtx F{};
       F.flags = (int*)(sm + L.red);
       F.pool = fork ? A.F.pool + (size_t)blockIdx.x * A.F.cta_bytes : nullptr;
       F.stride = kSnapHeader + L.b_size;
       F.slot = slot;
       F.slot_bytes = L.b_size;
-      F.st0 = tr ? (const StepTrace*)(tr + trace_off_st(A.P.nb)) : nullptr;
+      F.st0 = tr ? (const StepTrace*)(tr + trace_off_st(nb)) : nullptr;
+      F.sched = (fork && A.F.sched) ? (unsigned*)(sm + L.red) + kMaxForkNodes : nullptr;
+      F.fnode = A.F.fnode;
+      F.fdep = A.F.fdep;
+      F.n_nodes = A.F.n_nodes;
+      int next = -1;  // the path taken at a preemption point
+      unsigned next_w = 0;
       while (true) {
-        int pos = 0;
-        if (lane == 0) pos = atomicAdd(&misc[2], 1);
-        pos = __shfl_sync(FULL, pos, 0);
-        if (pos >= A.P.nb) break;
-        const int id = fork ? (int)A.F.order[pos] : path_at(A.P, pos);
+        int id = -1;
+        unsigned w0 = PS_QUEUED;  // the taken path's state word: queued or parked after step D
+        if (next >= 0) {
+          id = next;
+          w0 = next_w;
+          next = -1;
+        } else {
+          while (true) {  // the next queued path that no preemption took
+            int pos = 0;
+            if (lane == 0) pos = atomicAdd(&misc[2], 1);
+            pos = __shfl_sync(FULL, pos, 0);
+            if (pos >= nb) break;
+            const int cand = fork ? (int)A.F.order[pos] : path_at(A.P, pos);
+            int ok = 1;
+            if (F.sched && lane == 0) ok = atomicCAS(&F.sched[cand], (unsigned)PS_QUEUED, (unsigned)PS_RUNNING) == PS_QUEUED;
+            if (__shfl_sync(FULL, ok, 0)) {
+              id = cand;
+              break;
+            }
+          }
+          if (id < 0 && F.sched) {  // a parked path, the one with the most steps left
+            int c = -1;
+            unsigned cw = 0;
+            if (lane == 0)
+              for (int tries = 0; tries < 4 * nb; ++tries) {
+                c = -1;
+                int best = 0;
+                for (int p = 0; p < nb; ++p) {
+                  const unsigned w = *(volatile unsigned*)&F.sched[p];
+                  if ((w & 3u) != PS_PARKED) continue;
+                  const int rem = path_dmax(A.P, p, path_split(A.P, p)) - (int)(w >> 8) + 1;
+                  if (rem > best) {
+                    best = rem;
+                    c = p;
+                    cw = w;
+                  }
+                }
+                if (c < 0 || atomicCAS(&F.sched[c], cw, (unsigned)PS_RUNNING) == cw) break;
+                c = -1;
+              }
+            c = __shfl_sync(FULL, c, 0);
+            cw = __shfl_sync(FULL, cw, 0);
+            if (c >= 0) {
+              id = c;
+              w0 = cw;
+            }
+          }
+          if (id < 0) break;
+        }
         PathOut o = trace_out(A, tr, id, shot);
         o.status = &res_status[id];
         o.pm = &res_pm[id];
         o.ebits = res_e + (size_t)id * L.sw;
-        F.chain = fork ? A.F.chain + (size_t)id * A.dmx : nullptr;
+        F.chain = (fork && F.n_nodes > 0) ? A.F.chain + (size_t)id * A.dmx : nullptr;
         F.src = nullptr;
-        if (fork) {  // the deepest ready snapshot on this path's chain
+        if ((w0 & 3u) == PS_PARKED) {  // its own parking snapshot
+          __threadfence();
+          F.src = F.pool + (size_t)(F.n_nodes + id) * F.stride;
+        } else if (F.chain) {  // the deepest ready snapshot on this path's chain
           int node = -1;
           if (lane == 0) {
             const int dm = path_dmax(A.P, id, path_split(A.P, id));
@@ -1846,7 +1965,7 @@ __device__ void shot_body(const DecodeArgs& A, long long shot, char* sm, Stager&
             F.src = F.pool + (size_t)node * F.stride;
           }
         }
-        run_path<LW>(A.P, G, B, id, g, o, A.dmx, F);
+        next = run_path<LW>(A.P, G, B, id, g, o, A.dmx, F, &next_w);
       }
     }
     __syncthreads();
@@ -1882,7 +2001,8 @@ __global__ void __launch_bounds__(256, 2) decode_shot_kernel(DecodeArgs A) {
       misc[0] = atomicAdd(A.work, 1);
       misc[2] = 0;  // decision-path queue, path 0 first
     }
-    if (threadIdx.x < kMaxForkNodes) ((int*)(sm + A.L.red))[threadIdx.x] = 0;  // no snapshot yet
+    // no snapshot yet, every path queued
+    if (threadIdx.x < 2 * kMaxForkNodes) ((int*)(sm + A.L.red))[threadIdx.x] = 0;
     __syncthreads();
     const long long shot = misc[0];
     if (shot >= A.n_shots) break;

@@ -102,14 +102,20 @@ struct WinDev {
 // (chain[p * dmx + D - 1], -1: none).  Snapshots of CTA b live at
 // pool + b * cta_bytes, nodes `stride` bytes apart; pool = nullptr: no
 // snapshots, the path-queue order of path_at.
-constexpr int kMaxForkNodes = 64;  // node flags live in the shot-mode CTA's 512-byte reduction area
+// node flags, then path states, live in the shot-mode CTA's 512-byte reduction area
+constexpr int kMaxForkNodes = 64;
 constexpr unsigned kSnapHeaderBytes = 32;  // a snapshot's header, before the copy of the slot
+// fnode / fdep: each path's planned snapshot node (-1: none) and its depth;
+// sched != 0: preemption at step boundaries, each path's parking snapshot
+// after the n_nodes node snapshots of the CTA's pool.
 struct ForkDev {
   const int16_t* order;
   const int16_t* chain;
+  const int16_t* fnode;
+  const int16_t* fdep;
   char* pool;
   size_t cta_bytes;
-  int n_nodes, pool_ctas;
+  int n_nodes, pool_ctas, sched;
 };
 
 // A window's Tanner graph for the learned weighted min-sum (training kernels).

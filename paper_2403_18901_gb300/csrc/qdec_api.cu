@@ -85,6 +85,7 @@ struct WinGpu {
   // node chain [nb][dmx]; fork_nodes = 0: none
   int16_t* d_fork = nullptr;
   int fork_nodes = 0;
+  bool fork_on = false;
 };
 
 template <class T>
@@ -131,6 +132,7 @@ struct qd_decoder {
   size_t snap_cta_bytes = 0;
   int snap_ctas = 0;
   bool fork_on = true;
+  bool sched_on = true;  // preemption at step boundaries (with fork_on)
   uint32_t *d_det = nullptr, *d_obs = nullptr, *d_pred = nullptr, *d_fail = nullptr, *d_resid = nullptr;
   long long* d_nfail = nullptr;
 };
@@ -165,8 +167,9 @@ qd_status ensure_uscratch(qd_decoder* dec, bool all) {
 // that share the deepest prefix with a path before them; node = the deepest
 // state such a later path shares with an earlier one.
 struct ForkPlan {
-  std::vector<int16_t> order, chain;
+  std::vector<int16_t> order, chain, fnode, fdep;
   int n_nodes = 0;
+  bool on = false;  // more paths than warps: a plan (preemption, and snapshots when n_nodes > 0)
 };
 
 ForkPlan fork_plan(const qd::KParams& P, int dmx, int wave) {
@@ -219,15 +222,23 @@ ForkPlan fork_plan(const qd::KParams& P, int dmx, int wave) {
       const std::vector<int> k = key_of(q, share[q]);
       if (std::find(keys.begin(), keys.end(), k) == keys.end()) keys.push_back(k);
     }
-  if (keys.empty() || (int)keys.size() > qd::kMaxForkNodes) return F;
+  if (nb <= wave || nb > qd::kMaxForkNodes || (int)keys.size() > qd::kMaxForkNodes) return F;
+  F.on = true;
   F.n_nodes = (int)keys.size();
   F.order.assign(order.begin(), order.end());
   F.chain.assign((size_t)nb * dmx, (int16_t)-1);
-  for (int p = 0; p < nb; ++p)
+  F.fnode.assign(nb, (int16_t)-1);
+  F.fdep.assign(nb, (int16_t)0);
+  for (int p = 0; p < nb; ++p) {
     for (int D = 1; D <= dmax(p) && D <= dmx; ++D) {
       const auto it = std::find(keys.begin(), keys.end(), key_of(p, D));
       if (it != keys.end()) F.chain[(size_t)p * dmx + D - 1] = (int16_t)(it - keys.begin());
     }
+    if (share[p] >= 1) {
+      F.fnode[p] = F.chain[(size_t)p * dmx + share[p] - 1];
+      F.fdep[p] = (int16_t)share[p];
+    }
+  }
   return F;
 }
 
@@ -321,13 +332,17 @@ qd_status configure_layouts(qd_decoder* dec, bool hist, const char* who) {
   int ctas = 0;
   for (WinGpu& g : dec->wins) {
     const ForkPlan F = fork_plan(dec->kp, dec->dmx, std::max(1, g.L.nslots));
+    g.fork_on = F.on;
     g.fork_nodes = F.n_nodes;
-    if (!F.n_nodes) continue;
+    if (!F.on) continue;
     std::vector<int16_t> v(F.order);
     v.insert(v.end(), F.chain.begin(), F.chain.end());
-    if (!g.d_fork) QD_CK(cudaMalloc(&g.d_fork, sizeof(int16_t) * (size_t)dec->kp.nb * (1 + dec->dmx)));
+    v.insert(v.end(), F.fnode.begin(), F.fnode.end());
+    v.insert(v.end(), F.fdep.begin(), F.fdep.end());
+    if (!g.d_fork) QD_CK(cudaMalloc(&g.d_fork, sizeof(int16_t) * (size_t)dec->kp.nb * (3 + dec->dmx)));
     QD_CK(cudaMemcpy(g.d_fork, v.data(), sizeof(int16_t) * v.size(), cudaMemcpyHostToDevice));
-    cta_bytes = std::max(cta_bytes, (size_t)F.n_nodes * (qd::kSnapHeaderBytes + g.L.b_size));
+    // node snapshots, then one parking snapshot per path
+    cta_bytes = std::max(cta_bytes, (size_t)(F.n_nodes + dec->kp.nb) * (qd::kSnapHeaderBytes + g.L.b_size));
     ctas = std::max(ctas, dec->sm_count * std::max(g.grid_per_sm, g.grid_g));
   }
   if (cta_bytes > dec->snap_cta_bytes || ctas > dec->snap_ctas) {
@@ -479,6 +494,7 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
     return QD_EUNSUPPORTED;
   }
   QD_REQ(p->iters_first >= 0, "qd_decoder_create: iters_first < 0");
+  QD_REQ(p->merge_h1 >= 0 && p->merge_h1 <= 2, "qd_decoder_create: merge_h1 must be 0, 1 or 2");
   QD_REQ(p->side_max == 0 || (p->side_max >= p->k_guess && p->side_max <= 32),
          "qd_decoder_create: side_max must be 0 or in [k_guess, 32]");
   QD_REQ(p->d_max_other >= p->k_guess, "qd_decoder_create: d_max_other < k_guess");
@@ -527,7 +543,7 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
   dec->wins.resize(nwin);
   for (int w = 0; w < nwin; ++w) {
     WinGpu& g = dec->wins[w];
-    if (!qd::build_window(dem->h, p->W, p->F, w, p->shorten != 0, g.h)) return QD_EINVAL;
+    if (!qd::build_window(dem->h, p->W, p->F, w, p->shorten != 0, g.h, p->merge_h1)) return QD_EINVAL;
     const auto& h = g.h;
     dec->corr_words = std::max(dec->corr_words, (h.n_cols + 31) / 32);
     dec->ns_max = std::max(dec->ns_max, h.n_short);
@@ -638,13 +654,17 @@ namespace {
 qd::ForkDev fork_dev(const qd_decoder* dec, const WinGpu& g) {
   qd::ForkDev F{};
   // the candidate dump records path 0's every step, so path 0 runs from the root
-  if (!dec->fork_on || !g.fork_nodes || !dec->d_snap || dec->kp.dump) return F;
+  if (!dec->fork_on || !g.fork_on || !dec->d_snap || dec->kp.dump) return F;
+  const int nb = dec->kp.nb;
   F.order = g.d_fork;
-  F.chain = g.d_fork + dec->kp.nb;
+  F.chain = g.d_fork + nb;
+  F.fnode = F.chain + (size_t)nb * dec->dmx;
+  F.fdep = F.fnode + nb;
   F.pool = dec->d_snap;
   F.cta_bytes = dec->snap_cta_bytes;
   F.n_nodes = g.fork_nodes;
   F.pool_ctas = dec->snap_ctas;
+  F.sched = dec->sched_on ? 1 : 0;
   return F;
 }
 }  // namespace
@@ -866,7 +886,9 @@ qd_status qd_decoder_counters_ex(qd_decoder* dec, long long* out, int n) {
 
 qd_status qd_decoder_set_fork(qd_decoder* dec, int on) {
   QD_REQ(dec, "null argument");
+  QD_REQ(on >= 0 && on <= 2, "qd_decoder_set_fork: on must be 0, 1 or 2");
   dec->fork_on = on != 0;
+  dec->sched_on = on == 2;
   return QD_OK;
 }
 

@@ -49,7 +49,8 @@ bool build_dem_host(const qd_bb_code& code, const qd_noise& noise, DemHost& out)
 // Code-capacity models of the appendices (BSC on data qubits; [H_X | I]).
 bool build_dem_code_capacity(const qd_bb_code& code, double p_data, double p_synd, DemHost& out);
 int n_windows(const DemHost& d, int W, int F);
-bool build_window(const DemHost& d, int W, int F, int k, bool shorten, WindowHost& out);
+// merge: the H_1 merge of Sec. III (0 none, 1 equal restrictions, 2 identity)
+bool build_window(const DemHost& d, int W, int F, int k, bool shorten, WindowHost& out, int merge = 0);
 
 size_t trace_bytes_per_shot(int nb, int dmx, int ns_max);
 cudaError_t set_decode_smem(size_t bytes);

@@ -40,7 +40,7 @@ class GdgParams(C.Structure):
                 ("pa_other", C.c_float), ("pb_main", C.c_float), ("pb_other", C.c_float),
                 ("pb_d1", C.c_float), ("pc", C.c_float), ("pd", C.c_float),
                 ("pc_max_depth", C.c_int), ("n_unsat_min", C.c_int), ("side_max", C.c_int),
-                ("reinit_on_split", C.c_int), ("iters_first", C.c_int)]
+                ("reinit_on_split", C.c_int), ("iters_first", C.c_int), ("merge_h1", C.c_int)]
 
 
 class DemInfo(C.Structure):
@@ -332,9 +332,11 @@ class Decoder:
         _check(lib().qd_decoder_counters_ex(self.h, _ptr(out), int(n)))
         return out
 
-    def set_fork(self, on):
-        """Shot mode: resume decision paths from snapshots of shared prefixes (default on)."""
-        _check(lib().qd_decoder_set_fork(self.h, int(bool(on))))
+    def set_fork(self, mode):
+        """Shot mode's path scheduling: 0 every path from the root, in a fixed
+        order; 1 paths resume from snapshots of shared prefixes; 2 (default)
+        also preemption at step boundaries, longest remaining work first."""
+        _check(lib().qd_decoder_set_fork(self.h, int(mode)))
 
     def reset_counters(self, stream=None):
         _check(lib().qd_decoder_reset_counters(self.h, _stream(stream)))

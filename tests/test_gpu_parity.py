@@ -404,17 +404,19 @@ def test_initial_bp_as_first_step_bit_exact(key, R, n, mode, tw):
     _pipeline(key, R, 0.003, params, n=n, seed=int(key) * 1000 + 7, trace_windows=tw, mode=mode)
 
 
-@pytest.mark.parametrize("pname,p,n", [("configured", 0.003, 400), ("configured", 0.002, 300), ("paper", 0.004, 300)])
-def test_shared_prefixes_change_nothing(pname, p, n):
+@pytest.mark.parametrize("pname,p,n,mode", [("configured", 0.003, 400, 2), ("configured", 0.002, 300, 2),
+                                            ("paper", 0.004, 300, 2), ("configured", 0.003, 300, 1)])
+def test_shared_prefixes_change_nothing(pname, p, n, mode):
     """Shot mode resumes decision paths from snapshots of the prefixes they
-    share with paths queued before them.  Every output -- corrections,
+    share with paths queued before them (mode 1), and parks and resumes
+    paths at step boundaries to balance the warps (mode 2).  Every output -- corrections,
     statuses, the whole per-shot trace (every path's status, depth,
     iterations, metric, step log and final statuses) -- and the per-path work
     count equal those of every path run from the root; only the executed
     work drops."""
     d = qdec.Dem(CODES["144"], p, 12)
     runs = []
-    for fork in (True, False):
+    for fork in (mode, 0):
         dec = qdec.Decoder(d, preset(pname, k_guess=4, p=p), max_shots=n)
         dec.set_launch(1)
         dec.set_fork(fork)
