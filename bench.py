@@ -512,19 +512,26 @@ def ranker_288(args, torch, qdec, CODES, preset, latency_fn):
 
 def readings(args, torch, qdec, CODES, preset):
     """The configured preset (alpha = 0.625, 100 initial BP iterations, steps
-    of 10) on the headline workload under two changes: the second reading of
-    "100 initial BP iterations" (no pre-BP and no shortening; GDG's first
-    step runs 100 iterations on the whole window), and alpha = 1.0 (the
-    paper's) with the preset otherwise unchanged."""
+    of 10) on the headline workload under single changes: the second reading
+    of "100 initial BP iterations" (no pre-BP and no shortening; GDG's first
+    step runs 100 iterations on the whole window), alpha = 1.0 (the paper's)
+    with the preset otherwise unchanged, and the two readings of the H_1
+    merge of Sec. III; the paper preset with and without the H_1 merges."""
     dem = qdec.Dem(CODES[CODE_KEY], P_PHYS, ROUNDS)
     out = {}
-    for name, over, n in (("initial_bp_as_first_step", dict(n_pre=0, shorten=0, iters_first=100), args.reading_shots),
-                          ("alpha_1.0", dict(alpha=1.0), args.shots)):
-        params = preset("configured", k_guess=K_GUESS, p=P_PHYS, **over)
+    for name, pname, over, n in (
+            ("initial_bp_as_first_step", "configured", dict(n_pre=0, shorten=0, iters_first=100), args.reading_shots),
+            ("alpha_1.0", "configured", dict(alpha=1.0), args.shots),
+            ("h1_merge_equal_restrictions", "configured", dict(merge_h1=1), args.shots),
+            ("h1_merge_identity", "configured", dict(merge_h1=2), args.shots),
+            ("paper_preset", "paper", {}, args.shots),
+            ("paper_h1_merge_equal_restrictions", "paper", dict(merge_h1=1), args.shots),
+            ("paper_h1_merge_identity", "paper", dict(merge_h1=2), args.shots)):
+        params = preset(pname, k_guess=K_GUESS, p=P_PHYS, **over)
         B = min(n, args.shots)
         dec = qdec.Decoder(dem, params, max_shots=B)
         t, f, f11, gdg = decode_pass(torch, dec, dem, args.seed + 5, n, B)
-        out[name] = {"change": over, "shots": n, "windows_per_s": n * dec.n_windows / t,
+        out[name] = {"preset": pname, "change": over, "shots": n, "windows_per_s": n * dec.n_windows / t,
                      "gdg_windows_frac": gdg / (n * dec.n_windows), "ler_per_round": ler_entry(f, n),
                      "failures_eq11_only": f11}
     return out

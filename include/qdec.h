@@ -158,6 +158,16 @@ qd_status qd_dem_info(const qd_dem* dem, qd_dem_info_t* out);
  * log((1-p_i)/p_i), Sec. II-A).  Any pointer may be NULL. */
 qd_status qd_dem_columns(const qd_dem* dem, int* col_ptr, int* col_dets, uint32_t* obs,
                          double* prob, float* llr);
+/* Window k of the (W,F) schedule as the decoder builds it (Sec. III, Eq. (8);
+ * host only, no device call), after the H_1 merge `merge_h1` (see
+ * qd_gdg_params; 0: none): info[7] = (first block, blocks, rows, columns,
+ * edges, committed columns, last window); with gcols != NULL also gcols[n_cols]
+ * (DEM column, or a merged class's first member), col_ptr[n_cols+1],
+ * col_rows[n_edges] (window rows, ascending per column) and llr[n_cols]
+ * (the priors GDG uses).  QD_EINVAL for a bad window index or a merged prior
+ * outside (2^-15, 16). */
+qd_status qd_dem_window(const qd_dem* dem, int W, int F, int k, int merge_h1, int info[7], int* gcols,
+                        int* col_ptr, int* col_rows, float* llr);
 qd_status qd_dem_destroy(qd_dem* dem);
 
 /*

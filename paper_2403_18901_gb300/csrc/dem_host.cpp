@@ -383,8 +383,9 @@ double odd_probability(std::vector<std::pair<double, int>> v) {
 // whose restriction holds t.
 static void merge_h1(const DemHost& d, int merge, int r1, WindowHost& o) {
   const int hi = r1 * d.w, last0 = (r1 - 1) * d.w - o.row0;
-  std::vector<char> ext(o.n_cols, 0);
-  for (int c = 0; c < o.n_cols; ++c) {
+  const int nc = (int)o.gcols.size();  // (n_cols is set after the merge)
+  std::vector<char> ext(nc, 0);
+  for (int c = 0; c < nc; ++c) {
     const int g = o.gcols[c];
     ext[c] = d.col_dets[d.col_ptr[g + 1] - 1] >= hi;  // detectors ascend: the last one decides
   }
@@ -396,10 +397,10 @@ static void merge_h1(const DemHost& d, int merge, int r1, WindowHost& o) {
   std::vector<float> llr;
   std::map<std::vector<uint16_t>, std::vector<std::pair<double, int>>> cls;  // restriction -> members
   if (merge == 1)
-    for (int c = 0; c < o.n_cols; ++c)
+    for (int c = 0; c < nc; ++c)
       if (ext[c]) cls[rows_of(c)].push_back({d.col_p[o.gcols[c]], o.gcols[c]});
   std::set<std::vector<uint16_t>> seen;
-  for (int c = 0; c < o.n_cols; ++c) {
+  for (int c = 0; c < nc; ++c) {
     float l = o.llr[c];
     if (ext[c]) {
       if (merge == 2) continue;
@@ -418,7 +419,7 @@ static void merge_h1(const DemHost& d, int merge, int r1, WindowHost& o) {
     for (int t = 0; t < d.w; ++t) {
       std::vector<std::pair<double, int>> members;
       int rep = -1;
-      for (int c = 0; c < o.n_cols; ++c) {
+      for (int c = 0; c < nc; ++c) {
         if (!ext[c]) continue;
         for (int e = o.col_ptr[c]; e < o.col_ptr[c + 1]; ++e)
           if (o.col_rows[e] == last0 + t) {

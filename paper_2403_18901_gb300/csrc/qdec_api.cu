@@ -431,6 +431,25 @@ qd_status qd_dem_columns(const qd_dem* d, int* col_ptr, int* col_dets, uint32_t*
   return QD_OK;
 }
 
+qd_status qd_dem_window(const qd_dem* d, int W, int F, int k, int merge_h1, int info[7], int* gcols, int* col_ptr,
+                        int* col_rows, float* llr) {
+  QD_REQ(d && info, "qd_dem_window: null argument");
+  QD_REQ(W >= 1 && F >= 1 && F <= W, "qd_dem_window: need 1 <= F <= W");
+  QD_REQ(k >= 0 && k < qd::n_windows(d->h, W, F), "qd_dem_window: window out of range");
+  QD_REQ(merge_h1 >= 0 && merge_h1 <= 2, "qd_dem_window: merge_h1 must be 0, 1 or 2");
+  qd::WindowHost h;
+  if (!qd::build_window(d->h, W, F, k, false, h, merge_h1)) return QD_EINVAL;
+  const int v[7] = {h.r0, h.n_blocks, h.n_rows, h.n_cols, h.n_edges, h.n_commit, h.last};
+  std::copy(v, v + 7, info);
+  if (gcols) {
+    std::copy(h.gcols.begin(), h.gcols.end(), gcols);
+    std::copy(h.col_ptr.begin(), h.col_ptr.end(), col_ptr);
+    std::copy(h.col_rows.begin(), h.col_rows.end(), col_rows);
+    std::copy(h.llr.begin(), h.llr.end(), llr);
+  }
+  return QD_OK;
+}
+
 qd_status qd_dem_destroy(qd_dem* d) {
   if (!d) return QD_OK;
   if (d->d_thr) {

@@ -61,6 +61,7 @@ _SIGS = {
     "qd_build_dem_code_capacity": (_I, [C.POINTER(BBCode), C.c_double, C.c_double, C.POINTER(_VP)]),
     "qd_dem_info": (_I, [_VP, C.POINTER(DemInfo)]),
     "qd_dem_columns": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    "qd_dem_window": (_I, [_VP, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, _VP, _VP]),
     "qd_dem_destroy": (_I, [_VP]),
     "qd_sample_shots": (_I, [_VP, _U64, _U64, _I64, _VP, _VP, _VP]),
     "qd_decoder_create": (_I, [_VP, C.POINTER(GdgParams), _I64, C.POINTER(_VP)]),
@@ -194,6 +195,20 @@ class Dem:
         ll = np.zeros(self.n_cols, np.float32)
         _check(lib().qd_dem_columns(self.h, _ptr(cp), _ptr(cd), _ptr(ob), _ptr(pr), _ptr(ll)))
         return dict(col_ptr=cp, col_dets=cd[:self.info.n_edges], obs=ob, prob=pr, llr=ll)
+
+    def window(self, W, F, k, merge_h1=0):
+        """Window k as the decoder builds it (host only): dict of r0, n_blocks,
+        n_rows, n_cols, n_edges, n_commit, last, gcols, col_ptr, col_rows, llr."""
+        info = np.zeros(7, np.int32)
+        _check(lib().qd_dem_window(self.h, W, F, k, merge_h1, _ptr(info), None, None, None, None))
+        r0, nb, nr, nc, ne, ncom, last = (int(x) for x in info)
+        g = np.zeros(nc, np.int32)
+        cp = np.zeros(nc + 1, np.int32)
+        cr = np.zeros(max(ne, 1), np.int32)
+        ll = np.zeros(nc, np.float32)
+        _check(lib().qd_dem_window(self.h, W, F, k, merge_h1, _ptr(info), _ptr(g), _ptr(cp), _ptr(cr), _ptr(ll)))
+        return dict(r0=r0, n_blocks=nb, n_rows=nr, n_cols=nc, n_edges=ne, n_commit=ncom, last=bool(last),
+                    gcols=g, col_ptr=cp, col_rows=cr[:ne], llr=ll)
 
     def sample(self, seed, shot_offset, n_shots, det=None, obs=None, stream=None):
         import torch

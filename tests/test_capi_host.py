@@ -117,3 +117,22 @@ def test_parameter_validation_without_a_gpu(lib):
     h = ctypes.c_void_p()
     assert lib.qd_batch_create((ctypes.c_void_p * 1)(), 0, ctypes.byref(h)) == qdec.QD_EINVAL
     assert lib.qd_ranker_eval(None, None, None, 0, 0, 1.0, 1.0, None, None, None, None) == qdec.QD_EINVAL
+
+
+@pytest.mark.parametrize("key,R,W,F,merge", [("144", 12, 3, 1, 0), ("144", 12, 3, 1, 1), ("144", 12, 3, 1, 2),
+                                              ("72", 6, 5, 2, 1), ("72", 6, 3, 1, 2), ("288", 3, 3, 1, 1)])
+def test_windows_equal_the_oracle(lib, key, R, W, F, merge):
+    """The decoder's windows (Eq. (8)), with and without the H_1 merge of
+    Sec. III, equal the oracle's: columns, rows, commit prefix and the priors
+    GDG uses, bit for bit."""
+    p = 0.003
+    d = qdec.Dem(CODES[key], p, R)
+    o = oracle_dem(key, p, R)
+    import numpy as np
+    for k in range(o.n_windows(W, F)):
+        g, w = d.window(W, F, k, merge), o.window(W, F, k, merge)
+        for f in ("r0", "n_blocks", "n_rows", "n_cols", "n_edges", "n_commit"):
+            assert g[f] == w[f], (k, f)
+        assert (g["gcols"] == w["gcols"]).all() and (g["col_ptr"] == w["col_ptr"]).all()
+        assert (g["col_rows"] == w["col_rows"]).all()
+        assert (g["llr"].view(np.int32) == w["llr"].view(np.int32)).all(), k

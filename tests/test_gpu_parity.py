@@ -92,7 +92,7 @@ def _pipeline(key, R, p, params, n, seed, trace_windows=(), mode=0, weights=None
     n_gdg = 0
     for k in range(dec.n_windows):
         win = dec.window_info(k)
-        owin = o.window(params["W"], params["F"], k)
+        owin = o.window(params["W"], params["F"], k, params.get("merge_h1", 0))
         assert (win["gcols"] == owin["gcols"]).all()
         assert win["n_commit"] == owin["n_commit"]
         tr = None
@@ -441,3 +441,13 @@ def test_shared_prefixes_change_nothing(pname, p, n, mode):
     assert list(ca[:5]) == list(cb[:5]) and ca[4] == 0
     assert cb[5] == cb[1]  # from the root: executed = counted
     assert ca[5] < ca[1], "no decision path resumed from a shared prefix"
+
+
+@pytest.mark.parametrize("merge,pname,mode,n", [(1, "configured", 1, 80), (2, "configured", 1, 80),
+                                                (1, "paper", 2, 16), (2, "paper", 1, 60)])
+def test_h1_merge_bit_exact(merge, pname, mode, n):
+    """The H_1 merge of Sec. III (1: equal restrictions, 2: identity with the
+    XOR priors): the GPU host builds the same merged windows as the oracle
+    (columns, priors) and decodes them identically."""
+    params = preset(pname, k_guess=4, p=0.003, merge_h1=merge)
+    _pipeline("144", 12, 0.003, params, n=n, seed=144_900 + 10 * merge + mode, trace_windows=(1, 4), mode=mode)
