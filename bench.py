@@ -510,13 +510,15 @@ def ranker_288(args, torch, qdec, CODES, preset, latency_fn):
     return out
 
 
-def readings(args, torch, qdec, CODES, preset):
+def readings(args, torch, qdec, CODES, preset, latency_fn=None):
     """The configured preset (alpha = 0.625, 100 initial BP iterations, steps
     of 10) on the headline workload under single changes: the second reading
     of "100 initial BP iterations" (no pre-BP and no shortening; GDG's first
     step runs 100 iterations on the whole window), alpha = 1.0 (the paper's)
     with the preset otherwise unchanged, and the two readings of the H_1
-    merge of Sec. III; the paper preset with and without the H_1 merges."""
+    merge of Sec. III; the paper preset with and without the H_1 merges;
+    message reuse between windows (Sec. VI) with both presets, with
+    per-window latency against reuse off."""
     dem = qdec.Dem(CODES[CODE_KEY], P_PHYS, ROUNDS)
     out = {}
     for name, pname, over, n in (
@@ -526,7 +528,9 @@ def readings(args, torch, qdec, CODES, preset):
             ("h1_merge_identity", "configured", dict(merge_h1=2), args.shots),
             ("paper_preset", "paper", {}, args.shots),
             ("paper_h1_merge_equal_restrictions", "paper", dict(merge_h1=1), args.shots),
-            ("paper_h1_merge_identity", "paper", dict(merge_h1=2), args.shots)):
+            ("paper_h1_merge_identity", "paper", dict(merge_h1=2), args.shots),
+            ("message_reuse", "configured", dict(reuse_msgs=1), args.shots),
+            ("paper_message_reuse", "paper", dict(reuse_msgs=1), args.shots)):
         params = preset(pname, k_guess=K_GUESS, p=P_PHYS, **over)
         B = min(n, args.shots)
         dec = qdec.Decoder(dem, params, max_shots=B)
@@ -534,6 +538,13 @@ def readings(args, torch, qdec, CODES, preset):
         out[name] = {"preset": pname, "change": over, "shots": n, "windows_per_s": n * dec.n_windows / t,
                      "gdg_windows_frac": gdg / (n * dec.n_windows), "ler_per_round": ler_entry(f, n),
                      "failures_eq11_only": f11}
+        if over.get("reuse_msgs") and latency_fn is not None:
+            # per-window latency with and without reuse, on the same shots
+            src, _ = dem.sample(args.seed + 5, 0, max(1, args.latency_shots // 4))
+            ld = qdec.Decoder(dem, params, max_shots=1)
+            out[name]["latency_ms"] = latency_fn(ld, src)
+            ld0 = qdec.Decoder(dem, dict(params, reuse_msgs=0), max_shots=1)
+            out[name]["latency_ms_without_reuse"] = latency_fn(ld0, src)
     return out
 
 
@@ -825,7 +836,7 @@ def main():
         if args.paper_shots > 0:
             paper = paper_tree(args, torch, qdec, CODES, preset, latency)
         r288 = ranker_288(args, torch, qdec, CODES, preset, latency) if args.r288_shots > 0 else None
-        rdg = readings(args, torch, qdec, CODES, preset) if args.reading_shots > 0 else None
+        rdg = readings(args, torch, qdec, CODES, preset, latency) if args.reading_shots > 0 else None
         shapes = window_shapes(args, torch, qdec, CODES, preset) if args.shape_shots > 0 else None
 
         # the metric's own numbers first: plain vs learned GDG on the headline

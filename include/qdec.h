@@ -99,6 +99,15 @@ typedef struct {
                          /* by one column per last-block detector with the XOR    */
                          /* of the H_1 columns holding it.  Not in the last       */
                          /* window, and only with W > F (never committed).        */
+  int reuse_msgs;        /* Sec. VI (future work there): 1 = the next window's    */
+                         /* pre-BP starts the first VN->CN messages of every      */
+                         /* column it shares with this window from what this      */
+                         /* window's output path ends with (final posterior;      */
+                         /* +-clip for a column decimated to 0 / 1; the pre-BP's  */
+                         /* posterior when the pre-BP converged); other columns   */
+                         /* start from their prior.  Windows must be decoded in   */
+                         /* order, each call on the same shots; window 0 starts   */
+                         /* from the priors.  Not in batched steps.               */
 } qd_gdg_params;
 
 typedef struct qd_dem qd_dem;

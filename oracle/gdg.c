@@ -645,7 +645,8 @@ int qdo_bp_run(int n_rows, int n_cols, const int* col_ptr, const int* col_rows, 
 
 /* GDG over all decision paths of graph g; returns the winning id or -1. */
 static int gdg_all(const graph_t* g, const uint8_t* synd, const qdo_params* P, uint8_t* e_out,
-                   qdo_branch_summary* br_out, qdo_step_record* steps_out, int8_t* status_out) {
+                   qdo_branch_summary* br_out, qdo_step_record* steps_out, int8_t* status_out,
+                   float* keep_out) {
   int nb = qdo_n_paths(P);
   int dmx = qdo_path_dmax_all(P);
   state_t s;
@@ -654,6 +655,10 @@ static int gdg_all(const graph_t* g, const uint8_t* synd, const qdo_params* P, u
   double best_pm = INFINITY;
   uint8_t* e0 = malloc(g->nc > 0 ? g->nc : 1);
   uint8_t* eb = malloc(g->nc > 0 ? g->nc : 1);
+  /* what the output path leaves for the next window (message reuse): its
+   * final posterior, or +-clip for a column it decimated to 0 / 1 */
+  float* k0 = malloc(sizeof(float) * (g->nc > 0 ? g->nc : 1));
+  float* kb = malloc(sizeof(float) * (g->nc > 0 ? g->nc : 1));
   for (int id = 0; id < nb; ++id) {
     qdo_branch_summary sm;
     qdo_step_record* rec = steps_out ? steps_out + (size_t)id * dmx : NULL;
@@ -663,19 +668,28 @@ static int gdg_all(const graph_t* g, const uint8_t* synd, const qdo_params* P, u
     if (br_out) br_out[id] = sm;
     if (status_out) memcpy(status_out + (size_t)id * g->nc, s.status, g->nc);
     if (id == 0)
-      for (int i = 0; i < g->nc; ++i) e0[i] = (uint8_t)hard(&s, i);
+      for (int i = 0; i < g->nc; ++i) {
+        e0[i] = (uint8_t)hard(&s, i);
+        k0[i] = s.status[i] == -1 ? s.post[i] : (s.status[i] ? -P->clip : P->clip);
+      }
     /* Alg. 2: the estimate with the smallest path metric; ties keep the
      * lowest id */
     if (sm.status == BR_CONVERGED && sm.pm < best_pm) {
       best_pm = sm.pm;
       best = id;
-      for (int i = 0; i < g->nc; ++i) eb[i] = (uint8_t)hard(&s, i);
+      for (int i = 0; i < g->nc; ++i) {
+        eb[i] = (uint8_t)hard(&s, i);
+        kb[i] = s.status[i] == -1 ? s.post[i] : (s.status[i] ? -P->clip : P->clip);
+      }
     }
   }
   /* READING: if no path converges, the window outputs path 0's estimate */
   memcpy(e_out, best >= 0 ? eb : e0, g->nc);
+  if (keep_out) memcpy(keep_out, best >= 0 ? kb : k0, sizeof(float) * g->nc);
   free(e0);
   free(eb);
+  free(k0);
+  free(kb);
   state_free(&s);
   return best;
 }
@@ -685,7 +699,7 @@ int qdo_gdg_graph(const qdo_params* P, int n_rows, int n_cols, const int* col_pt
                   qdo_branch_summary* br) {
   graph_t g;
   graph_init(&g, n_rows, n_cols, col_ptr, col_rows, llr);
-  int best = gdg_all(&g, synd, P, corr, br, NULL, NULL);
+  int best = gdg_all(&g, synd, P, corr, br, NULL, NULL, NULL);
   graph_free(&g);
   return best;
 }
@@ -893,9 +907,23 @@ static int cmp_rank(const void* a, const void* b) {
  *   3. GDG on the kept columns (messages restart from the priors), winner by
  *      Eq. (5); dropped columns are decided 0.
  */
+/*
+ * READING of the message reuse between windows (Sec. VI leaves it to future
+ * work, naming the branch with the minimum path metric as the source): the
+ * next window's pre-BP starts its first VN->CN messages of every column it
+ * shares with this window from what this window's output path ends with --
+ * the column's final posterior, or +-clip for a column that path decimated
+ * to 0 / 1; the pre-BP's own posterior when the pre-BP converged.  Columns
+ * the output path did not hold (dropped by the shortening) and the next
+ * window's new columns start from their prior.  keep[c] per window column
+ * (NaN: nothing kept); init[c] the values kept for this window's columns
+ * (NaN: the prior).
+ */
 static int decode_window_impl(const window_t* wd, const qdo_params* P, const uint8_t* synd,
                               uint8_t* corr, int* info, int* short_cols, qdo_branch_summary* br,
-                              qdo_step_record* steps, int8_t* fstat) {
+                              qdo_step_record* steps, int8_t* fstat, const float* init, float* keep) {
+  if (keep)
+    for (int c = 0; c < wd->nc; ++c) keep[c] = NAN;
   if (wd->nc == 0) {
     /* READING: a window without columns decides nothing; the commit's
      * residue test sees its syndrome */
@@ -911,6 +939,9 @@ static int decode_window_impl(const window_t* wd, const qdo_params* P, const uin
   state_t s;
   state_alloc(&s, &g);
   state_reset(&s, &g, synd);
+  if (init)
+    for (int e = 0; e < g.ne; ++e)
+      if (!isnan(init[g.edge_col[e]])) s.v2c[e] = init[g.edge_col[e]];
   int conv = 0, it = 0;
   for (it = 0; it < P->n_pre;) {
     bp_iteration(&g, &s, P->alpha, P->clip, it + 1);
@@ -921,6 +952,8 @@ static int decode_window_impl(const window_t* wd, const qdo_params* P, const uin
   if (info) { info[0] = conv; info[1] = -1; info[2] = 0; info[3] = it; }
   if (conv) {
     for (int i = 0; i < wd->nc; ++i) corr[i] = (uint8_t)hard(&s, i);
+    if (keep)
+      for (int i = 0; i < wd->nc; ++i) keep[i] = s.post[i];
     state_free(&s);
     graph_free(&g);
     return 0;
@@ -962,9 +995,13 @@ static int decode_window_impl(const window_t* wd, const qdo_params* P, const uin
   gs.efull = ef;
   gs.wcol = sel;
   uint8_t* es = malloc(ns + 1);
-  int best = gdg_all(&gs, synd, P, es, br, steps, fstat);
+  float* ks = keep ? malloc(sizeof(float) * (ns + 1)) : NULL;
+  int best = gdg_all(&gs, synd, P, es, br, steps, fstat, ks);
   memset(corr, 0, wd->nc);
   for (int k = 0; k < ns; ++k) corr[sel[k]] = es[k];
+  if (keep)
+    for (int k = 0; k < ns; ++k) keep[sel[k]] = ks[k];
+  free(ks);
   if (info) { info[1] = best; info[2] = ns; }
   if (short_cols) memcpy(short_cols, sel, sizeof(int) * ns);
   free(es);
@@ -978,12 +1015,21 @@ static int decode_window_impl(const window_t* wd, const qdo_params* P, const uin
   return 0;
 }
 
+int qdo_decode_window_ex(const qdo_dem* d, const qdo_params* P, int k, const uint8_t* synd, uint8_t* corr,
+                         int* info, const float* init, float* keep) {
+  window_t wd;
+  window_build(d, P->W, P->F, k, P->merge_h1, &wd);
+  int rc = decode_window_impl(&wd, P, synd, corr, info, NULL, NULL, NULL, NULL, init, keep);
+  window_free(&wd);
+  return rc;
+}
+
 int qdo_decode_window(const qdo_dem* d, const qdo_params* P, int k, const uint8_t* synd,
                       uint8_t* corr, int* info, int* short_cols, qdo_branch_summary* br,
                       qdo_step_record* steps, int8_t* final_status) {
   window_t wd;
   window_build(d, P->W, P->F, k, P->merge_h1, &wd);
-  int rc = decode_window_impl(&wd, P, synd, corr, info, short_cols, br, steps, final_status);
+  int rc = decode_window_impl(&wd, P, synd, corr, info, short_cols, br, steps, final_status, NULL, NULL);
   window_free(&wd);
   return rc;
 }
@@ -1015,6 +1061,11 @@ int qdo_run_shots(const qdo_dem* d, const qdo_params* P, const uint32_t* det_bit
   uint32_t* det = malloc(sizeof(uint32_t) * dw);
   uint8_t* synd = malloc(maxr + 1);
   uint8_t* corr = malloc(maxc + 1);
+  /* message reuse: what window k - 1 kept per column, and the window k
+   * column of every DEM column (-1: none) */
+  float* kept = malloc(sizeof(float) * (maxc + 1));
+  float* init = malloc(sizeof(float) * (maxc + 1));
+  int* at = malloc(sizeof(int) * (qdo__ncols(d) + 1));
   for (int64_t sh = 0; sh < n_shots; ++sh) {
     memcpy(det, det_bits + sh * dw, sizeof(uint32_t) * dw);
     uint32_t pred = 0;
@@ -1023,7 +1074,14 @@ int qdo_run_shots(const qdo_dem* d, const qdo_params* P, const uint32_t* det_bit
       window_t* wd = &wins[k];
       int row0 = wd->r0 * w;
       for (int j = 0; j < wd->nr; ++j) synd[j] = (det[(row0 + j) >> 5] >> ((row0 + j) & 31)) & 1;
-      decode_window_impl(wd, P, synd, corr, NULL, NULL, NULL, NULL, NULL);
+      const int reuse = P->reuse_msgs && k > 0;
+      if (reuse) {  /* a column reuses what window k - 1 kept for the same DEM column */
+        for (int c = 0; c < qdo__ncols(d); ++c) at[c] = -1;
+        for (int c = 0; c < wins[k - 1].nc; ++c) at[wins[k - 1].gcols[c]] = c;
+        for (int c = 0; c < wd->nc; ++c) init[c] = at[wd->gcols[c]] >= 0 ? kept[at[wd->gcols[c]]] : NAN;
+      }
+      decode_window_impl(wd, P, synd, corr, NULL, NULL, NULL, NULL, NULL, reuse ? init : NULL,
+                         P->reuse_msgs ? kept : NULL);
       if (win_corr_words) {
         uint32_t* o = win_corr_words + ((size_t)sh * nwin + k) * corr_words_per_window;
         memset(o, 0, sizeof(uint32_t) * corr_words_per_window);
@@ -1047,6 +1105,9 @@ int qdo_run_shots(const qdo_dem* d, const qdo_params* P, const uint32_t* det_bit
   free(det);
   free(synd);
   free(corr);
+  free(kept);
+  free(init);
+  free(at);
   for (int k = 0; k < nwin; ++k) window_free(&wins[k]);
   free(wins);
   return 0;

@@ -42,6 +42,7 @@ class QdoParams(C.Structure):
                 ("pb_d1", C.c_float), ("pc", C.c_float), ("pd", C.c_float),
                 ("pc_max_depth", C.c_int), ("n_unsat_min", C.c_int), ("side_max", C.c_int),
                 ("reinit_on_split", C.c_int), ("iters_first", C.c_int), ("merge_h1", C.c_int),
+                ("reuse_msgs", C.c_int),
                 ("wts", C.POINTER(C.c_void_p)), ("wT", C.c_int), ("ranker", C.c_void_p),
                 ("dump", C.c_void_p), ("dump_n", C.c_void_p), ("dump_cap", C.c_int)]
 
@@ -96,6 +97,7 @@ def lib():
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.qdo_run_shots.argtypes = [C.c_void_p, P(QdoParams), C.c_void_p, C.c_void_p,
                                     C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
+        L.qdo_decode_window_ex.argtypes = [C.c_void_p, P(QdoParams), C.c_int] + [C.c_void_p] * 5
         L.qdo_window_build.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int] + [C.c_void_p] * 6
         declare_select(L)
         _lib = L
@@ -383,6 +385,20 @@ class OracleDEM:
             tr = None
         return corr, dict(n_dump=int(dn[0]), prebp_converged=bool(info[0]), winner=int(info[1]),
                           n_short=int(info[2]), prebp_iters=int(info[3])), tr
+
+    def decode_window_reuse(self, params, k, synd, init=None):
+        """One window with message reuse: returns (corrections, info dict, kept
+        values [n_cols]); init [n_cols] or None (NaN entries: the prior)."""
+        win = self.window(params["W"], params["F"], k, params.get("merge_h1", 0))
+        synd = np.ascontiguousarray(synd, np.uint8)
+        corr = np.zeros(win["n_cols"], np.uint8)
+        info = np.zeros(4, np.int32)
+        keep = np.zeros(win["n_cols"], np.float32)
+        ini = None if init is None else np.ascontiguousarray(init, np.float32)
+        P = make_params(params)
+        lib().qdo_decode_window_ex(self.h, C.byref(P), k, _ptr(synd), _ptr(corr), _ptr(info), _ptr(ini), _ptr(keep))
+        return corr, dict(prebp_converged=bool(info[0]), winner=int(info[1]), n_short=int(info[2]),
+                          prebp_iters=int(info[3])), keep
 
     def run_shots(self, params, det, obs, threads=1, want_corr=False, weights=None, ranker=None):
         """Sliding-window decode of every shot.  Returns (fail, obs_pred, corr_words)."""

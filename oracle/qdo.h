@@ -51,6 +51,8 @@ typedef struct {
   int iters_first;       /* BP iterations of step D = 1 (0: iters_per_step)    */
   int merge_h1;          /* Sec. III H_1 merge: 0 off, 1 equal restrictions,   */
                          /* 2 identity with XOR priors (see gdg.c)             */
+  int reuse_msgs;        /* Sec. VI: the next window's pre-BP starts from what */
+                         /* this window's output path ends with (see gdg.c)    */
   /* Learned weighted min-sum (no counterpart in the paper; alpha of Eq. (1)
    * replaced by w[t][e]): wts[k] is window k's array [wT][n_edges] over the
    * full-window edges (CSC order), or NULL for plain alpha.  Iteration t
@@ -156,6 +158,12 @@ int qdo_decode_window(const qdo_dem* d, const qdo_params* P, int k, const uint8_
                       int* short_cols /* 2w' or NULL */, qdo_branch_summary* br /* 2^k or NULL */,
                       qdo_step_record* steps /* 2^k * max(Dmax) or NULL */,
                       int8_t* final_status /* 2^k * n_short or NULL */);
+/* qdo_decode_window with message reuse (Sec. VI reading, see gdg.c): init
+ * [n_cols] the first VN->CN message of each window column's edges (NaN: its
+ * prior; NULL: all priors), keep [n_cols] (may be NULL) receives what the
+ * window's output path leaves the next window (NaN: nothing). */
+int qdo_decode_window_ex(const qdo_dem* d, const qdo_params* P, int k, const uint8_t* synd, uint8_t* corr,
+                         int* info, const float* init, float* keep);
 /* Decode with an explicit graph (column order = index order), no shortening
  * table; for tests on tiny graphs. */
 int qdo_gdg_graph(const qdo_params* P, int n_rows, int n_cols, const int* col_ptr,

@@ -640,6 +640,7 @@ struct PathOut {
   long long* visits;  // accumulates active edge visits, the path's shared prefix included
   long long* exec;    // accumulates the active edge visits this launch executed (nullable)
   long long shot;
+  float* keep;        // message reuse: this path's final values by label (nullable)
 };
 
 // Shot mode's shared path prefixes.  Paths that made the same decisions at
@@ -1051,6 +1052,14 @@ done:
     if (s8 == 1 || (s8 == -1 && B.post[k] <= 0.0f)) atomicOr(&out.ebits[kr >> 5], 1u << (kr & 31));
     if (out.fstat) out.fstat[kr] = (int8_t)s8;
   }
+  // message reuse: what this path would leave the next window if it is the
+  // window's output path (converged, or path 0): the final posterior of each
+  // active column, +-clip for a decimated one
+  if (out.keep && (status == BR_CONVERGED || id == 0))
+    for (int k = R; k < ns; k += S) {
+      const int s8 = B.status[k];
+      out.keep[k] = s8 == -1 ? B.post[k] : (s8 ? -P.clip : P.clip);
+    }
   visits = g.sum_ll(visits);
   if (R == 0) {
     *out.status = status;
@@ -1109,6 +1118,16 @@ struct DecodeArgs {
   // whole run, resumed prefixes included)
   long long* exec;
   ForkDev F;  // shot mode: snapshots of shared path prefixes
+  // message reuse between windows (nullptr: off): keep[shot * keep_ld + c]
+  // what the output path of this window ends with for window column c (NaN:
+  // nothing), read by the next window through prev[c] (this window's column
+  // -> the previous window's, -1: none; nullptr for the first window);
+  // kpath[(slot * nb + path) * ns_max + label] each candidate path's values
+  // (slot: the CTA in shot mode, the shot in path mode)
+  float* keep;
+  int keep_ld;
+  const int16_t* prev;
+  float* kpath;
 };
 
 // UG (a template parameter, so that shared-memory kernels keep shared-memory
@@ -1403,7 +1422,7 @@ __device__ int prebp_cluster(const DecodeArgs& A, const WinDev& W, const WinDev&
           pv[u] = 0.0f;
           sg[u] = 0u;
           if (q + u < end) {
-            pv[u] = (t == 1) ? Wg.llr[i] : post[i];
+            pv[u] = post[i];  // t = 1: the first VN->CN message (the prior, or the value kept for the column)
             sg[u] = sign[e];
           }
         }
@@ -1580,6 +1599,23 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
     for (int x = 0; x < L.rw; ++x) ok &= (pb[x] == sbits[x]);
     conv = ok;
   }
+  if (P.n_pre > 0) {
+    // the first VN->CN messages of the pre-BP: the prior, or (message reuse)
+    // what the previous window's output path kept for the same DEM column
+    const float* kept = (A.keep && A.prev) ? A.keep + (size_t)shot * A.keep_ld : nullptr;
+    for (int i = tid; i < nc; i += NT) {
+      float v = Wg.llr[i];
+      if (kept) {
+        const int pc = A.prev[i];
+        if (pc >= 0) {
+          const float x = kept[pc];
+          if (x == x) v = x;
+        }
+      }
+      post[i] = v;
+    }
+    __syncthreads();
+  }
   int t_conv = 0;
   if (WIDE && !UG && P.n_pre > 0 && cl_size() > 1 && nr >= 2 * (int)cl_size() && nc >= 2 * (int)cl_size()) {
     t = prebp_cluster<LW>(A, W, Wg, sm, U, sbits, conv, t_conv);
@@ -1604,7 +1640,7 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int i = (int)(ent[u] >> 16), e = (int)(ent[u] & 0xFFFFu);
-          pv[u] = (t == 1) ? Wg.llr[i] : post[i];
+          pv[u] = post[i];  // t = 1: the first VN->CN message (the prior, or the value kept for the column)
           sg[u] = sign[e];
         }
 #pragma unroll
@@ -1849,6 +1885,25 @@ __device__ void write_outputs(const DecodeArgs& A, char* sm, long long shot, boo
   }
 }
 
+// Message reuse: the values this window leaves the next one, per window
+// column (all threads of the CTA).  kp = the output path's values by label;
+// kp = nullptr: the pre-BP converged, and its posterior `post` (still in the
+// union region's pre-BP scratch) is kept for every column.
+__device__ void keep_for_next(const DecodeArgs& A, char* sm, long long shot, const float* kp, int n_short,
+                              const float* post = nullptr) {
+  const int tid = threadIdx.x, NT = blockDim.x, nc = A.W.n_cols;
+  float* out = A.keep + (size_t)shot * A.keep_ld;
+  if (!kp) {
+    for (int c = tid; c < nc; c += NT) out[c] = post[c];
+    return;
+  }
+  const uint16_t* sel = (const uint16_t*)(sm + A.L.sel);
+  const uint16_t* vperm = (const uint16_t*)(sm + A.L.s_vperm);
+  for (int c = tid; c < nc; c += NT) out[c] = CUDART_NAN_F;
+  __syncthreads();
+  for (int k = tid; k < n_short; k += NT) out[sel[vperm[k]]] = __ldcg(kp + k);
+}
+
 // ---- shot mode: persistent CTAs of up to 8 warps, one warp per decision path ----
 // One shot of one window by the whole CTA (every thread calls).  misc[2], the
 // decision-path queue, must be 0 on entry.
@@ -1945,6 +2000,7 @@ __device__ void shot_body(const DecodeArgs& A, long long shot, char* sm, Stager&
         o.status = &res_status[id];
         o.pm = &res_pm[id];
         o.ebits = res_e + (size_t)id * L.sw;
+        if (A.keep) o.keep = A.kpath + ((size_t)blockIdx.x * nb + id) * A.ns_max;
         F.chain = (fork && F.n_nodes > 0) ? A.F.chain + (size_t)id * A.dmx : nullptr;
         F.src = nullptr;
         if ((w0 & 3u) == PS_PARKED) {  // its own parking snapshot
@@ -1985,7 +2041,13 @@ __device__ void shot_body(const DecodeArgs& A, long long shot, char* sm, Stager&
     const uint32_t* eb = res_e + (size_t)(winner >= 0 ? winner : 0) * L.sw;
     for (int k = tid; k < n_short; k += blockDim.x)
       if ((eb[k >> 5] >> (k & 31)) & 1u) atomicOr(&cbits[sel[k] >> 5], 1u << (sel[k] & 31));
+    if (A.keep) {
+      const float* kp = A.kpath + ((size_t)blockIdx.x * A.P.nb + (winner >= 0 ? winner : 0)) * A.ns_max;
+      keep_for_next(A, sm, shot, kp, n_short);
+    }
     __syncthreads();
+  } else if (A.keep) {
+    keep_for_next(A, sm, shot, nullptr, 0, (const float*)(union_base<UG>(A, sm) + L.p_post));
   }
   write_outputs(A, sm, shot, conv, winner, n_short, t_run, tr);
 }
@@ -2072,7 +2134,10 @@ __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
   const bool conv = window_prefix<LW, true, false>(A, W, sm, shot, &t_run, stg);
   if (id >= nb) return;  // a CTA that only shared the pre-BP of its cluster
   if (conv) {
-    if (id == 0) write_outputs(A, sm, shot, true, -1, 0, t_run, tr);
+    if (id == 0) {
+      write_outputs(A, sm, shot, true, -1, 0, t_run, tr);
+      if (A.keep) keep_for_next(A, sm, shot, nullptr, 0, (const float*)(union_base<false>(A, sm) + L.p_post));
+    }
     return;
   }
   const int n_short = A.W.n_short;
@@ -2085,6 +2150,7 @@ __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
   o.status = (int*)mine;
   o.pm = (double*)(mine + 8);
   o.ebits = (uint32_t*)(mine + 16);
+  if (A.keep) o.keep = A.kpath + ((size_t)shot * nb + id) * A.ns_max;
   run_path<LW>(A.P, G, B, id, g, o, A.dmx, ForkCtx{});
   // publish, then count arrivals; the last CTA of the shot reduces
   __threadfence();
@@ -2115,6 +2181,7 @@ __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
   const uint16_t* sel = (const uint16_t*)(sm + L.sel);
   for (int k = tid; k < n_short; k += blockDim.x)
     if ((__ldcg(&eb[k >> 5]) >> (k & 31)) & 1u) atomicOr(&cbits[sel[k] >> 5], 1u << (sel[k] & 31));
+  if (A.keep) keep_for_next(A, sm, shot, A.kpath + ((size_t)shot * nb + (winner >= 0 ? winner : 0)) * A.ns_max, n_short);
   __syncthreads();
   write_outputs(A, sm, shot, false, winner, n_short, t_run, tr);
 }
@@ -2337,12 +2404,15 @@ cudaError_t launch_decode(int mode, int grid, int threads, size_t smem, cudaStre
                           const WinDev& W, const Layout& L, const uint32_t* det, int det_words, long long n,
                           uint32_t* corr, int corr_words, int32_t* status, char* trace, size_t tr_bytes, int dmx,
                           int ns_max, int* work, long long* counters, char* path_res, int* arrive, int sw_max,
-                          char* uglob, size_t ubytes, int cps, int cluster, const ForkDev* fork) {
+                          char* uglob, size_t ubytes, int cps, int cluster, const ForkDev* fork,
+                          const ReuseDev* reuse) {
   // counters[5]: the GDG edge visits the launch executed (counters[1] adds
   // the resumed prefixes every path counts as its own)
   const dev::DecodeArgs A{P,     W,        L,     det,      det_words, n,     corr,     corr_words, status,
                           trace, tr_bytes, dmx,   ns_max,   work,      counters, path_res, arrive,     sw_max,
-                          uglob, ubytes,   cps,   counters ? counters + 5 : nullptr, fork ? *fork : ForkDev{}};
+                          uglob, ubytes,   cps,   counters ? counters + 5 : nullptr, fork ? *fork : ForkDev{},
+                          reuse ? reuse->keep : nullptr, reuse ? reuse->keep_ld : 0, reuse ? reuse->prev : nullptr,
+                          reuse ? reuse->kpath : nullptr};
   const bool lw = W.wts != nullptr;
   if (mode == 1) {  // one cluster of `cluster` CTAs shares each shot's pre-BP
     // every path needs its CTA, and a cluster never spans two shots

@@ -118,6 +118,14 @@ struct ForkDev {
   int n_nodes, pool_ctas, sched;
 };
 
+// Message reuse between windows (see DecodeArgs::keep); keep = nullptr: off.
+struct ReuseDev {
+  float* keep;
+  int keep_ld;
+  const int16_t* prev;
+  float* kpath;
+};
+
 // A window's Tanner graph for the learned weighted min-sum (training kernels).
 struct WmsGraph {
   int nr, nc, ne, rw, T, ckpt;

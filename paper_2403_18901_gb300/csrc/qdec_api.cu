@@ -86,6 +86,9 @@ struct WinGpu {
   int16_t* d_fork = nullptr;
   int fork_nodes = 0;
   bool fork_on = false;
+  // message reuse: this window's column -> the previous window's column of
+  // the same DEM column (-1: none); nullptr for the first window
+  int16_t* d_prev = nullptr;
 };
 
 template <class T>
@@ -133,6 +136,13 @@ struct qd_decoder {
   int snap_ctas = 0;
   bool fork_on = true;
   bool sched_on = true;  // preemption at step boundaries (with fork_on)
+  // message reuse between windows (qd_gdg_params.reuse_msgs): per shot the
+  // values a window keeps for the next [max_shots][keep_ld], and every
+  // candidate path's values [slots][nb][ns_max]
+  float* d_keep = nullptr;
+  int keep_ld = 0;
+  float* d_kpath = nullptr;
+  size_t kpath_slots = 0;
   uint32_t *d_det = nullptr, *d_obs = nullptr, *d_pred = nullptr, *d_fail = nullptr, *d_resid = nullptr;
   long long* d_nfail = nullptr;
 };
@@ -356,6 +366,18 @@ qd_status configure_layouts(qd_decoder* dec, bool hist, const char* who) {
     dec->snap_cta_bytes = cb;
     dec->snap_ctas = nc;
   }
+  if (dec->P.reuse_msgs) {  // candidate paths' kept values: one set per resident CTA, or per path-mode shot
+    int cmax = 0;
+    for (const WinGpu& g : dec->wins) cmax = std::max(cmax, dec->sm_count * std::max(g.grid_per_sm, g.grid_g));
+    const size_t slots = std::max<size_t>(cmax, (size_t)std::min<long long>(dec->max_shots, kPathModeMaxShots));
+    if (slots > dec->kpath_slots) {
+      cudaFree(dec->d_kpath);
+      dec->d_kpath = nullptr;
+      dec->kpath_slots = 0;
+      QD_CK(cudaMalloc(&dec->d_kpath, sizeof(float) * slots * dec->kp.nb * std::max(1, dec->ns_max)));
+      dec->kpath_slots = slots;
+    }
+  }
   dec->smem_max = smem_max;
   dec->hist_on = hist;
   return QD_OK;
@@ -481,8 +503,11 @@ qd_status qd_decoder_destroy(qd_decoder* dec) {
     cudaFree(w.d_ccobs);
     cudaFree(w.d_wthr);
     cudaFree(w.d_fork);
+    cudaFree(w.d_prev);
   }
   cudaFree(dec->d_snap);
+  cudaFree(dec->d_keep);
+  cudaFree(dec->d_kpath);
   cudaFree(dec->d_work);
   cudaFree(dec->d_uscratch);
   cudaFree(dec->d_ranker);
@@ -514,6 +539,7 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
   }
   QD_REQ(p->iters_first >= 0, "qd_decoder_create: iters_first < 0");
   QD_REQ(p->merge_h1 >= 0 && p->merge_h1 <= 2, "qd_decoder_create: merge_h1 must be 0, 1 or 2");
+  QD_REQ(p->reuse_msgs == 0 || p->reuse_msgs == 1, "qd_decoder_create: reuse_msgs must be 0 or 1");
   QD_REQ(p->side_max == 0 || (p->side_max >= p->k_guess && p->side_max <= 32),
          "qd_decoder_create: side_max must be 0 or in [k_guess, 32]");
   QD_REQ(p->d_max_other >= p->k_guess, "qd_decoder_create: d_max_other < k_guess");
@@ -628,6 +654,20 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
   QD_CK(cudaMalloc(&dec->d_fail, sizeof(uint32_t) * (size_t)max_shots));
   QD_CK(cudaMalloc(&dec->d_resid, sizeof(uint32_t) * (size_t)max_shots));
   QD_CK(cudaMalloc(&dec->d_nfail, sizeof(long long)));
+  if (p->reuse_msgs) {
+    for (const WinGpu& g : dec->wins) dec->keep_ld = std::max(dec->keep_ld, g.h.n_cols);
+    QD_CK(cudaMalloc(&dec->d_keep, sizeof(float) * (size_t)max_shots * std::max(1, dec->keep_ld)));
+    for (int w = 1; w < nwin; ++w) {
+      const auto& a = dec->wins[w - 1].h;
+      const auto& b = dec->wins[w].h;
+      if (!a.n_cols || !b.n_cols) continue;  // nothing kept across a window without columns
+      std::vector<int> at(dem->h.n_cols, -1);
+      for (int c = 0; c < a.n_cols; ++c) at[a.gcols[c]] = c;  // a repeated DEM column: its last column
+      std::vector<int16_t> prev(b.n_cols);
+      for (int c = 0; c < b.n_cols; ++c) prev[c] = (int16_t)at[b.gcols[c]];
+      QD_CK(upload(&dec->wins[w].d_prev, prev));
+    }
+  }
   *out = dec.release();
   return QD_OK;
 }
@@ -669,6 +709,17 @@ qd_status qd_window_info(const qd_decoder* dec, int k, qd_window_info_t* o, int*
 }  // extern "C"
 
 namespace {
+// message reuse buffers for window g (keep = nullptr: off)
+qd::ReuseDev reuse_dev(const qd_decoder* dec, const WinGpu& g) {
+  qd::ReuseDev R{};
+  if (!dec->d_keep) return R;
+  R.keep = dec->d_keep;
+  R.keep_ld = dec->keep_ld;
+  R.prev = g.d_prev;
+  R.kpath = dec->d_kpath;
+  return R;
+}
+
 // shot mode's snapshot plan of window g (pool = nullptr: none, or turned off)
 qd::ForkDev fork_dev(const qd_decoder* dec, const WinGpu& g) {
   qd::ForkDev F{};
@@ -713,13 +764,14 @@ qd_status qd_decode_windows(qd_decoder* dec, int k, const uint32_t* det_bits, in
   if (path_mode && (n_shots > std::min<long long>(dec->max_shots, kPathModeMaxShots) || !g.path_fits || global))
     path_mode = false;
   const qd::ForkDev fk = fork_dev(dec, g);
+  const qd::ReuseDev ru = reuse_dev(dec, g);
   if (global) {
     QD_CK(cudaMemsetAsync(dec->d_work + k, 0, sizeof(int), st));
     const long long grid = std::min<long long>(n_shots, (long long)dec->sm_count * g.grid_g);
     QD_CK(qd::launch_decode(0, (int)grid, 32 * kShotWarps, g.Lg.U, st, dec->kp, g.dv, g.Lg, det_bits, dw, n_shots,
                             win_correction, dec->corr_words, status, (char*)trace, dec->trace_bytes, dec->dmx,
                             dec->ns_max, dec->d_work + k, dec->d_counters, nullptr, nullptr, dec->sw_max,
-                            dec->d_uscratch, g.Lg.total - g.Lg.U, 1, 1, &fk));
+                            dec->d_uscratch, g.Lg.total - g.Lg.U, 1, 1, &fk, &ru));
     return QD_OK;
   }
   if (path_mode) {
@@ -727,7 +779,7 @@ qd_status qd_decode_windows(qd_decoder* dec, int k, const uint32_t* det_bits, in
     QD_CK(qd::launch_decode(1, (int)(n_shots * cps), kPathThreads, g.Lp.total, st, dec->kp, g.dv, g.Lp, det_bits,
                             dw, n_shots, win_correction, dec->corr_words, status, (char*)trace, dec->trace_bytes,
                             dec->dmx, dec->ns_max, nullptr, dec->d_counters, dec->d_path_res, dec->d_arrive,
-                            dec->sw_max, nullptr, 0, cps, g.pcl));
+                            dec->sw_max, nullptr, 0, cps, g.pcl, nullptr, &ru));
     return QD_OK;
   }
   QD_CK(cudaMemsetAsync(dec->d_work + k, 0, sizeof(int), st));
@@ -735,7 +787,7 @@ qd_status qd_decode_windows(qd_decoder* dec, int k, const uint32_t* det_bits, in
   QD_CK(qd::launch_decode(0, (int)grid, 32 * g.shot_warps, g.L.total, st, dec->kp, g.dv, g.L, det_bits, dw,
                           n_shots, win_correction, dec->corr_words, status, (char*)trace, dec->trace_bytes,
                           dec->dmx, dec->ns_max, dec->d_work + k, dec->d_counters, nullptr, nullptr, dec->sw_max,
-                          nullptr, 0, 1, 1, &fk));
+                          nullptr, 0, 1, 1, &fk, &ru));
   return QD_OK;
 }
 
@@ -968,11 +1020,13 @@ extern "C" qd_status qd_decode_commit_static(qd_decoder* dec, int k, uint32_t* d
     return QD_EINVAL;
   }
   if (n_shots == 0) return QD_OK;
+  QD_REQ(!dec->d_keep || n_shots <= dec->max_shots, "qd_decode_commit_static: n_shots > max_shots with message reuse");
   void* base = nullptr;
   if (qd_status st = static_scratch_address(&base)) return st;
   int* work = (int*)base;
   uint32_t* corr = (uint32_t*)((char*)base + kStaticHeader);
   const WinGpu& g = dec->wins[k];
+  const qd::ReuseDev ru = reuse_dev(dec, g);
   cudaStream_t st = (cudaStream_t)stream;
   const int dw = (dec->dem->h.n_det + 31) / 32;
   if (g.h.n_cols > 0) {
@@ -989,7 +1043,8 @@ extern "C" qd_status qd_decode_commit_static(qd_decoder* dec, int k, uint32_t* d
       const int cps = (dec->kp.nb + g.pcl - 1) / g.pcl * g.pcl;
       QD_CK(qd::launch_decode(1, (int)(n_shots * cps), kPathThreads, g.Lp.total, st, dec->kp, g.dv, g.Lp, det_bits,
                               dw, n_shots, corr, dec->corr_words, nullptr, nullptr, 0, dec->dmx, dec->ns_max, nullptr,
-                              dec->d_counters, dec->d_path_res, dec->d_arrive, dec->sw_max, nullptr, 0, cps, g.pcl));
+                              dec->d_counters, dec->d_path_res, dec->d_arrive, dec->sw_max, nullptr, 0, cps, g.pcl,
+                              nullptr, &ru));
     } else {
       // the array keeps the previous call's contents: the work counter restarts at 0
       QD_CK(cudaMemsetAsync(work, 0, sizeof(int), st));
@@ -1000,7 +1055,7 @@ extern "C" qd_status qd_decode_commit_static(qd_decoder* dec, int k, uint32_t* d
       QD_CK(qd::launch_decode(0, (int)grid, 32 * (global ? kShotWarps : g.shot_warps), global ? L.U : L.total, st,
                               dec->kp, g.dv, L, det_bits, dw, n_shots, corr, dec->corr_words, nullptr, nullptr, 0,
                               dec->dmx, dec->ns_max, work, dec->d_counters, nullptr, nullptr, dec->sw_max,
-                              global ? dec->d_uscratch : nullptr, global ? L.total - L.U : 0, 1, 1, &fk));
+                              global ? dec->d_uscratch : nullptr, global ? L.total - L.U : 0, 1, 1, &fk, &ru));
     }
   }
   const int w = dec->dem->h.w;
@@ -1129,6 +1184,10 @@ qd_status qd_batch_create(qd_decoder* const* members, int n_members, qd_batch** 
   if (!b) return QD_ENOMEM;
   for (int i = 0; i < n_members; ++i) {
     QD_REQ(members[i], "qd_batch_create: null member");
+    if (members[i]->P.reuse_msgs) {
+      set_error("qd_batch_create: message reuse between windows is not supported in batched steps");
+      return QD_EUNSUPPORTED;
+    }
     b->mem.push_back(members[i]);
     b->n_steps = std::max(b->n_steps, (int)members[i]->wins.size());
   }

@@ -43,6 +43,7 @@ struct Layout;
 struct WmsGraph;
 struct RankRec;
 struct ForkDev;
+struct ReuseDev;
 
 // Build the merged DEM (backward sensitivity sweep over the circuit).
 bool build_dem_host(const qd_bb_code& code, const qd_noise& noise, DemHost& out);
@@ -62,7 +63,7 @@ cudaError_t launch_decode(int mode, int grid, int threads, size_t smem, cudaStre
                           uint32_t* corr, int corr_words, int32_t* status, char* trace, size_t tr_bytes, int dmx,
                           int ns_max, int* work, long long* counters, char* path_res, int* arrive, int sw_max,
                           char* uglob = nullptr, size_t ubytes = 0, int cps = 1, int cluster = 1,
-                          const ForkDev* fork = nullptr);
+                          const ForkDev* fork = nullptr, const ReuseDev* reuse = nullptr);
 // Clusters of `cluster` path-mode CTAs that can be resident at once (0: none).
 cudaError_t path_cluster_occupancy(int threads, size_t smem, int cluster, int* clusters);
 // One decoder's share of a batched window step (decode + commit).

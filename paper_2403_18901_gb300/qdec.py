@@ -40,7 +40,8 @@ class GdgParams(C.Structure):
                 ("pa_other", C.c_float), ("pb_main", C.c_float), ("pb_other", C.c_float),
                 ("pb_d1", C.c_float), ("pc", C.c_float), ("pd", C.c_float),
                 ("pc_max_depth", C.c_int), ("n_unsat_min", C.c_int), ("side_max", C.c_int),
-                ("reinit_on_split", C.c_int), ("iters_first", C.c_int), ("merge_h1", C.c_int)]
+                ("reinit_on_split", C.c_int), ("iters_first", C.c_int), ("merge_h1", C.c_int),
+                ("reuse_msgs", C.c_int)]
 
 
 class DemInfo(C.Structure):

@@ -451,3 +451,15 @@ def test_h1_merge_bit_exact(merge, pname, mode, n):
     (columns, priors) and decodes them identically."""
     params = preset(pname, k_guess=4, p=0.003, merge_h1=merge)
     _pipeline("144", 12, 0.003, params, n=n, seed=144_900 + 10 * merge + mode, trace_windows=(1, 4), mode=mode)
+
+
+@pytest.mark.parametrize("pname,mode,n", [("configured", 1, 120), ("configured", 2, 16), ("paper", 1, 120),
+                                          ("configured", 3, 60)])
+def test_message_reuse_bit_exact(pname, mode, n):
+    """Message reuse between windows (Sec. VI): each window's pre-BP starts
+    from what the previous window's output path kept; every window's
+    corrections, the committed syndromes and the outcomes equal the oracle's,
+    in the throughput shape, the path-per-CTA shape and with the path states
+    in global memory."""
+    params = preset(pname, k_guess=4, p=0.003, reuse_msgs=1)
+    _pipeline("144", 12, 0.003, params, n=n, seed=144_610 + mode, mode=mode)
