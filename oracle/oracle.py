@@ -408,7 +408,7 @@ class OracleDEM:
         fail = np.zeros(n, np.uint8)
         pred = np.zeros(n, np.uint32)
         nwin = self.n_windows(params["W"], params["F"])
-        maxc = max(self.window(params["W"], params["F"], k)["n_cols"] for k in range(nwin))
+        maxc = max(self.window(params["W"], params["F"], k, params.get("merge_h1", 0))["n_cols"] for k in range(nwin))
         cw = (maxc + 31) // 32
         corr = np.zeros((n, nwin, cw), np.uint32) if want_corr else None
         P = make_params(params, weights, ranker)
