@@ -39,7 +39,7 @@ BYTES_PER_EDGE_ITER = 16  # explicit-message shared-memory bytes per edge and it
 # the current kernel (dram__bytes_read.sum + dram__bytes_write.sum; see
 # profiles/decode_shot_kernel_bb144_w3_p3e-3_configured.md).  Reported only for
 # that workload; per launch, like "achieved".
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {("configured", 20000): 6856704 + 3092475136}
 
 
 def workload_name(preset_name):
