@@ -2094,6 +2094,8 @@ __global__ void __launch_bounds__(256, 2) decode_batch_kernel(const __grid_const
     const DecodeArgs& A = B.seg[m];
     const long long shot = g - (m ? B.seg_end[m - 1] : 0);
     if (threadIdx.x == 0) ((int*)(sm + A.L.misc))[2] = 0;
+    // no snapshot yet, every path queued
+    if (A.F.pool && threadIdx.x < 2 * kMaxForkNodes) ((int*)(sm + A.L.red))[threadIdx.x] = 0;
     __syncthreads();
     shot_body<LW, false>(A, shot, sm, stg);
   }
@@ -2351,7 +2353,7 @@ cudaError_t launch_decode_batch(cudaStream_t st, int grid, int threads, size_t s
     B.seg[i] = dev::DecodeArgs{*x.P,   *x.W,   *x.L,     x.det,      x.det_words, x.n,      x.corr,
                                x.corr_words, nullptr, nullptr, 0,     x.dmx,    x.ns_max, nullptr,
                                x.counters, nullptr, nullptr, x.sw_max, nullptr, 0, 1,
-                               x.counters ? x.counters + 5 : nullptr, ForkDev{}};
+                               x.counters ? x.counters + 5 : nullptr, x.fork ? *x.fork : ForkDev{}};
     lw = lw || x.W->wts != nullptr;
   }
   if (lw) dev::decode_batch_kernel<true><<<grid, threads, smem, st>>>(B);

@@ -1078,6 +1078,7 @@ struct qd_batch {
   };
   std::vector<Step> steps;
   int* d_work = nullptr;  // one counter per step
+  std::vector<qd::ForkDev> forks;  // per member: the current step's path-scheduling plan
 };
 
 namespace {
@@ -1152,6 +1153,9 @@ int batch_members(qd_batch* b, int j, uint32_t* const* det, const int64_t* n, ui
     const int w = d->dem->h.w;
     m.b0 = g.h.r0 * w;
     m.b1 = g.h.commit_b1 * w;
+    b->forks.resize(b->mem.size());
+    b->forks[i] = fork_dev(d, g);
+    m.fork = &b->forks[i];
     out.push_back(m);
   }
   return (int)out.size();

@@ -82,6 +82,7 @@ struct BatchMember {
   const uint32_t* cobs;
   uint32_t *obs_pred, *resid;
   int b0, b1;
+  const ForkDev* fork;  // the member's path-scheduling plan (nullptr: none)
 };
 cudaError_t batch_occupancy(int threads, size_t smem, int* blocks);
 cudaError_t launch_decode_batch(cudaStream_t st, int grid, int threads, size_t smem, unsigned q_off, int* work,
