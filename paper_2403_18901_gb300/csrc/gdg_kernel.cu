@@ -718,14 +718,12 @@ __device__ __forceinline__ bool check_pass(const KParams& P, const ShortG& G, co
       continue;
     }
     const CNState oc = B.cns[j];
-    // two independent (min1, min2, argmin) chains, the even and the odd row
-    // entries, merged below: the pair and so every message do not depend on
-    // the order in which a check sees its inputs (with equal minima the
-    // argmin is immaterial: both messages are then min1 = min2)
-    float m1 = CUDART_INF_F, m2 = CUDART_INF_F, n1 = CUDART_INF_F, n2 = CUDART_INF_F;
-    int am = 0xFFFF, an = 0xFFFF;
+    float m1 = CUDART_INF_F, m2 = CUDART_INF_F;
+    int am = 0xFFFF;
     uint32_t neg = 0, hp = 0;
-    auto take = [&](uint32_t ent, float pv, uint32_t sg, float& x1, float& x2, int& ax) {
+    // one row entry; the (min1, min2) pair and so every message do not
+    // depend on the order in which a check sees its inputs
+    auto take = [&](uint32_t ent, float pv, uint32_t sg) {
       if (pv != pv) return;  // stale message of a decimated VN
       hp ^= pv <= 0.0f;
       const int e = (int)(ent & 0xFFFFu);
@@ -734,12 +732,12 @@ __device__ __forceinline__ bool check_pass(const KParams& P, const ShortG& G, co
       const float wprev = (LW && !first) ? edge_weight(G.wts, G.wT, G.wE, P.alpha, tw, G.efull[e]) : P.alpha;
       const float v = first ? pv : clipf(__fsub_rn(pv, c2v<LW>(wprev, P.clip, oc, e, sg)), P.clip);
       const float a = fabsf(v);
-      if (a < x1) {
-        x2 = x1;
-        x1 = a;
-        ax = e;
-      } else if (a < x2) {
-        x2 = a;
+      if (a < m1) {
+        m2 = m1;
+        m1 = a;
+        am = e;
+      } else if (a < m2) {
+        m2 = a;
       }
       const uint32_t sgn = v < 0.0f;
       neg ^= sgn;
@@ -751,15 +749,8 @@ __device__ __forceinline__ bool check_pass(const KParams& P, const ShortG& G, co
       const uint32_t e0 = G.rowent[q], e1 = two ? G.rowent[q + 1] : e0;
       const float p0 = B.post[e0 >> 16], p1 = B.post[e1 >> 16];
       const uint32_t s0 = B.sign[e0 & 0xFFFFu], s1 = B.sign[e1 & 0xFFFFu];
-      take(e0, p0, s0, m1, m2, am);
-      if (two) take(e1, p1, s1, n1, n2, an);
-    }
-    if (n1 < m1) {
-      m2 = fminf(m1, n2);
-      m1 = n1;
-      am = an;
-    } else {
-      m2 = fminf(m2, n1);
+      take(e0, p0, s0);
+      if (two) take(e1, p1, s1);
     }
     if (TPC > 1) {
       group_min2(m1, m2, am, neg, TPC);
@@ -1637,10 +1628,8 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
       const int j = j0 < nr ? j0 : nr - 1;
       const int beg = Wg.row_ptr[j], end = j0 < nr ? Wg.row_ptr[j + 1] : beg;
       const CNState oc = cns[j];
-      // two independent (min1, min2, argmin) chains (even / odd entries),
-      // merged below; with equal minima the argmin is immaterial
-      float mm1[2] = {CUDART_INF_F, CUDART_INF_F}, mm2[2] = {CUDART_INF_F, CUDART_INF_F};
-      int amm[2] = {0xFFFF, 0xFFFF};
+      float m1 = CUDART_INF_F, m2 = CUDART_INF_F;
+      int am = 0xFFFF;
       uint32_t neg = 0, hp = 0;
       for (int q = beg + 4 * sub_pre; q < end; q += 4 * tpc_pre) {
         uint32_t ent[4];
@@ -1662,26 +1651,17 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
           const float wprev = (LW && t > 1) ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t - 1, e) : P.alpha;
           const float v = (t == 1) ? pv[u] : clipf(__fsub_rn(pv[u], c2v<LW>(wprev, P.clip, oc, e, sg[u])), P.clip);
           const float a = fabsf(v);
-          if (a < mm1[u & 1]) {
-            mm2[u & 1] = mm1[u & 1];
-            mm1[u & 1] = a;
-            amm[u & 1] = e;
-          } else if (a < mm2[u & 1]) {
-            mm2[u & 1] = a;
+          if (a < m1) {
+            m2 = m1;
+            m1 = a;
+            am = e;
+          } else if (a < m2) {
+            m2 = a;
           }
           const uint32_t sgn = v < 0.0f;
           neg ^= sgn;
           sign[e] = (uint8_t)sgn;
         }
-      }
-      float m1 = mm1[0], m2 = mm2[0];
-      int am = amm[0];
-      if (mm1[1] < m1) {
-        m2 = fminf(m1, mm2[1]);
-        m1 = mm1[1];
-        am = amm[1];
-      } else {
-        m2 = fminf(m2, mm1[1]);
       }
       if (tpc_pre > 1) {
         group_min2(m1, m2, am, neg, tpc_pre);
