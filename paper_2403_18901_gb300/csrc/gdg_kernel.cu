@@ -1814,7 +1814,7 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
     int o = tmp[k];
     for (int e = W.col_ptr[c]; e < W.col_ptr[c + 1]; ++e, ++o) {
       scr[o] = cinv[W.col_rows[e]];
-      sef[o] = (uint16_t)e;  // the shortened edge keeps its full-window edge's weights
+      if (LW) sef[o] = (uint16_t)e;  // the shortened edge keeps its full-window edge's weights
     }
   }
   for (int j = tid; j <= nr; j += NT) rc[j] = 0;

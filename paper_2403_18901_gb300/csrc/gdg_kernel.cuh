@@ -179,8 +179,11 @@ struct Layout {
 
 __host__ __device__ inline unsigned al16(unsigned x) { return (x + 15u) & ~15u; }
 
+// lw: the shortened edges' full-window edge ids (s_efull) are kept, which
+// only learned weights read
 __host__ __device__ inline Layout make_layout(int nr, int nc, int ne, int ns, int es, int nb,
-                                              int nslots, bool stage_graph = false, bool ranker = false) {
+                                              int nslots, bool stage_graph = false, bool ranker = false,
+                                              bool lw = true) {
   Layout L{};
   L.rw = (nr + 31) / 32;
   L.cw = (nc + 31) / 32;
@@ -199,7 +202,7 @@ __host__ __device__ inline Layout make_layout(int nr, int nc, int ne, int ns, in
   L.s_rowent = o; o = al16(o + 4u * es);
   L.s_llr = o; o = al16(o + 4u * ns);
   L.s_vdeg = o; o = al16(o + 1u * ns);
-  L.s_efull = o; o = al16(o + 2u * es);
+  L.s_efull = o; o = al16(o + (lw ? 2u * es : 0u));
   L.s_cperm = o; o = al16(o + 2u * nr);
   L.s_vperm = o; o = al16(o + 2u * ns);
   L.rowcnt = o; o = al16(o + 4u * (nr + 1));

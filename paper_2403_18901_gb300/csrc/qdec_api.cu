@@ -126,6 +126,7 @@ struct qd_decoder {
   size_t trace_bytes = 0, smem_max = 0;
   int smem_optin = 0;
   bool hist_on = false;  // layouts hold the quantised history (ranker or dump)
+  bool lw_on = false;    // layouts keep the shortened edges' full-window ids (learned weights)
   void* d_ranker = nullptr;  // grid-rounded parameters (644 floats), then the 256 B fragments
   int* d_work = nullptr;
   long long* d_counters = nullptr;  // kCounters entries (qd_decoder_counters_ex)
@@ -267,7 +268,8 @@ qd_status configure_layouts(qd_decoder* dec, bool hist, const char* who) {
     c.pcl = 1;
     const auto& h = dec->wins[w].h;
     auto lay = [&](int slots, bool stage) {
-      return qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, nb, slots, stage, hist);
+      return qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, nb, slots, stage, hist,
+                             dec->lw_on);
     };
     // the most resident decision-path warps per SM (slots per CTA x CTAs per
     // SM); ties to more slots per CTA
@@ -855,8 +857,23 @@ qd_status qd_decoder_set_weights(qd_decoder* dec, int k, const float* w, int T) 
   QD_REQ(dec, "null argument");
   QD_REQ(k >= 0 && k < (int)dec->wins.size(), "qd_decoder_set_weights: window out of range");
   QD_REQ(w == nullptr || T >= 1, "qd_decoder_set_weights: T must be >= 1");
+  const float* old_w = dec->wins[k].dv.wts;
+  const int old_t = dec->wins[k].dv.wT;
   dec->wins[k].dv.wts = w;
   dec->wins[k].dv.wT = w ? T : 0;
+  // the layouts keep the shortened edges' full-window ids only while some
+  // window has learned weights
+  bool want = false;
+  for (const WinGpu& g : dec->wins) want = want || g.dv.wts != nullptr;
+  if (want != dec->lw_on) {
+    dec->lw_on = want;
+    if (qd_status st = configure_layouts(dec, dec->hist_on, "qd_decoder_set_weights")) {
+      dec->wins[k].dv.wts = old_w;
+      dec->wins[k].dv.wT = old_t;
+      dec->lw_on = !want;
+      return st;
+    }
+  }
   return QD_OK;
 }
 
@@ -1095,7 +1112,7 @@ qd_status batch_plan(qd_batch* b, int j, int warps, size_t budget) {
     int s = warps;
     for (; s >= 1; --s) {
       S.L[i] = qd::make_layout(h.n_rows, h.n_cols, h.n_edges, h.n_short, h.short_edges_max, d->kp.nb, s, false,
-                               d->hist_on);
+                               d->hist_on, d->lw_on);
       if (qd::al16(S.L[i].total) + 32 <= budget) break;
     }
     if (s < 1) {
