@@ -177,6 +177,16 @@ qd_status qd_dem_columns(const qd_dem* dem, int* col_ptr, int* col_dets, uint32_
  * outside (2^-15, 16). */
 qd_status qd_dem_window(const qd_dem* dem, int W, int F, int k, int merge_h1, int info[7], int* gcols,
                         int* col_ptr, int* col_rows, float* llr);
+/* Shot mode's decision-path plan for parameters p and `wave` warps (host
+ * only; see qd_decoder_set_fork): info = (paths nb, deepest D_max dmx, nodes
+ * or -1 when there is no plan: nb <= wave); with order != NULL also the queue
+ * order[nb], chain[nb][dmx] (the snapshot node of path q after the BP of step
+ * D at chain[q * dmx + D - 1], -1: none), fnode[nb] / fdep[nb] (each path's
+ * planned resume node and its depth, -1 / 0: none).  Paths with equal
+ * decisions at depths 1..D-1 -- guess value (Alg. 2, Fig. 2), Alg. 3's
+ * thresholds, message restart -- share the node of depth D. */
+qd_status qd_path_plan(const qd_gdg_params* p, int wave, int info[3], int16_t* order, int16_t* chain, int16_t* fnode,
+                       int16_t* fdep);
 qd_status qd_dem_destroy(qd_dem* dem);
 
 /*

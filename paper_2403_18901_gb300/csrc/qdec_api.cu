@@ -474,6 +474,34 @@ qd_status qd_dem_window(const qd_dem* d, int W, int F, int k, int merge_h1, int 
   return QD_OK;
 }
 
+qd_status qd_path_plan(const qd_gdg_params* p, int wave, int info[3], int16_t* order, int16_t* chain, int16_t* fnode,
+                       int16_t* fdep) {
+  QD_REQ(p && info, "qd_path_plan: null argument");
+  QD_REQ(p->k_guess >= 0 && p->k_guess <= 5 && wave >= 1, "qd_path_plan: k_guess outside [0, 5] or wave < 1");
+  QD_REQ(p->side_max == 0 || (p->side_max >= p->k_guess && p->side_max <= 32), "qd_path_plan: bad side_max");
+  qd::KParams k{};
+  k.dmax_main = p->d_max_main;
+  k.dmax_other = p->d_max_other;
+  k.k = p->k_guess;
+  k.low_err = p->low_error_mode;
+  k.side_max = p->side_max;
+  k.reinit = p->reinit_on_split != 0;
+  k.nb = (1 << p->k_guess) + (p->side_max > p->k_guess ? p->side_max - p->k_guess : 0);
+  int dmx = 0;
+  for (int id = 0; id < k.nb; ++id) dmx = std::max(dmx, qd::path_dmax(k, id, qd::path_split(k, id)));
+  const ForkPlan F = fork_plan(k, dmx, wave);
+  info[0] = k.nb;
+  info[1] = dmx;
+  info[2] = F.on ? F.n_nodes : -1;
+  if (F.on && order) {
+    std::copy(F.order.begin(), F.order.end(), order);
+    std::copy(F.chain.begin(), F.chain.end(), chain);
+    std::copy(F.fnode.begin(), F.fnode.end(), fnode);
+    std::copy(F.fdep.begin(), F.fdep.end(), fdep);
+  }
+  return QD_OK;
+}
+
 qd_status qd_dem_destroy(qd_dem* d) {
   if (!d) return QD_OK;
   if (d->d_thr) {

@@ -63,6 +63,7 @@ _SIGS = {
     "qd_dem_info": (_I, [_VP, C.POINTER(DemInfo)]),
     "qd_dem_columns": (_I, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "qd_dem_window": (_I, [_VP, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, _VP, _VP]),
+    "qd_path_plan": (_I, [_VP, C.c_int, _VP, _VP, _VP, _VP, _VP]),
     "qd_dem_destroy": (_I, [_VP]),
     "qd_sample_shots": (_I, [_VP, _U64, _U64, _I64, _VP, _VP, _VP]),
     "qd_decoder_create": (_I, [_VP, C.POINTER(GdgParams), _I64, C.POINTER(_VP)]),
@@ -161,6 +162,26 @@ def make_params(p):
     for name, _ in GdgParams._fields_:
         setattr(q, name, p.get(name, 0) if name in ("side_max", "reinit_on_split") else p[name])
     return q
+
+
+def path_plan(params, wave):
+    """Shot mode's decision-path plan (host only): dict of nb, dmx, n_nodes
+    (-1: no plan) and, with a plan, order [nb], chain [nb][dmx], fnode [nb],
+    fdep [nb]."""
+    info = np.zeros(3, np.int32)
+    p = make_params(params)
+    _check(lib().qd_path_plan(C.byref(p), int(wave), _ptr(info), None, None, None, None))
+    nb, dmx, nn = (int(x) for x in info)
+    out = dict(nb=nb, dmx=dmx, n_nodes=nn)
+    if nn >= 0:
+        order = np.zeros(nb, np.int16)
+        chain = np.zeros(nb * dmx, np.int16)
+        fnode = np.zeros(nb, np.int16)
+        fdep = np.zeros(nb, np.int16)
+        _check(lib().qd_path_plan(C.byref(p), int(wave), _ptr(info), _ptr(order), _ptr(chain), _ptr(fnode),
+                                  _ptr(fdep)))
+        out.update(order=order, chain=chain.reshape(nb, dmx), fnode=fnode, fdep=fdep)
+    return out
 
 
 class Dem:
