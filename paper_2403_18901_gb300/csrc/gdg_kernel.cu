@@ -15,12 +15,18 @@
 //       with aggressive decimation (Alg. 3), guess value by the path id,
 //       peeling
 //   a8  minimum path metric Eq. (5) over converged paths, ties to the lowest id
+//   (message reuse between windows, optional) the output path's final
+//       posteriors kept per window column; the next window's pre-BP starts
+//       its first VN->CN messages from them
 //
 // Two launch shapes run the same path code:
 //   shot mode (throughput): persistent CTAs of up to 8 warps take shots from
 //     a work counter; after the CTA-wide pre-BP the warps take decision paths
-//     from a shared-memory queue, path 0 (the longest) first, one warp per
-//     path;
+//     from a shared-memory queue in a host-planned order, one warp per path;
+//     paths resume from snapshots of the prefixes they share with earlier
+//     paths, and at every step boundary a warp parks its path for a waiting
+//     one with more steps left (snapshots in a per-CTA pool in global memory;
+//     see ForkCtx);
 //   path mode (latency, small batches): one CTA per (shot, path); the path
 //     CTAs of a shot form a thread-block cluster that splits the pre-BP over
 //     distributed shared memory, each CTA then ranks, shortens and runs its
@@ -28,7 +34,8 @@
 //     and the last CTA of the shot to arrive (atomic counter, no waiting)
 //     picks the winner.
 // Every wait is a CTA, warp or cluster barrier, except the bulk-copy
-// mbarrier, whose wait is bounded.
+// mbarrier, whose wait is bounded; the path scheduler never waits (a path
+// whose snapshot is not ready starts from an earlier one or from the root).
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
