@@ -35,16 +35,29 @@ METRIC = "[[144,12,12]] W=3 windows/s"
 OPS_PER_EDGE_ITER = 10  # FP32/ALU operations of Eq. (1)-(3) per edge and iteration
 BYTES_PER_EDGE_ITER = 16  # explicit-message shared-memory bytes per edge and iteration (4 B x 2 read + 2 written)
 # DRAM bytes (read + write) of one decode_shot_kernel launch of the default
-# workload (configured preset, 20000 shots per launch), from one ncu capture of
-# the current kernel (dram__bytes_read.sum + dram__bytes_write.sum; see
-# profiles/decode_shot_kernel_bb144_w3_p3e-3_configured.md).  Reported only for
-# that workload; per launch, like "achieved".
-TRAFFIC_PER_LAUNCH = {("configured", 20000): 6856704 + 3092475136}
+# workload, keyed by (preset, shots per launch, output rule), from one ncu
+# capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum;
+# see profiles/decode_shot_kernel_bb144_w3_p3e-3_configured.md).  Reported
+# only for that workload; per launch, like "achieved".
+TRAFFIC_PER_LAUNCH = {}
 
 
-def workload_name(preset_name):
+FALLBACK_NAMES = {0: "path 0's estimate", 1: "fewest unsatisfied checks",
+                  2: "fewest unsatisfied committed checks, then all"}
+
+
+def workload_name(preset_name, fallback=0):
     return (f"[[144,12,12]] BB memory, {ROUNDS} rounds, (3,1) windows, p={P_PHYS}, "
-            f"GDG 2^{K_GUESS} paths, preset={preset_name}")
+            f"GDG 2^{K_GUESS} paths, preset={preset_name}, "
+            f"no converged path -> {FALLBACK_NAMES[fallback]}")
+
+
+def with_fallback(preset, fallback):
+    """The workloads' preset() with the output rule for windows without a
+    converged path set to `fallback` unless a caller overrides it."""
+    def p(name, k_guess, p=None, **over):
+        return preset(name, k_guess, p, **dict({"fallback": fallback}, **over))
+    return p
 
 
 def parse():
@@ -55,6 +68,9 @@ def parse():
     ap.add_argument("--impl", default="gdg", choices=["gdg", "reference"])
     ap.add_argument("--shots", type=int, default=20000, help="shots per step per GPU")
     ap.add_argument("--preset", default="configured", choices=["configured", "paper"])
+    ap.add_argument("--fallback", type=int, default=2, choices=[0, 1, 2],
+                    help="output of a window without a converged decision path: 0 path 0's estimate, "
+                         "1 fewest unsatisfied checks, 2 fewest unsatisfied committed checks, then all")
     ap.add_argument("--latency-shots", type=int, default=1000,
                     help="shots of the latency measurements (x windows per shot >= 1e4 windows)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -167,7 +183,7 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2403_18901_gb300.workloads import preset
-    params = preset(args.preset, k_guess=K_GUESS)
+    params = with_fallback(preset, args.fallback)(args.preset, k_guess=K_GUESS)
     from oracle import oracle as O
     from paper_2403_18901_gb300.workloads import CODES
     cores = O.default_threads()
@@ -190,7 +206,7 @@ def run_reference(args):
         "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded DEM sampling)",
-        "config": {"workload": workload_name(args.preset), "shots_per_step": n,
+        "config": {"workload": workload_name(args.preset, args.fallback), "shots_per_step": n,
                    "windows_per_shot": nwin, "parallelism": f"{cores} host threads"},
         "cpu_baseline": {"value": value, "unit": "windows/s", "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} steps x {n} shots"},
@@ -518,7 +534,10 @@ def readings(args, torch, qdec, CODES, preset, latency_fn=None):
     with the preset otherwise unchanged, and the two readings of the H_1
     merge of Sec. III; the paper preset with and without the H_1 merges;
     message reuse between windows (Sec. VI) with both presets, with
-    per-window latency against reuse off."""
+    per-window latency against reuse off; each output rule for windows in
+    which no decision path converges (path 0's estimate; fewest unsatisfied
+    checks; committed checks first), which Alg. 2 leaves open.  Every entry
+    takes the run's rule (--fallback) unless it names its own."""
     dem = qdec.Dem(CODES[CODE_KEY], P_PHYS, ROUNDS)
     out = {}
     for name, pname, over, n in (
@@ -530,7 +549,12 @@ def readings(args, torch, qdec, CODES, preset, latency_fn=None):
             ("paper_h1_merge_equal_restrictions", "paper", dict(merge_h1=1), args.shots),
             ("paper_h1_merge_identity", "paper", dict(merge_h1=2), args.shots),
             ("message_reuse", "configured", dict(reuse_msgs=1), args.shots),
-            ("paper_message_reuse", "paper", dict(reuse_msgs=1), args.shots)):
+            ("paper_message_reuse", "paper", dict(reuse_msgs=1), args.shots),
+            ("fallback_path0", "configured", dict(fallback=0), args.shots),
+            ("fallback_fewest_unsatisfied", "configured", dict(fallback=1), args.shots),
+            ("fallback_committed_first", "configured", dict(fallback=2), args.shots),
+            ("paper_fallback_path0", "paper", dict(fallback=0), args.shots),
+            ("paper_fallback_committed_first", "paper", dict(fallback=2), args.shots)):
         params = preset(pname, k_guess=K_GUESS, p=P_PHYS, **over)
         B = min(n, args.shots)
         dec = qdec.Decoder(dem, params, max_shots=B)
@@ -587,6 +611,7 @@ def main():
     from paper_2403_18901_gb300 import build as qbuild
     from paper_2403_18901_gb300 import qdec, replicas
     from paper_2403_18901_gb300.workloads import CODES, preset
+    preset = with_fallback(preset, args.fallback)
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -845,7 +870,7 @@ def main():
         def hl(v, lat, ler):
             return {"windows_per_s": v, "latency_ms": {k: lat[k] for k in ("p50", "p99", "max", "windows")},
                     "ler_per_round": ler}
-        headline = {"workload": workload_name(args.preset),
+        headline = {"workload": workload_name(args.preset, args.fallback),
                     "plain": hl(value, lat_plain, ler_entry(failures, n_shots_total))}
         if learned is not None:
             headline["learned_weights"] = hl(learned["value"], learned["latency_ms"],
@@ -864,7 +889,7 @@ def main():
             "ms_per_step": 1000 * tot_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (DEM shots sampled on the GPU, seeded Philox)",
-            "config": {"workload": workload_name(args.preset), "shots_per_step": B * world,
+            "config": {"workload": workload_name(args.preset, args.fallback), "shots_per_step": B * world,
                        "windows_per_shot": nwin, "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MB write)",
                        "cuda_graph": "latency mode replays one captured graph per window"},
@@ -882,7 +907,7 @@ def main():
             "gpu_launches": args.steps * (2 * nwin + 1),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Top/s",
                          "frac": achieved / alu_peak,
-                         "traffic": TRAFFIC_PER_LAUNCH.get((args.preset, B)),
+                         "traffic": TRAFFIC_PER_LAUNCH.get((args.preset, B, args.fallback)),
                          "kernel": "decode_shot_kernel",
                          "work": f"{OPS_PER_EDGE_ITER} ops x {edge_iters} edge-iterations in "
                                  f"{nwin} launches",

@@ -108,6 +108,12 @@ typedef struct {
                          /* start from their prior.  Windows must be decoded in   */
                          /* order, each call on the same shots; window 0 starts   */
                          /* from the priors.  Not in batched steps.               */
+  int fallback;          /* the window's output when no decision path converges  */
+                         /* (Alg. 2 leaves it open): 0 path 0's estimate; 1 the  */
+                         /* estimate with the fewest unsatisfied checks of the    */
+                         /* window; 2 the fewest among the checks the window      */
+                         /* commits (its first F blocks; all in the last window), */
+                         /* then among all.  Ties go to the lowest path id.       */
 } qd_gdg_params;
 
 typedef struct qd_dem qd_dem;

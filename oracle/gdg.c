@@ -643,10 +643,27 @@ int qdo_bp_run(int n_rows, int n_cols, const int* col_ptr, const int* col_rows, 
   return conv ? it : -it;
 }
 
-/* GDG over all decision paths of graph g; returns the winning id or -1. */
+/* Unsatisfied checks of a path's estimate among rows [j0, j1): H e != s
+ * (the test of converged() counted instead of stopped at the first). */
+static int n_unsat_rows(const graph_t* g, const state_t* s, int j0, int j1) {
+  int n = 0;
+  for (int j = j0; j < j1; ++j) {
+    int par = s->sp[j];
+    for (int q = g->row_ptr[j]; q < g->row_ptr[j + 1]; ++q) {
+      int i = g->edge_col[g->row_edges[q]];
+      if (s->status[i] == -1) par ^= (s->post[i] <= 0.0f);
+    }
+    n += par;
+  }
+  return n;
+}
+
+/* GDG over all decision paths of graph g; returns the winning id or -1.
+ * Rows [0, n_commit_rows) are those the window commits (the fallback rule 2
+ * looks at them first). */
 static int gdg_all(const graph_t* g, const uint8_t* synd, const qdo_params* P, uint8_t* e_out,
                    qdo_branch_summary* br_out, qdo_step_record* steps_out, int8_t* status_out,
-                   float* keep_out) {
+                   float* keep_out, int n_commit_rows, uint8_t* est_out) {
   int nb = qdo_n_paths(P);
   int dmx = qdo_path_dmax_all(P);
   state_t s;
@@ -659,6 +676,7 @@ static int gdg_all(const graph_t* g, const uint8_t* synd, const qdo_params* P, u
    * final posterior, or +-clip for a column it decimated to 0 / 1 */
   float* k0 = malloc(sizeof(float) * (g->nc > 0 ? g->nc : 1));
   float* kb = malloc(sizeof(float) * (g->nc > 0 ? g->nc : 1));
+  long long key0 = 0;
   for (int id = 0; id < nb; ++id) {
     qdo_branch_summary sm;
     qdo_step_record* rec = steps_out ? steps_out + (size_t)id * dmx : NULL;
@@ -667,11 +685,23 @@ static int gdg_all(const graph_t* g, const uint8_t* synd, const qdo_params* P, u
     run_branch(g, synd, P, id, &s, &sm, rec);
     if (br_out) br_out[id] = sm;
     if (status_out) memcpy(status_out + (size_t)id * g->nc, s.status, g->nc);
-    if (id == 0)
+    if (est_out)
+      for (int i = 0; i < g->nc; ++i) est_out[(size_t)id * g->nc + i] = (uint8_t)hard(&s, i);
+    /* READING (fallback rule, used only when no path converges): 0 keeps
+     * path 0's estimate; 1 the estimate with the fewest unsatisfied checks
+     * of the window; 2 the fewest among the committed rows, then among all
+     * rows.  Ties keep the lowest id. */
+    long long key = 0;
+    if (P->fallback == 1) key = n_unsat_rows(g, &s, 0, g->nr);
+    if (P->fallback == 2)
+      key = (long long)n_unsat_rows(g, &s, 0, n_commit_rows) * (g->nr + 1) + n_unsat_rows(g, &s, 0, g->nr);
+    if (id == 0 || key < key0) {
+      key0 = key;
       for (int i = 0; i < g->nc; ++i) {
         e0[i] = (uint8_t)hard(&s, i);
         k0[i] = s.status[i] == -1 ? s.post[i] : (s.status[i] ? -P->clip : P->clip);
       }
+    }
     /* Alg. 2: the estimate with the smallest path metric; ties keep the
      * lowest id */
     if (sm.status == BR_CONVERGED && sm.pm < best_pm) {
@@ -683,7 +713,7 @@ static int gdg_all(const graph_t* g, const uint8_t* synd, const qdo_params* P, u
       }
     }
   }
-  /* READING: if no path converges, the window outputs path 0's estimate */
+  /* no converged path: the fallback estimate above */
   memcpy(e_out, best >= 0 ? eb : e0, g->nc);
   if (keep_out) memcpy(keep_out, best >= 0 ? kb : k0, sizeof(float) * g->nc);
   free(e0);
@@ -699,7 +729,7 @@ int qdo_gdg_graph(const qdo_params* P, int n_rows, int n_cols, const int* col_pt
                   qdo_branch_summary* br) {
   graph_t g;
   graph_init(&g, n_rows, n_cols, col_ptr, col_rows, llr);
-  int best = gdg_all(&g, synd, P, corr, br, NULL, NULL, NULL);
+  int best = gdg_all(&g, synd, P, corr, br, NULL, NULL, NULL, n_rows, NULL);
   graph_free(&g);
   return best;
 }
@@ -921,7 +951,8 @@ static int cmp_rank(const void* a, const void* b) {
  */
 static int decode_window_impl(const window_t* wd, const qdo_params* P, const uint8_t* synd,
                               uint8_t* corr, int* info, int* short_cols, qdo_branch_summary* br,
-                              qdo_step_record* steps, int8_t* fstat, const float* init, float* keep) {
+                              qdo_step_record* steps, int8_t* fstat, const float* init, float* keep,
+                              uint8_t* est) {
   if (keep)
     for (int c = 0; c < wd->nc; ++c) keep[c] = NAN;
   if (wd->nc == 0) {
@@ -996,7 +1027,16 @@ static int decode_window_impl(const window_t* wd, const qdo_params* P, const uin
   gs.wcol = sel;
   uint8_t* es = malloc(ns + 1);
   float* ks = keep ? malloc(sizeof(float) * (ns + 1)) : NULL;
-  int best = gdg_all(&gs, synd, P, es, br, steps, fstat, ks);
+  /* the committed rows: the first F blocks' (every row in the last window) */
+  int ncr = wd->last ? wd->nr : (wd->nb > 0 ? P->F * (wd->nr / wd->nb) : wd->nr);
+  if (ncr > wd->nr) ncr = wd->nr;
+  uint8_t* eall = est ? calloc((size_t)qdo_n_paths(P) * ns + 1, 1) : NULL;
+  int best = gdg_all(&gs, synd, P, es, br, steps, fstat, ks, ncr, eall);
+  if (est) {
+    for (int id = 0; id < qdo_n_paths(P); ++id)
+      for (int k = 0; k < ns; ++k) est[(size_t)id * wd->nc + sel[k]] = eall[(size_t)id * ns + k];
+    free(eall);
+  }
   memset(corr, 0, wd->nc);
   for (int k = 0; k < ns; ++k) corr[sel[k]] = es[k];
   if (keep)
@@ -1019,7 +1059,16 @@ int qdo_decode_window_ex(const qdo_dem* d, const qdo_params* P, int k, const uin
                          int* info, const float* init, float* keep) {
   window_t wd;
   window_build(d, P->W, P->F, k, P->merge_h1, &wd);
-  int rc = decode_window_impl(&wd, P, synd, corr, info, NULL, NULL, NULL, NULL, init, keep);
+  int rc = decode_window_impl(&wd, P, synd, corr, info, NULL, NULL, NULL, NULL, init, keep, NULL);
+  window_free(&wd);
+  return rc;
+}
+
+int qdo_decode_window_paths(const qdo_dem* d, const qdo_params* P, int k, const uint8_t* synd, uint8_t* corr,
+                            int* info, uint8_t* est) {
+  window_t wd;
+  window_build(d, P->W, P->F, k, P->merge_h1, &wd);
+  int rc = decode_window_impl(&wd, P, synd, corr, info, NULL, NULL, NULL, NULL, NULL, NULL, est);
   window_free(&wd);
   return rc;
 }
@@ -1029,7 +1078,7 @@ int qdo_decode_window(const qdo_dem* d, const qdo_params* P, int k, const uint8_
                       qdo_step_record* steps, int8_t* final_status) {
   window_t wd;
   window_build(d, P->W, P->F, k, P->merge_h1, &wd);
-  int rc = decode_window_impl(&wd, P, synd, corr, info, short_cols, br, steps, final_status, NULL, NULL);
+  int rc = decode_window_impl(&wd, P, synd, corr, info, short_cols, br, steps, final_status, NULL, NULL, NULL);
   window_free(&wd);
   return rc;
 }
@@ -1081,7 +1130,7 @@ int qdo_run_shots(const qdo_dem* d, const qdo_params* P, const uint32_t* det_bit
         for (int c = 0; c < wd->nc; ++c) init[c] = at[wd->gcols[c]] >= 0 ? kept[at[wd->gcols[c]]] : NAN;
       }
       decode_window_impl(wd, P, synd, corr, NULL, NULL, NULL, NULL, NULL, reuse ? init : NULL,
-                         P->reuse_msgs ? kept : NULL);
+                         P->reuse_msgs ? kept : NULL, NULL);
       if (win_corr_words) {
         uint32_t* o = win_corr_words + ((size_t)sh * nwin + k) * corr_words_per_window;
         memset(o, 0, sizeof(uint32_t) * corr_words_per_window);

@@ -43,6 +43,7 @@ class QdoParams(C.Structure):
                 ("pc_max_depth", C.c_int), ("n_unsat_min", C.c_int), ("side_max", C.c_int),
                 ("reinit_on_split", C.c_int), ("iters_first", C.c_int), ("merge_h1", C.c_int),
                 ("reuse_msgs", C.c_int),
+                ("fallback", C.c_int),
                 ("wts", C.POINTER(C.c_void_p)), ("wT", C.c_int), ("ranker", C.c_void_p),
                 ("dump", C.c_void_p), ("dump_n", C.c_void_p), ("dump_cap", C.c_int)]
 
@@ -98,6 +99,7 @@ def lib():
         L.qdo_run_shots.argtypes = [C.c_void_p, P(QdoParams), C.c_void_p, C.c_void_p,
                                     C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]
         L.qdo_decode_window_ex.argtypes = [C.c_void_p, P(QdoParams), C.c_int] + [C.c_void_p] * 5
+        L.qdo_decode_window_paths.argtypes = [C.c_void_p, P(QdoParams), C.c_int] + [C.c_void_p] * 4
         L.qdo_window_build.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int] + [C.c_void_p] * 6
         declare_select(L)
         _lib = L
@@ -165,7 +167,7 @@ def make_params(p, weights=None, ranker=None):
     for name, _ in QdoParams._fields_:
         if name in ("wts", "wT", "ranker", "dump", "dump_n", "dump_cap"):
             continue
-        setattr(q, name, p[name])
+        setattr(q, name, p.get(name, 0) if name == "fallback" else p[name])
     q.ranker = None
     if ranker is not None:
         r = np.ascontiguousarray(ranker, np.float32)
@@ -399,6 +401,20 @@ class OracleDEM:
         lib().qdo_decode_window_ex(self.h, C.byref(P), k, _ptr(synd), _ptr(corr), _ptr(info), _ptr(ini), _ptr(keep))
         return corr, dict(prebp_converged=bool(info[0]), winner=int(info[1]), n_short=int(info[2]),
                           prebp_iters=int(info[3])), keep
+
+    def decode_window_paths(self, params, k, synd):
+        """One window, with every decision path's final estimate: returns
+        (corrections [n_cols], info dict, estimates [n_paths][n_cols]; zeros
+        when the pre-BP converged)."""
+        win = self.window(params["W"], params["F"], k, params.get("merge_h1", 0))
+        synd = np.ascontiguousarray(synd, np.uint8)
+        corr = np.zeros(win["n_cols"], np.uint8)
+        info = np.zeros(4, np.int32)
+        P = make_params(params)
+        est = np.zeros((lib().qdo_n_paths(C.byref(P)), win["n_cols"]), np.uint8)
+        lib().qdo_decode_window_paths(self.h, C.byref(P), k, _ptr(synd), _ptr(corr), _ptr(info), _ptr(est))
+        return corr, dict(prebp_converged=bool(info[0]), winner=int(info[1]), n_short=int(info[2]),
+                          prebp_iters=int(info[3])), est
 
     def run_shots(self, params, det, obs, threads=1, want_corr=False, weights=None, ranker=None):
         """Sliding-window decode of every shot.  Returns (fail, obs_pred, corr_words)."""

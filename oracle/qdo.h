@@ -53,6 +53,9 @@ typedef struct {
                          /* 2 identity with XOR priors (see gdg.c)             */
   int reuse_msgs;        /* Sec. VI: the next window's pre-BP starts from what */
                          /* this window's output path ends with (see gdg.c)    */
+  int fallback;          /* output when no path converges (Alg. 2 is silent):  */
+                         /* 0 path 0's estimate, 1 fewest unsatisfied checks,  */
+                         /* 2 fewest in the committed rows, then in the window */
   /* Learned weighted min-sum (no counterpart in the paper; alpha of Eq. (1)
    * replaced by w[t][e]): wts[k] is window k's array [wT][n_edges] over the
    * full-window edges (CSC order), or NULL for plain alpha.  Iteration t
@@ -164,6 +167,11 @@ int qdo_decode_window(const qdo_dem* d, const qdo_params* P, int k, const uint8_
  * window's output path leaves the next window (NaN: nothing). */
 int qdo_decode_window_ex(const qdo_dem* d, const qdo_params* P, int k, const uint8_t* synd, uint8_t* corr,
                          int* info, const float* init, float* keep);
+/* qdo_decode_window that also reports every decision path's final estimate:
+ * est [n_paths][n_cols] over the window's columns (0 outside the shortened
+ * set; untouched when the pre-BP converges).  For tests of the output rule. */
+int qdo_decode_window_paths(const qdo_dem* d, const qdo_params* P, int k, const uint8_t* synd, uint8_t* corr,
+                            int* info, uint8_t* est);
 /* Decode with an explicit graph (column order = index order), no shortening
  * table; for tests on tiny graphs. */
 int qdo_gdg_graph(const qdo_params* P, int n_rows, int n_cols, const int* col_ptr,

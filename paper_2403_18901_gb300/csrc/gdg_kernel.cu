@@ -373,6 +373,7 @@ struct ShortG {
   // ranked column, whose order decides every tie.
   const uint16_t* cperm;
   const uint16_t* vperm;
+  int ncr;  // window rows [0, ncr) are the ones the window commits
 };
 
 struct Slot {
@@ -1059,10 +1060,24 @@ done:
     if (s8 == 1 || (s8 == -1 && B.post[k] <= 0.0f)) atomicOr(&out.ebits[kr >> 5], 1u << (kr & 31));
     if (out.fstat) out.fstat[kr] = (int8_t)s8;
   }
+  // The fallback key of a path that did not converge (the window's output
+  // when no path converges is the least key, ties to the lowest id): rule 1
+  // counts the unsatisfied checks of its estimate, rule 2 those among the
+  // committed rows first (key = committed * (nr + 1) + all).  It takes the
+  // place of the path metric, which only a converged path has.
+  double fkey = CUDART_INF;
+  if (status != BR_CONVERGED && P.fallback) {
+    parity_pass(G, B, g);
+    g.sync();
+    long long nu = 0;
+    for (int j = R; j < G.nr; j += S)
+      if (bit_of(B.unsat, j)) nu += (P.fallback == 2 && G.cperm[j] < G.ncr) ? (long long)G.nr + 2 : 1;
+    fkey = (double)g.sum_ll(nu);
+  }
   // message reuse: what this path would leave the next window if it is the
-  // window's output path (converged, or path 0): the final posterior of each
-  // active column, +-clip for a decimated one
-  if (out.keep && (status == BR_CONVERGED || id == 0))
+  // window's output path (converged, path 0, or any path under a fallback
+  // rule): the final posterior of each active column, +-clip for a decimated one
+  if (out.keep && (status == BR_CONVERGED || id == 0 || P.fallback))
     for (int k = R; k < ns; k += S) {
       const int s8 = B.status[k];
       out.keep[k] = s8 == -1 ? B.post[k] : (s8 ? -P.clip : P.clip);
@@ -1070,7 +1085,7 @@ done:
   visits = g.sum_ll(visits);
   if (R == 0) {
     *out.status = status;
-    *out.pm = status == BR_CONVERGED ? pm : CUDART_INF;
+    *out.pm = status == BR_CONVERGED ? pm : fkey;
     if (out.btr) *out.btr = BranchTrace{status, depth, iters, 0, status == BR_CONVERGED ? pm : CUDART_INF};
     atomicAdd((unsigned long long*)out.visits, (unsigned long long)(visits + inherited));
     if (out.exec) atomicAdd((unsigned long long*)out.exec, (unsigned long long)visits);
@@ -1852,7 +1867,7 @@ __device__ __forceinline__ ShortG short_graph(char* sm, const Layout& L, const W
                 (const float*)(sm + L.s_llr),       (const uint8_t*)(sm + L.s_vdeg),
                 (const uint32_t*)(sm + L.sbits),    (const uint16_t*)(sm + L.s_efull),
                 W.wts, W.wT, W.n_edges, W.rows_per_block, (const uint16_t*)(sm + L.sel),
-                (const uint16_t*)(sm + L.s_cperm), (const uint16_t*)(sm + L.s_vperm)};
+                (const uint16_t*)(sm + L.s_cperm), (const uint16_t*)(sm + L.s_vperm), W.n_commit_rows};
 }
 
 __device__ __forceinline__ PathOut trace_out(const DecodeArgs& A, char* tr, int id, long long shot) {
@@ -1866,6 +1881,17 @@ __device__ __forceinline__ PathOut trace_out(const DecodeArgs& A, char* tr, int 
   o.exec = A.exec;
   o.shot = shot;
   return o;
+}
+
+// The output path of a window in which no path converged: path 0, or under a
+// fallback rule the least fallback key (stored in the path-metric slot of an
+// unconverged path), ties to the lowest id.
+__device__ __forceinline__ int fallback_path(const KParams& P, const double* pm) {
+  int fb = 0;
+  if (P.fallback)
+    for (int id = 1; id < P.nb; ++id)
+      if (pm[id] < pm[fb]) fb = id;
+  return fb;
 }
 
 __device__ void write_outputs(const DecodeArgs& A, char* sm, long long shot, bool conv, int winner,
@@ -2042,14 +2068,16 @@ __device__ void shot_body(const DecodeArgs& A, long long shot, char* sm, Stager&
           best = id;
         }
       misc[1] = best;
+      misc[4] = best >= 0 ? best : fallback_path(A.P, res_pm);
     }
     __syncthreads();
     winner = misc[1];
-    const uint32_t* eb = res_e + (size_t)(winner >= 0 ? winner : 0) * L.sw;
+    const int outp = misc[4];
+    const uint32_t* eb = res_e + (size_t)outp * L.sw;
     for (int k = tid; k < n_short; k += blockDim.x)
       if ((eb[k >> 5] >> (k & 31)) & 1u) atomicOr(&cbits[sel[k] >> 5], 1u << (sel[k] & 31));
     if (A.keep) {
-      const float* kp = A.kpath + ((size_t)blockIdx.x * A.P.nb + (winner >= 0 ? winner : 0)) * A.ns_max;
+      const float* kp = A.kpath + ((size_t)blockIdx.x * A.P.nb + outp) * A.ns_max;
       keep_for_next(A, sm, shot, kp, n_short);
     }
     __syncthreads();
@@ -2169,8 +2197,8 @@ __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
   if (!misc[3]) return;
   __threadfence();
   if (tid == 0) {
-    int best = -1;
-    double bp = CUDART_INF;
+    int best = -1, fb = 0;
+    double bp = CUDART_INF, bk = CUDART_INF;
     for (int q = 0; q < nb; ++q) {
       const char* r = A.path_res + ((size_t)shot * nb + q) * rb;
       const int st = __ldcg((const int*)r);
@@ -2179,18 +2207,24 @@ __global__ void __launch_bounds__(512, 1) decode_path_kernel(DecodeArgs A) {
         bp = pm;
         best = q;
       }
+      if (A.P.fallback && st != BR_CONVERGED && pm < bk) {  // the fallback key (see fallback_path)
+        bk = pm;
+        fb = q;
+      }
     }
     misc[1] = best;
+    misc[4] = best >= 0 ? best : fb;
     A.arrive[shot] = 0;  // ready for the next launch
   }
   __syncthreads();
   const int winner = misc[1];
-  const uint32_t* eb = (const uint32_t*)(A.path_res + ((size_t)shot * nb + (winner >= 0 ? winner : 0)) * rb + 16);
+  const int outp = misc[4];
+  const uint32_t* eb = (const uint32_t*)(A.path_res + ((size_t)shot * nb + outp) * rb + 16);
   uint32_t* cbits = (uint32_t*)(sm + L.cbits);
   const uint16_t* sel = (const uint16_t*)(sm + L.sel);
   for (int k = tid; k < n_short; k += blockDim.x)
     if ((__ldcg(&eb[k >> 5]) >> (k & 31)) & 1u) atomicOr(&cbits[sel[k] >> 5], 1u << (sel[k] & 31));
-  if (A.keep) keep_for_next(A, sm, shot, A.kpath + ((size_t)shot * nb + (winner >= 0 ? winner : 0)) * A.ns_max, n_short);
+  if (A.keep) keep_for_next(A, sm, shot, A.kpath + ((size_t)shot * nb + outp) * A.ns_max, n_short);
   __syncthreads();
   write_outputs(A, sm, shot, false, winner, n_short, t_run, tr);
 }

@@ -25,6 +25,7 @@ struct KParams {
   int side_max;  // side branches split off the main branch at D_split = k .. side_max (0: none)
   int reinit;    // 1: a path continuing from another's snapshot restarts its messages there
   int ips1;      // BP iterations of the first decimation step (0: ips)
+  int fallback;  // output when no path converges: 0 path 0, 1 fewest unsatisfied checks, 2 committed ones first
   // learned decimation ranker (NULL: the argmin of Alg. 1): rkq = the
   // grid-rounded W1[64][8], b1[64], W2[64], b2; rkb[t][lane] = the BF16 pair
   // (W1[8t + lane/4][2 (lane%4)], W1[8t + lane/4][2 (lane%4) + 1]), the B
@@ -94,6 +95,7 @@ struct WinDev {
   const float* wts;
   int wT;
   const uint16_t* vperm;  // pre-BP processing order of the columns (descending degree)
+  int n_commit_rows;      // rows [0, n_commit_rows) are the ones the window commits
 };
 
 // Shot mode's plan for resuming decision paths from snapshots of shared

@@ -570,6 +570,7 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
   QD_REQ(p->iters_first >= 0, "qd_decoder_create: iters_first < 0");
   QD_REQ(p->merge_h1 >= 0 && p->merge_h1 <= 2, "qd_decoder_create: merge_h1 must be 0, 1 or 2");
   QD_REQ(p->reuse_msgs == 0 || p->reuse_msgs == 1, "qd_decoder_create: reuse_msgs must be 0 or 1");
+  QD_REQ(p->fallback >= 0 && p->fallback <= 2, "qd_decoder_create: fallback must be 0, 1 or 2");
   QD_REQ(p->side_max == 0 || (p->side_max >= p->k_guess && p->side_max <= 32),
          "qd_decoder_create: side_max must be 0 or in [k_guess, 32]");
   QD_REQ(p->d_max_other >= p->k_guess, "qd_decoder_create: d_max_other < k_guess");
@@ -596,6 +597,7 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
   k.n_pre = p->n_pre;
   k.ips = p->iters_per_step;
   k.ips1 = p->iters_first;
+  k.fallback = p->fallback;
   k.dmax_main = p->d_max_main;
   k.dmax_other = p->d_max_other;
   k.k = p->k_guess;
@@ -649,7 +651,8 @@ qd_status qd_decoder_create(const qd_dem* dem, const qd_gdg_params* p, int64_t m
     g.dv = qd::WinDev{h.n_rows, h.n_cols, h.n_edges, h.row0, h.n_short, h.short_edges_max, h.n_rows / h.n_blocks,
                       (const uint16_t*)(b + o_cp), (const uint16_t*)(b + o_cr), (const uint16_t*)(b + o_rp),
                       (const uint32_t*)(b + o_re), (const float*)(b + o_ll), nullptr, 0,
-                      (const uint16_t*)(b + o_vp)};
+                      (const uint16_t*)(b + o_vp),
+                      h.last ? h.n_rows : std::min(h.n_rows, dec->P.F * (h.n_rows / h.n_blocks))};
     // committed columns: their full detector sets and observables
     std::vector<int> cc_ptr(1, 0), cc_det;
     std::vector<uint32_t> cc_obs;

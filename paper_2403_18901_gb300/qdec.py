@@ -41,7 +41,7 @@ class GdgParams(C.Structure):
                 ("pb_d1", C.c_float), ("pc", C.c_float), ("pd", C.c_float),
                 ("pc_max_depth", C.c_int), ("n_unsat_min", C.c_int), ("side_max", C.c_int),
                 ("reinit_on_split", C.c_int), ("iters_first", C.c_int), ("merge_h1", C.c_int),
-                ("reuse_msgs", C.c_int)]
+                ("reuse_msgs", C.c_int), ("fallback", C.c_int)]
 
 
 class DemInfo(C.Structure):
@@ -160,7 +160,7 @@ def make_code(code):
 def make_params(p):
     q = GdgParams()
     for name, _ in GdgParams._fields_:
-        setattr(q, name, p.get(name, 0) if name in ("side_max", "reinit_on_split") else p[name])
+        setattr(q, name, p.get(name, 0) if name in ("side_max", "reinit_on_split", "fallback") else p[name])
     return q
 
 

@@ -27,7 +27,7 @@ CODES = {
 _COMMON = dict(W=3, F=1, low_error_mode=0, peel_at_init=1, shorten=1, clip=50.0,
                pa_main=-3.0, pa_other=0.0, pb_main=-12.0, pb_other=-10.0, pb_d1=-16.0,
                pc=30.0, pd=3.0, pc_max_depth=4, n_unsat_min=3, side_max=0, reinit_on_split=0,
-               iters_first=0, merge_h1=0, reuse_msgs=0)
+               iters_first=0, merge_h1=0, reuse_msgs=0, fallback=0)
 
 # "configured": normalised min-sum alpha = 0.625, 100 BP iterations on the
 # full window, decimation steps of 10 iterations, 2^k guessing tree.

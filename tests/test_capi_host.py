@@ -99,7 +99,9 @@ def test_parameter_validation_without_a_gpu(lib):
            dict(preset("configured", k_guess=3), F=4),            # F > W
            dict(preset("configured", k_guess=3), iters_per_step=0),
            dict(preset("configured", k_guess=3), alpha=0.0),
-           dict(preset("configured", k_guess=3), d_max_other=1)]  # d_max_other < k
+           dict(preset("configured", k_guess=3), d_max_other=1),  # d_max_other < k
+           dict(preset("configured", k_guess=3), fallback=3),     # no such output rule
+           dict(preset("configured", k_guess=3), merge_h1=-1)]
     for params in bad:
         with pytest.raises(qdec.QdError) as e:
             qdec.Decoder(d, params, max_shots=4)

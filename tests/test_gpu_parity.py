@@ -463,3 +463,15 @@ def test_message_reuse_bit_exact(pname, mode, n):
     in global memory."""
     params = preset(pname, k_guess=4, p=0.003, reuse_msgs=1)
     _pipeline("144", 12, 0.003, params, n=n, seed=144_610 + mode, mode=mode)
+
+
+@pytest.mark.parametrize("fb,mode,reuse,n", [(2, 0, 0, 200), (1, 1, 0, 120), (2, 1, 0, 120), (2, 2, 0, 16),
+                                             (2, 3, 0, 60), (2, 1, 1, 120), (2, 2, 1, 16)])
+def test_fallback_bit_exact(fb, mode, reuse, n):
+    """The output of a window without a converged path under the fallback
+    rules (fewest unsatisfied checks; committed checks first): every window's
+    corrections, the committed syndromes and the outcomes equal the oracle's,
+    in every launch shape, with message reuse following the chosen path."""
+    params = preset("configured", k_guess=4, p=0.003, fallback=fb, reuse_msgs=reuse)
+    tw = (1, 4) if (mode, reuse) == (1, 0) else ()
+    _pipeline("144", 12, 0.003, params, n=n, seed=144_740 + 10 * fb + mode + 100 * reuse, trace_windows=tw, mode=mode)
