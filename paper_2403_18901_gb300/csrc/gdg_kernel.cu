@@ -52,7 +52,9 @@ constexpr unsigned FULL = 0xffffffffu;
 enum { BR_CONVERGED = 0, BR_MAXDEPTH = 1, BR_CONTRADICTION = 2, BR_NOCAND = 3, BR_INTERNAL = 4 };
 constexpr int kNone = 0x7fffffff;
 
-__device__ __forceinline__ float clipf(float x, float c) { return x > c ? c : (x < -c ? -c : x); }
+// |x| bounded by c; x is never NaN where it is called (a decimated VN's stale
+// message is skipped before), so the min / max form equals the comparisons
+__device__ __forceinline__ float clipf(float x, float c) { return fminf(fmaxf(x, -c), c); }
 
 // mu_{j->i} from the check's compressed state (see gdg_kernel.cuh).
 __device__ __forceinline__ float c2v_msg(float alpha, float clip, const CNState& c, int e, uint32_t sg) {
@@ -1704,17 +1706,24 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
       const int i = Wg.vperm[i0];  // descending degree: the lanes of a round loop alike
       float p = Wg.llr[i];
       const int eb = Wg.col_ptr[i], ee = Wg.col_ptr[i + 1];
-      auto msg = [&](int e) {
-        const float wt = LW ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t, e) : P.alpha;
-        return c2v<LW>(wt, P.clip, cns[Wg.col_rows[e]], e, sign[e]);
-      };
-      int e = eb;  // ascending check order (Eq. (2))
-      for (; e + 1 < ee; e += 2) {
-        const float c0 = msg(e), c1 = msg(e + 1);
-        p = __fadd_rn(p, c0);
-        p = __fadd_rn(p, c1);
+      // up to six messages requested at once, then added in ascending check
+      // order (Eq. (2))
+      for (int e0 = eb; e0 < ee; e0 += 6) {
+        CNState c[6];
+        uint32_t sg[6];
+#pragma unroll
+        for (int u = 0; u < 6; ++u)
+          if (e0 + u < ee) {
+            c[u] = cns[Wg.col_rows[e0 + u]];
+            sg[u] = sign[e0 + u];
+          }
+#pragma unroll
+        for (int u = 0; u < 6; ++u)
+          if (e0 + u < ee) {
+            const float wt = LW ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t, e0 + u) : P.alpha;
+            p = __fadd_rn(p, c2v<LW>(wt, P.clip, c[u], e0 + u, sg[u]));
+          }
       }
-      if (e < ee) p = __fadd_rn(p, msg(e));
       post[i] = p;
       if (kacc) {
         float kv;
