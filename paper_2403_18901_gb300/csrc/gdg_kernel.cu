@@ -714,12 +714,15 @@ __device__ void write_snapshot(char* dst, const ForkCtx& F, const Grp& g, int D,
 // of its active VNs' hard decisions (Eq. (4)) from the posteriors it reads:
 // for it >= 2 this pass is the convergence test H e = s of the previous
 // iteration (Sec. II-A).  Returns whether this lane saw an unsatisfied check.
-template <bool LW, int TPC>
-__device__ __forceinline__ bool check_pass(const KParams& P, const ShortG& G, const Slot& B, int R, int S, bool first,
-                                           int tw, long long& visits) {
+template <bool LW, int TPC, int FM>
+__device__ __forceinline__ bool check_pass_fm(const KParams& P, const ShortG& G, const Slot& B, int R, int S,
+                                              bool first_rt, int tw, long long& visits) {
+  // FM: 0 the first-iteration flag at run time, 1 / 2 fixed true / false
+  const bool first = FM == 0 ? first_rt : FM == 1;
   const int nr = G.nr, sub = R & (TPC - 1);
   const int nr_rounds = (nr + S / TPC - 1) / (S / TPC) * (S / TPC);
   bool unsat = false;
+  int nvis = 0;  // this pass's active edge visits (added to the 64-bit count once)
   for (int j0 = R / TPC; j0 < nr_rounds; j0 += S / TPC) {
     const int j = j0 < nr ? j0 : nr - 1;
     const int d = j0 < nr ? B.deg[j] : 0;
@@ -737,7 +740,7 @@ __device__ __forceinline__ bool check_pass(const KParams& P, const ShortG& G, co
       if (pv != pv) return;  // stale message of a decimated VN
       hp ^= pv <= 0.0f;
       const int e = (int)(ent & 0xFFFFu);
-      ++visits;
+      ++nvis;
       // the previous iteration's multiplier, only when there was one (tw >= 1)
       const float wprev = (LW && !first) ? edge_weight(G.wts, G.wT, G.wE, P.alpha, tw, G.efull[e]) : P.alpha;
       const float v = first ? pv : clipf(__fsub_rn(pv, c2v<LW>(wprev, P.clip, oc, e, sg)), P.clip);
@@ -770,7 +773,19 @@ __device__ __forceinline__ bool check_pass(const KParams& P, const ShortG& G, co
     if (sub == 0 && d > 0)
       B.cns[j] = cn_store<LW>(P.alpha, P.clip, m1, m2, am, neg ^ bit_of(B.sp, j), d == 1, oc.pad);
   }
+  visits += nvis;
   return unsat;
+}
+
+// One-warp paths (TPC 1) run a copy specialised for the first iteration after
+// the messages were (re)initialised and one for the others.
+template <bool LW, int TPC>
+__device__ __forceinline__ bool check_pass(const KParams& P, const ShortG& G, const Slot& B, int R, int S, bool first,
+                                           int tw, long long& visits) {
+  if (TPC == 1)
+    return first ? check_pass_fm<LW, TPC, 1>(P, G, B, R, S, true, tw, visits)
+                 : check_pass_fm<LW, TPC, 2>(P, G, B, R, S, false, tw, visits);
+  return check_pass_fm<LW, TPC, 0>(P, G, B, R, S, first, tw, visits);
 }
 
 // One decision path of Alg. 2 on the shortened window, run by group g.
