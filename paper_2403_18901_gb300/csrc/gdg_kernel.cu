@@ -745,13 +745,9 @@ __device__ __forceinline__ bool check_pass_fm(const KParams& P, const ShortG& G,
       const float wprev = (LW && !first) ? edge_weight(G.wts, G.wT, G.wE, P.alpha, tw, G.efull[e]) : P.alpha;
       const float v = first ? pv : clipf(__fsub_rn(pv, c2v<LW>(wprev, P.clip, oc, e, sg)), P.clip);
       const float a = fabsf(v);
-      if (a < m1) {
-        m2 = m1;
-        m1 = a;
-        am = e;
-      } else if (a < m2) {
-        m2 = a;
-      }
+      am = a < m1 ? e : am;
+      m2 = fminf(m2, fmaxf(m1, a));
+      m1 = fminf(m1, a);
       const uint32_t sgn = v < 0.0f;
       neg ^= sgn;
       B.sign[e] = (uint8_t)sgn;
@@ -1473,13 +1469,9 @@ __device__ int prebp_cluster(const DecodeArgs& A, const WinDev& W, const WinDev&
           const float wprev = (LW && t > 1) ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t - 1, e) : P.alpha;
           const float v = (t == 1) ? pv[u] : clipf(__fsub_rn(pv[u], c2v<LW>(wprev, P.clip, oc, e, sg[u])), P.clip);
           const float a = fabsf(v);
-          if (a < m1) {
-            m2 = m1;
-            m1 = a;
-            am = e;
-          } else if (a < m2) {
-            m2 = a;
-          }
+          am = a < m1 ? e : am;
+          m2 = fminf(m2, fmaxf(m1, a));
+          m1 = fminf(m1, a);
           const uint32_t sgn = v < 0.0f;
           neg ^= sgn;
           sign[e] = (uint8_t)sgn;
@@ -1690,13 +1682,9 @@ __device__ bool window_prefix(const DecodeArgs& A, const WinDev& W, char* sm, lo
           const float wprev = (LW && t > 1) ? edge_weight(W.wts, W.wT, W.n_edges, P.alpha, t - 1, e) : P.alpha;
           const float v = (t == 1) ? pv[u] : clipf(__fsub_rn(pv[u], c2v<LW>(wprev, P.clip, oc, e, sg[u])), P.clip);
           const float a = fabsf(v);
-          if (a < m1) {
-            m2 = m1;
-            m1 = a;
-            am = e;
-          } else if (a < m2) {
-            m2 = a;
-          }
+          am = a < m1 ? e : am;
+          m2 = fminf(m2, fmaxf(m1, a));
+          m1 = fminf(m1, a);
           const uint32_t sgn = v < 0.0f;
           neg ^= sgn;
           sign[e] = (uint8_t)sgn;
