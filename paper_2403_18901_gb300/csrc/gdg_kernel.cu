@@ -736,30 +736,32 @@ __device__ __forceinline__ bool check_pass_fm(const KParams& P, const ShortG& G,
     uint32_t neg = 0, hp = 0;
     // one row entry; the (min1, min2) pair and so every message do not
     // depend on the order in which a check sees its inputs
+    // (no branch: a NaN input -- the stale message of a decimated VN, or no
+    // entry -- takes part with magnitude +inf and writes nothing)
     auto take = [&](uint32_t ent, float pv, uint32_t sg) {
-      if (pv != pv) return;  // stale message of a decimated VN
-      hp ^= pv <= 0.0f;
+      const bool live = pv == pv;
+      hp ^= pv <= 0.0f;  // false for NaN
       const int e = (int)(ent & 0xFFFFu);
-      ++nvis;
+      nvis += live;
       // the previous iteration's multiplier, only when there was one (tw >= 1)
       const float wprev = (LW && !first) ? edge_weight(G.wts, G.wT, G.wE, P.alpha, tw, G.efull[e]) : P.alpha;
       const float v = first ? pv : clipf(__fsub_rn(pv, c2v<LW>(wprev, P.clip, oc, e, sg)), P.clip);
-      const float a = fabsf(v);
+      const float a = live ? fabsf(v) : CUDART_INF_F;
       am = a < m1 ? e : am;
       m2 = fminf(m2, fmaxf(m1, a));
       m1 = fminf(m1, a);
-      const uint32_t sgn = v < 0.0f;
+      const uint32_t sgn = live && v < 0.0f;
       neg ^= sgn;
-      B.sign[e] = (uint8_t)sgn;
+      if (live) B.sign[e] = (uint8_t)sgn;
     };
     const int qe = d ? (int)(oc.pad >> 16) : 0;
     for (int q = (d ? (int)(oc.pad & 0xFFFFu) : 0) + 2 * sub; q < qe; q += 2 * TPC) {
       const bool two = q + 1 < qe;
       const uint32_t e0 = G.rowent[q], e1 = two ? G.rowent[q + 1] : e0;
-      const float p0 = B.post[e0 >> 16], p1 = B.post[e1 >> 16];
+      const float p0 = B.post[e0 >> 16], p1 = two ? B.post[e1 >> 16] : stale();
       const uint32_t s0 = B.sign[e0 & 0xFFFFu], s1 = B.sign[e1 & 0xFFFFu];
       take(e0, p0, s0);
-      if (two) take(e1, p1, s1);
+      take(e1, p1, s1);
     }
     if (TPC > 1) {
       group_min2(m1, m2, am, neg, TPC);
@@ -883,7 +885,8 @@ __device__ int run_path(const KParams& P, const ShortG& G, const Slot& B, int id
       const bool hist0 = it == ips - 3;
       // variables in label order (descending degree): the lanes of a round loop alike
       for (int k = R; k < ns; k += S) {
-        if (B.status[k] != -1) continue;
+        // (a decimated column runs the loop too, without a branch, and stores nothing)
+        const bool act = B.status[k] == -1;
         float p = G.llr[k];
         const int eb = G.colptr[k], ee = G.colptr[k + 1];
         auto msg = [&](int e) {
@@ -898,6 +901,7 @@ __device__ int run_path(const KParams& P, const ShortG& G, const Slot& B, int id
           p = __fadd_rn(p, c1);
         }
         if (e < ee) p = __fadd_rn(p, msg(e));
+        if (!act) continue;
         B.post[k] = p;
         if (hist) {
           if (P.rkq || P.dump) B.hq[4 * k + (it - (ips - 3))] = qhist(p);
