@@ -67,7 +67,8 @@ __device__ __forceinline__ float c2v_msg(float alpha, float clip, const CNState&
 // Check state as stored.  With learned weights the magnitudes stay unscaled
 // (each edge applies its own weight); for the plain decoder they are stored
 // already multiplied by alpha (alpha * clip for a single active input), the
-// same FP32 products c2v_msg forms, so a message is one select and a sign.
+// same FP32 products c2v_msg forms, with the parity as their sign, so a
+// message is one select and the edge's own sign.
 // `rows` (the check's CSR range, begin | end << 16) rides along in the
 // record's last word, so the check pass loads it with the state.
 template <bool LW>
@@ -76,14 +77,15 @@ __device__ __forceinline__ CNState cn_store(float alpha, float clip, float m1, f
   if (LW) return CNState{m1, m2, (uint32_t)am | (par << 16) | ((uint32_t)single << 17), rows};
   const float s1 = __fmul_rn(alpha, single ? clip : m1);
   const float s2 = single ? s1 : __fmul_rn(alpha, m2);
-  return CNState{s1, s2, (uint32_t)am | (par << 16), rows};
+  // the sign parity rides in the sign bits of the two (non-negative) magnitudes
+  return CNState{par ? -s1 : s1, par ? -s2 : s2, (uint32_t)am, rows};
 }
 
 template <bool LW>
 __device__ __forceinline__ float c2v(float w, float clip, const CNState& c, int e, uint32_t sg) {
   if (LW) return c2v_msg(w, clip, c, e, sg);
-  const float m = ((c.ac & 0xFFFFu) == (uint32_t)e) ? c.m2 : c.m1;
-  return ((((c.ac >> 16) & 1u) ^ sg) != 0) ? -m : m;
+  const float m = (c.ac == (uint32_t)e) ? c.m2 : c.m1;  // signed by the parity already
+  return sg ? -m : m;
 }
 
 __device__ __forceinline__ uint32_t bit_of(const uint32_t* w, int j) { return (w[j >> 5] >> (j & 31)) & 1u; }

@@ -137,11 +137,12 @@ struct WmsGraph {
   float clip;
 };
 
-// Compressed state of one check node: two smallest |input| (multiplied by
-// alpha for the plain decoder; alpha * clip twice when exactly one input is
-// active), the edge holding the smallest (low 16 bits of ac) and flags
-// (bit 16: sign parity xor s_j; with learned weights bit 17: exactly one
-// active input, the magnitudes then unscaled).
+// Compressed state of one check node: two smallest |input| and the edge
+// holding the smallest (ac).  Plain decoder: the magnitudes multiplied by
+// alpha (alpha * clip twice when exactly one input is active), each negated
+// when the sign parity xor s_j is 1, and ac = the edge.  Learned weights: the
+// magnitudes unscaled, ac = edge | parity << 16 | (exactly one active input)
+// << 17.
 struct __align__(16) CNState {
   float m1, m2;
   uint32_t ac, pad;
