@@ -52,9 +52,10 @@ constexpr unsigned FULL = 0xffffffffu;
 enum { BR_CONVERGED = 0, BR_MAXDEPTH = 1, BR_CONTRADICTION = 2, BR_NOCAND = 3, BR_INTERNAL = 4 };
 constexpr int kNone = 0x7fffffff;
 
-// |x| bounded by c; x is never NaN where it is called (a decimated VN's stale
-// message is skipped before), so the min / max form equals the comparisons
-__device__ __forceinline__ float clipf(float x, float c) { return fminf(fmaxf(x, -c), c); }
+// |x| bounded by c by min / max: for finite x the comparisons' result; a NaN
+// x (only a dead entry of a decision path's check pass) gives +c, so its sign
+// bit is 0 and needs no mask there
+__device__ __forceinline__ float clipf(float x, float c) { return fmaxf(fminf(x, c), -c); }
 
 // mu_{j->i} from the check's compressed state (see gdg_kernel.cuh).
 __device__ __forceinline__ float c2v_msg(float alpha, float clip, const CNState& c, int e, uint32_t sg) {
@@ -744,7 +745,6 @@ __device__ __forceinline__ bool check_pass_fm(const KParams& P, const ShortG& G,
       const bool live = pv == pv;
       hp ^= pv <= 0.0f;  // false for NaN
       const int e = (int)(ent & 0xFFFFu);
-      nvis += live;
       // the previous iteration's multiplier, only when there was one (tw >= 1)
       const float wprev = (LW && !first) ? edge_weight(G.wts, G.wT, G.wE, P.alpha, tw, G.efull[e]) : P.alpha;
       const float v = first ? pv : clipf(__fsub_rn(pv, c2v<LW>(wprev, P.clip, oc, e, sg)), P.clip);
@@ -752,10 +752,11 @@ __device__ __forceinline__ bool check_pass_fm(const KParams& P, const ShortG& G,
       am = a < m1 ? e : am;
       m2 = fminf(m2, fmaxf(m1, a));
       m1 = fminf(m1, a);
-      const uint32_t sgn = live && v < 0.0f;
+      const uint32_t sgn = v < 0.0f;  // false for a NaN input: clipf gives +clip, the first pass NaN
       neg ^= sgn;
       if (live) B.sign[e] = (uint8_t)sgn;
     };
+    if (sub == 0) nvis += d;  // the row's active entries (B.deg counts the active VNs of a check)
     const int qe = d ? (int)(oc.pad >> 16) : 0;
     for (int q = (d ? (int)(oc.pad & 0xFFFFu) : 0) + 2 * sub; q < qe; q += 2 * TPC) {
       const bool two = q + 1 < qe;
