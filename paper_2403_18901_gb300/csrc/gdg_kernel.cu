@@ -290,6 +290,14 @@ struct WarpGrp {  // one warp
     return v;
   }
   __device__ void argmin(float& v, int& k) const { warp_argmin(v, k); }
+  // SELECT-VN's reductions in one: two lexicographic argmins and a count;
+  // every lane's shared-memory writes are visible after it
+  __device__ void select_reduce(float& bv, int& bk, float& tv, int& tk, int& n) const {
+    warp_argmin(bv, bk);
+    warp_argmin(tv, tk);
+    n = (int)__reduce_add_sync(FULL, (unsigned)n);
+    __syncwarp();
+  }
 };
 
 struct CtaGrp {  // the whole CTA; every member must call every primitive
@@ -358,6 +366,45 @@ struct CtaGrp {  // the whole CTA; every member must call every primitive
         v = rv[i];
         k = rk[i];
       }
+  }
+  // SELECT-VN's reductions in one exchange (two barriers instead of seven):
+  // two lexicographic argmins and a count, for at most 16 warps (the
+  // path-mode CTA); every thread's shared-memory writes are visible after it
+  __device__ void select_reduce(float& bv, int& bk, float& tv, int& tk, int& n) const {
+    warp_argmin(bv, bk);
+    warp_argmin(tv, tk);
+    n = (int)__reduce_add_sync(FULL, (unsigned)n);
+    float* r_bv = (float*)red;
+    int* r_bk = (int*)(red + 64);
+    float* r_tv = (float*)(red + 128);
+    int* r_tk = (int*)(red + 192);
+    int* r_n = (int*)(red + 256);
+    __syncthreads();
+    if ((rank & 31) == 0) {
+      const int w = rank >> 5;
+      r_bv[w] = bv;
+      r_bk[w] = bk;
+      r_tv[w] = tv;
+      r_tk[w] = tk;
+      r_n[w] = n;
+    }
+    __syncthreads();
+    bv = r_bv[0];
+    bk = r_bk[0];
+    tv = r_tv[0];
+    tk = r_tk[0];
+    n = r_n[0];
+    for (int i = 1; i < (size >> 5); ++i) {
+      if (r_bv[i] < bv || (r_bv[i] == bv && r_bk[i] < bk)) {
+        bv = r_bv[i];
+        bk = r_bk[i];
+      }
+      if (r_tv[i] < tv || (r_tv[i] == tv && r_tk[i] < tk)) {
+        tv = r_tv[i];
+        tk = r_tk[i];
+      }
+      n += r_n[i];
+    }
   }
 };
 
@@ -1024,12 +1071,11 @@ __device__ int run_path(const KParams& P, const ShortG& G, const Slot& B, int id
         g.sync();  // the aggressive decisions are visible
         ranker_select(P, G, B, g, bL, bk);
         if (bk != kNone) bL = B.acc[bk & 0xFFFF];  // f keeps the rule of Alg. 1: [L <= 0]
+        nagg = g.sum_i(nagg);
+        g.sync();
       } else {
-        g.argmin(bL, bk);
-        g.argmin(tL, tk);
+        g.select_reduce(bL, bk, tL, tk, nagg);
       }
-      nagg = g.sum_i(nagg);
-      g.sync();
       int gsel, f;
       if (tk != kNone) {
         gsel = tk & 0xFFFF;
