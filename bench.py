@@ -79,7 +79,7 @@ def parse():
                     help="Adam steps per window type for the learned weights (0: skip); "
                          "245 x 4096 = 1.0e6 samples per window type")
     ap.add_argument("--train-batch", type=int, default=4096)
-    ap.add_argument("--ranker-steps", type=int, default=300,
+    ap.add_argument("--ranker-steps", type=int, default=1500,
                     help="Adam steps of the decimation ranker (0: skip)")
     ap.add_argument("--paper-shots", type=int, default=20000,
                     help="shots of the paper-preset (Fig. 2 tree) measurement (0: skip)")
