@@ -39,7 +39,7 @@ BYTES_PER_EDGE_ITER = 16  # explicit-message shared-memory bytes per edge and it
 # capture of the current kernel (dram__bytes_read.sum + dram__bytes_write.sum;
 # see profiles/decode_shot_kernel_bb144_w3_p3e-3_configured.md).  Reported
 # only for that workload; per launch, like "achieved".
-TRAFFIC_PER_LAUNCH = {("configured", 20000, 2): 8515072 + 3022093568}
+TRAFFIC_PER_LAUNCH = {("configured", 20000, 2): 6414336 + 3036823040}
 
 
 FALLBACK_NAMES = {0: "path 0's estimate", 1: "fewest unsatisfied checks",
