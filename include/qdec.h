@@ -324,8 +324,9 @@ qd_status qd_decode_shots_host(qd_decoder* dec, const uint32_t* det_bits, const 
  * for shared memory), using the buffers the decoder allocated at creation;
  * the work counters add to the decoder's, read by qd_decoder_counters.
  * The first call on a device looks up the array's device address (once per
- * device, with that device current).  All calls share the array and it keeps the previous call's
- * contents: two calls whose work can overlap on the same GPU (for example
+ * device, with that device current).  All calls share the array and it
+ * keeps the previous call's contents: two calls whose work can overlap on
+ * the same GPU (for example
  * calls on two different streams, or on two decoders) race with each other;
  * issue them on one stream per device.  Allocates nothing and makes no
  * allocating library call.
