@@ -326,10 +326,9 @@ qd_status qd_decode_shots_host(qd_decoder* dec, const uint32_t* det_bits, const 
  * The first call on a device looks up the array's device address (once per
  * device, with that device current).  All calls share the array and it
  * keeps the previous call's contents: two calls whose work can overlap on
- * the same GPU (for example
- * calls on two different streams, or on two decoders) race with each other;
- * issue them on one stream per device.  Allocates nothing and makes no
- * allocating library call.
+ * the same GPU (for example calls on two different streams, or on two
+ * decoders) race with each other; issue them on one stream per device.
+ * Allocates nothing and makes no allocating library call.
  */
 #define QD_STATIC_SCRATCH_BYTES (8u << 20)
 qd_status qd_decode_commit_static(qd_decoder* dec, int k, uint32_t* det_bits, int64_t n_shots,
