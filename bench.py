@@ -40,6 +40,13 @@ BYTES_PER_EDGE_ITER = 16  # explicit-message shared-memory bytes per edge and it
 # see profiles/decode_shot_kernel_bb144_w3_p3e-3_configured.md).  Reported
 # only for that workload; per launch, like "achieved".
 TRAFFIC_PER_LAUNCH = {("configured", 20000, 2): 6414336 + 3036823040}
+# Unit utilisation of the same kernel from one ncu --set full capture of a
+# 4000-shot launch of this workload (same profile file): the shared-memory
+# data pipe (l1tex__data_pipe_lsu_wavefronts_mem_shared, % of peak) and the
+# ALU pipe (sm__pipe_alu_cycles_active, % of peak), as fractions.  What bounds
+# the kernel in hardware terms; the algorithmic fractions above count only
+# the method's arithmetic and message bytes.
+PIPES_PER_LAUNCH = {("configured", 2): {"shared_data_pipe": 0.695, "alu_pipe": 0.574}}
 
 
 FALLBACK_NAMES = {0: "path 0's estimate", 1: "fewest unsatisfied checks",
@@ -919,7 +926,8 @@ def main():
                                            f"read and written) against {n_sm} SMs x 128 B/clk x {sm_mhz:.0f} MHz "
                                            f"({peak_kind} sm_max_mhz); the kernel keeps compressed check state "
                                            f"and moves fewer bytes than this count"},
-                         "edge_iterations_executed": edge_exec},
+                         "edge_iterations_executed": edge_exec,
+                         "ncu_pipes": PIPES_PER_LAUNCH.get((args.preset, args.fallback))},
             "launch": dec.launch_info(1),
             "edge_iterations_per_window": edge_iters / (B * nwin),
             "gdg_windows_frac": float(kc[3]) / (B * nwin),
