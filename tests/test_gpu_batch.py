@@ -137,3 +137,31 @@ def test_members_match_oracle(setup):
         assert (_u32(pred[0]) == opred).all()
         fail = (_u32(resid[0]) & 1) | ((_u32(pred[0]) != obs0) << 1)
         assert (fail == ofail).all()
+
+
+def test_output_rules_in_a_batch():
+    """Members with different output rules for windows without a converged
+    path (0 path 0, 1 fewest unsatisfied checks, 2 committed checks first)
+    in one batch: each member equals its own per-decoder path, and a rule-2
+    member equals the oracle."""
+    mem = []
+    for i, (key, R, W, n) in enumerate(MEMBERS):
+        d = qdec.Dem(CODES[key], P, R)
+        params = preset("configured", k_guess=3, p=P, W=W, fallback=i % 3)
+        dec = qdec.Decoder(d, params, max_shots=n)
+        det, obs = d.sample(seed=950 + i, shot_offset=0, n_shots=n)
+        mem.append(dict(key=key, R=R, W=W, n=n, dem=d, params=params, dec=dec, det=det, obs=obs))
+    b = qdec.Batch([m["dec"] for m in mem])
+    det, pred, resid = _fresh(mem)
+    n = [m["n"] for m in mem]
+    for j in range(b.n_steps):
+        b.step(j, det, n, pred, resid)
+    _check(mem, det, pred, resid)
+    m = mem[2]  # [[90]], W = 4, rule 2
+    assert m["params"]["fallback"] == 2
+    o = oracle_dem(m["key"], P, m["R"])
+    det0, obs0 = o.sample(952, 0, m["n"])
+    ofail, opred, _ = o.run_shots(m["params"], det0, obs0, threads=8)
+    assert (_u32(pred[2]) == opred).all()
+    fail = (_u32(resid[2]) & 1) | ((_u32(pred[2]) != obs0) << 1)
+    assert (fail == ofail).all()
