@@ -23,11 +23,13 @@ CODES = {
 }
 
 # Decoder parameters shared by both presets: Alg. 3 thresholds (P_A..P_D),
-# the message clip of 50, peeling and shortening to 2w' columns.
+# the message clip of 50, peeling and shortening to 2w' columns; a window in
+# which no decision path converges outputs the estimate with the fewest
+# unsatisfied committed checks (fallback 2; Alg. 2 leaves this case open).
 _COMMON = dict(W=3, F=1, low_error_mode=0, peel_at_init=1, shorten=1, clip=50.0,
                pa_main=-3.0, pa_other=0.0, pb_main=-12.0, pb_other=-10.0, pb_d1=-16.0,
                pc=30.0, pd=3.0, pc_max_depth=4, n_unsat_min=3, side_max=0, reinit_on_split=0,
-               iters_first=0, merge_h1=0, reuse_msgs=0, fallback=0)
+               iters_first=0, merge_h1=0, reuse_msgs=0, fallback=2)
 
 # "configured": normalised min-sum alpha = 0.625, 100 BP iterations on the
 # full window, decimation steps of 10 iterations, 2^k guessing tree.

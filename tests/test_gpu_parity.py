@@ -465,7 +465,7 @@ def test_message_reuse_bit_exact(pname, mode, n):
     _pipeline("144", 12, 0.003, params, n=n, seed=144_610 + mode, mode=mode)
 
 
-@pytest.mark.parametrize("fb,mode,reuse,n", [(2, 0, 0, 200), (1, 1, 0, 120), (2, 1, 0, 120), (2, 2, 0, 16),
+@pytest.mark.parametrize("fb,mode,reuse,n", [(0, 1, 0, 120), (2, 0, 0, 200), (1, 1, 0, 120), (2, 1, 0, 120), (2, 2, 0, 16),
                                              (2, 3, 0, 60), (2, 1, 1, 120), (2, 2, 1, 16)])
 def test_fallback_bit_exact(fb, mode, reuse, n):
     """The output of a window without a converged path under the fallback

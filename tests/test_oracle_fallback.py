@@ -79,7 +79,7 @@ def test_rule_two_clears_committed_residue():
     estimate, and on a configured-preset sample it clears some that rule 0
     leaves (the residue that would fail Eq. (11) once committed)."""
     o = oracle_dem("144", 0.003, 12)
-    P0 = preset("configured", k_guess=4, p=0.003)
+    P0 = preset("configured", k_guess=4, p=0.003, fallback=0)
     P2 = dict(P0, fallback=2)
     win = o.window(3, 1, 5)
     H = _dense(win)
