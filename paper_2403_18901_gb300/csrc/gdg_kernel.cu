@@ -14,7 +14,9 @@
 //       Fig. 2): BP steps of iters_per_step iterations, SELECT-VN (Alg. 1)
 //       with aggressive decimation (Alg. 3), guess value by the path id,
 //       peeling
-//   a8  minimum path metric Eq. (5) over converged paths, ties to the lowest id
+//   a8  minimum path metric Eq. (5) over converged paths, ties to the lowest id;
+//       without a converged path, path 0 or (fallback rules) the estimate with
+//       the fewest unsatisfied (committed, then all) checks
 //   (message reuse between windows, optional) the output path's final
 //       posteriors kept per window column; the next window's pre-BP starts
 //       its first VN->CN messages from them
