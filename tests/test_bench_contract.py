@@ -40,3 +40,13 @@ def test_gpu_arm_fails_loudly_without_a_gpu():
     r = _run(["--steps", "1", "--warmup", "3"], timeout=300)
     assert r.returncode != 0
     assert not r.stdout.strip(), "no bench line may come from a CPU fallback"
+
+
+def test_reference_arm_takes_the_output_rule():
+    """--fallback reaches the oracle and the workload name: the reference arm
+    times the same decoder configuration as the GPU arm."""
+    for fb, words in ((0, "path 0's estimate"), (2, "fewest unsatisfied committed checks")):
+        r = _run(["--impl", "reference", "--steps", "1", "--warmup", "3", "--fallback", str(fb)])
+        assert r.returncode == 0, r.stderr[-2000:]
+        line = json.loads(r.stdout.strip().splitlines()[-1])
+        assert words in line["config"]["workload"], line["config"]["workload"]
